@@ -1,0 +1,157 @@
+"""CPU oracle for the batched octree hydro step (ctypes binding of hydro_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by the smoke check and by the
+CPU-baseline / reference leg of the benchmark.  The CUDA library and its Python
+binding never import it, and it imports nothing from them.
+
+``build()`` compiles ``hydro_oracle.c`` with gcc (-O2 -ffp-contract=off, OpenMP
+when available) into ``liboracle.so`` next to this file.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hydro_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+NF, NP = 11, 14
+RK3_BETA = (1.0, 0.25, 2.0 / 3.0)  # Shu-Osher SSP-RK3 stage weights beta (alpha = 1 - beta)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library; returns its path."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "hydro_oracle.h"))):
+        return _LIB
+    base = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c99", _SRC, "-o", _LIB,
+            "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True)
+    return _LIB
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("gamma", ctypes.c_double), ("de_switch", ctypes.c_double),
+                ("flux_form", ctypes.c_int32), ("dx", ctypes.c_void_p), ("neighbor", ctypes.c_void_p),
+                ("neighbor_rel", ctypes.c_void_p), ("octant", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.oracle_ppm_pencil.argtypes = [dp, dp, dp]
+        L.oracle_face_eos.argtypes = [dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, dp, dp]
+        L.oracle_face_flux.argtypes = [dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, dp]
+        L.oracle_face_flux.restype = ctypes.c_double
+        L.oracle_stage.argtypes = [ctypes.POINTER(_Grid), ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_void_p, dp, ctypes.c_void_p, ctypes.c_int]
+        L.oracle_fill_ghosts.argtypes = [ctypes.POINTER(_Grid), ctypes.c_void_p]
+        L.oracle_totals.argtypes = [ctypes.POINTER(_Grid), ctypes.c_void_p, dp]
+        _lib = L
+    return _lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def ppm_pencil(q: Sequence[float]) -> Tuple[np.ndarray, np.ndarray]:
+    q = np.ascontiguousarray(q, np.float64)
+    assert q.shape == (NP,)
+    aL = np.full(NP, np.nan)
+    aR = np.full(NP, np.nan)
+    lib().oracle_ppm_pencil(_dptr(q), _dptr(aL), _dptr(aR))
+    return aL, aR
+
+
+def face_eos(U, d, gamma=5.0 / 3.0, eta=1e-3):
+    U = np.ascontiguousarray(U, np.float64)
+    u, p, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    lib().oracle_face_eos(_dptr(U), d, gamma, eta, ctypes.byref(u), ctypes.byref(p), ctypes.byref(c))
+    return u.value, p.value, c.value
+
+
+def face_flux(UL, UR, d, gamma=5.0 / 3.0, eta=1e-3, form=0):
+    UL = np.ascontiguousarray(UL, np.float64)
+    UR = np.ascontiguousarray(UR, np.float64)
+    F = np.zeros(NF)
+    a = lib().oracle_face_flux(_dptr(UL), _dptr(UR), d, gamma, eta, form, _dptr(F))
+    return F, a
+
+
+class Oracle:
+    """Oracle bound to one grid descriptor (see ``paper_2210_06437_gb300.workloads.Grid``)."""
+
+    def __init__(self, grid, flux_form: int = 0, gamma: Optional[float] = None, de_switch: Optional[float] = None):
+        self.grid = grid
+        self._dx = np.ascontiguousarray(grid.dx, np.float64)
+        self._nb = np.ascontiguousarray(grid.neighbor, np.int32)
+        self._rel = np.ascontiguousarray(grid.neighbor_rel, np.int8)
+        self._oct = np.ascontiguousarray(grid.octant, np.int8)
+        self._g = _Grid(grid.n, grid.gamma if gamma is None else gamma,
+                        grid.de_switch if de_switch is None else de_switch, flux_form,
+                        self._dx.ctypes.data, self._nb.ctypes.data, self._rel.ctypes.data, self._oct.ctypes.data)
+
+    def _check(self, U):
+        assert U.dtype == np.float64 and U.flags.c_contiguous and U.shape == (self.grid.n, NF, NP, NP, NP)
+
+    def fill_ghosts(self, U: np.ndarray) -> np.ndarray:
+        self._check(U)
+        lib().oracle_fill_ghosts(ctypes.byref(self._g), U.ctypes.data)
+        return U
+
+    def stage(self, Uin: np.ndarray, dt: float, U0: Optional[np.ndarray] = None, beta: float = 1.0,
+              Uout: Optional[np.ndarray] = None, ids=None, nthreads: int = 0,
+              sub_amax: Optional[np.ndarray] = None):
+        """One RK stage Uout = U0 + beta (U* - U0), U* = Uin + dt/dx dU; returns
+        (Uout, max_speed[2], status).  Uout defaults to a copy of Uin."""
+        self._check(Uin)
+        if Uout is None:
+            Uout = Uin.copy()
+        self._check(Uout)
+        if U0 is not None:
+            self._check(U0)
+        ms = np.zeros(2)
+        if ids is not None:
+            ids = np.ascontiguousarray(ids, np.int32)
+        st = lib().oracle_stage(ctypes.byref(self._g), None if ids is None else ids.ctypes.data,
+                                0 if ids is None else len(ids), Uin.ctypes.data,
+                                None if U0 is None else U0.ctypes.data, beta, dt, Uout.ctypes.data,
+                                _dptr(ms), None if sub_amax is None else sub_amax.ctypes.data, nthreads)
+        return Uout, ms, st
+
+    def rk3_step(self, U: np.ndarray, dt: float, nthreads: int = 0):
+        """One SSP-RK3 step from U (ghosts filled); returns (U_new with ghosts filled,
+        max_speed of the first stage, worst status)."""
+        st_all = 0
+        U1, ms, st = self.stage(U, dt, nthreads=nthreads)
+        st_all = min(st_all, st)
+        self.fill_ghosts(U1)
+        U2, _, st = self.stage(U1, dt, U0=U, beta=RK3_BETA[1], nthreads=nthreads)
+        st_all = min(st_all, st)
+        self.fill_ghosts(U2)
+        U3, _, st = self.stage(U2, dt, U0=U, beta=RK3_BETA[2], nthreads=nthreads)
+        st_all = min(st_all, st)
+        self.fill_ghosts(U3)
+        return U3, ms, st_all
+
+    def totals(self, U: np.ndarray) -> np.ndarray:
+        self._check(U)
+        t = np.zeros(NF)
+        lib().oracle_totals(ctypes.byref(self._g), U.ctypes.data, _dptr(t))
+        return t

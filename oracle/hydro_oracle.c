@@ -1,0 +1,350 @@
+/* hydro_oracle.c -- plain FP64 CPU oracle for the batched octree hydro step.
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the
+ * CPU-baseline leg of the benchmark; never by the CUDA library.
+ *
+ * The paper (Section IV-C) names the method: inviscid Euler equations solved
+ * with a finite-volume central scheme (Kurganov-Tadmor) on an octree of N^3
+ * sub-grids, N = 8; Section V-B.1 names the two GPU kernels it profiles: a PPM
+ * reconstruction kernel and a flux kernel, inside the Runge-Kutta sub-step
+ * driver compute_fluxes that also reduces the global time-step.  The paper
+ * prints no formulas, so each function below follows the published method the
+ * paper cites, step by step, in the order those methods state them:
+ *   - PPM face interpolant and limiter: Colella & Woodward (1984), eqs. 1.6-1.10;
+ *   - central-upwind flux: Kurganov, Noelle & Petrova (2001), with the central
+ *     Kurganov-Tadmor (2000) flux as the a+ = -a- special case;
+ *   - Shu-Osher SSP-RK3 stage blend U0 + beta (U* - U0), beta supplied by the
+ *     caller (alpha = 1 - beta; the form keeps a uniform state exactly);
+ *   - Neumaier compensated summation for the totals.
+ * Readings where the paper is silent are listed with the design notes.
+ *
+ * Build: -O2 -ffp-contract=off, no -ffast-math, optional -fopenmp.
+ */
+#include "hydro_oracle.h"
+
+#include <math.h>
+#include <stddef.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+enum { NX = 8, NG = 3, NP = 14, NF = 11, NFACE = 9 };
+enum { F_RHO = 0, F_SX = 1, F_EGAS = 4, F_TAU = 5 };
+
+static size_t at(int s, int f, int k, int j, int i) {
+  return ((((size_t)s * NF + f) * NP + k) * NP + j) * NP + i;
+}
+
+/* Cell (k,j,i) of the pencil along direction d at position m, transverse
+ * interior coordinates (t1, t2): x-pencils (t1,t2) = (j,k), y: (i,k), z: (i,j). */
+static size_t pencil_at(int s, int f, int d, int t1, int t2, int m) {
+  if (d == 0) return at(s, f, t2, t1, m);
+  if (d == 1) return at(s, f, t2, m, t1);
+  return at(s, f, m, t2, t1);
+}
+
+/* ------------------------------------------------------------------------- */
+/* PPM reconstruction (Colella & Woodward 1984)                               */
+/* ------------------------------------------------------------------------- */
+
+/* Monotonized-central limited slope of cell with neighbours qm, q0, qp:
+ * delta = (qp - qm)/2; limited to min(|delta|, 2|q0-qm|, 2|qp-q0|) with the
+ * sign of delta when q0 is not a local extremum, else zero (CW84 eq. 1.8). */
+static double limited_slope(double qm, double q0, double qp) {
+  double dl = q0 - qm;
+  double dr = qp - q0;
+  if (dl * dr <= 0.0) return 0.0;
+  double delta = 0.5 * (qp - qm);
+  double m = fabs(delta);
+  double l = 2.0 * fabs(dl);
+  double r = 2.0 * fabs(dr);
+  if (l < m) m = l;
+  if (r < m) m = r;
+  return delta > 0.0 ? m : -m;
+}
+
+void oracle_ppm_pencil(const double *q, double *aL, double *aR) {
+  double dm[NP];
+  double face[NP]; /* face[m] is the interpolant at face m + 1/2 */
+  for (int m = 1; m <= 12; ++m) dm[m] = limited_slope(q[m - 1], q[m], q[m + 1]);
+  /* CW84 eq. 1.6 with limited slopes: a_{m+1/2} = (q_m + q_{m+1})/2 - (dm_{m+1} - dm_m)/6 */
+  for (int m = 1; m <= 11; ++m) face[m] = 0.5 * (q[m] + q[m + 1]) - (dm[m + 1] - dm[m]) / 6.0;
+  for (int m = 2; m <= 11; ++m) {
+    double a = q[m];
+    double l = face[m - 1];
+    double r = face[m];
+    /* CW84 eq. 1.10: flatten at a local extremum, else pull the far face in so
+     * that the parabola has no interior extremum. */
+    if ((r - a) * (a - l) <= 0.0) {
+      l = a;
+      r = a;
+    } else {
+      double da = r - l;
+      double lhs = da * (a - 0.5 * (l + r));
+      double rhs = da * da / 6.0;
+      if (lhs > rhs)
+        l = 3.0 * a - 2.0 * r;
+      else if (-rhs > lhs)
+        r = 3.0 * a - 2.0 * l;
+    }
+    aL[m] = l;
+    aR[m] = r;
+  }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Face EOS and numerical flux                                                */
+/* ------------------------------------------------------------------------- */
+
+void oracle_face_eos(const double *U, int d, double gamma, double eta, double *u, double *p, double *c) {
+  double rho = U[F_RHO];
+  double sx = U[F_SX], sy = U[F_SX + 1], sz = U[F_SX + 2];
+  double E = U[F_EGAS];
+  *u = U[F_SX + d] / rho;
+  double ek = 0.5 * (sx * sx + sy * sy + sz * sz) / rho;
+  double ei = E - ek;
+  /* dual-energy switch: when the internal energy is a small fraction of the
+   * total, take it from the entropy tracer, e_i = tau^gamma */
+  if (eta > 0.0 && ei < eta * E) ei = pow(U[F_TAU], gamma);
+  *p = (gamma - 1.0) * ei;
+  *c = sqrt(gamma * *p / rho);
+}
+
+/* Physical flux along d: every field is carried with velocity u; the normal
+ * momentum adds p and the energy adds p*u. */
+static void physical_flux(const double *U, int d, double u, double p, double *F) {
+  for (int f = 0; f < NF; ++f) F[f] = U[f] * u;
+  F[F_SX + d] = U[F_SX + d] * u + p;
+  F[F_EGAS] = (U[F_EGAS] + p) * u;
+}
+
+double oracle_face_flux(const double *UL, const double *UR, int d, double gamma, double eta, int form,
+                        double *F) {
+  double uL, pL, cL, uR, pR, cR;
+  oracle_face_eos(UL, d, gamma, eta, &uL, &pL, &cL);
+  oracle_face_eos(UR, d, gamma, eta, &uR, &pR, &cR);
+  double ap, am;
+  if (form == 1) { /* Kurganov-Tadmor: one local speed a, a+ = a, a- = -a */
+    double a = fabs(uL) + cL;
+    double b = fabs(uR) + cR;
+    ap = a > b ? a : b;
+    am = -ap;
+  } else { /* Kurganov-Noelle-Petrova one-sided local speeds */
+    ap = uL + cL;
+    if (uR + cR > ap) ap = uR + cR;
+    if (0.0 > ap) ap = 0.0;
+    am = uL - cL;
+    if (uR - cR < am) am = uR - cR;
+    if (0.0 < am) am = 0.0;
+  }
+  double FL[NF], FR[NF];
+  physical_flux(UL, d, uL, pL, FL);
+  physical_flux(UR, d, uR, pR, FR);
+  double den = ap - am;
+  if (den > 1e-300) {
+    for (int f = 0; f < NF; ++f) F[f] = ((ap * FL[f] - am * FR[f]) + ap * am * (UR[f] - UL[f])) / den;
+  } else {
+    for (int f = 0; f < NF; ++f) F[f] = 0.5 * (FL[f] + FR[f]);
+  }
+  return ap > -am ? ap : -am;
+}
+
+/* ------------------------------------------------------------------------- */
+/* One RK stage on one sub-grid                                               */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+  double flux[3][NF][NX][NX][NFACE]; /* [d][f][t2][t1][face], face m+1/2 for m = 2..10 */
+} work_t;
+
+static int stage_subgrid(const oracle_grid *g, int s, const double *Uin, const double *U0, double beta,
+                         double dt, double *Uout, double *amax_s, work_t *w) {
+  double q[NF][NP], aL[NF][NP], aR[NF][NP];
+  double UL[NF], UR[NF], F[NF];
+  double amax = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    for (int t2 = NG; t2 < NG + NX; ++t2) {
+      for (int t1 = NG; t1 < NG + NX; ++t1) {
+        for (int f = 0; f < NF; ++f) {
+          for (int m = 0; m < NP; ++m) q[f][m] = Uin[pencil_at(s, f, d, t1, t2, m)];
+          oracle_ppm_pencil(q[f], aL[f], aR[f]);
+        }
+        for (int m = 2; m <= 10; ++m) {
+          for (int f = 0; f < NF; ++f) {
+            UL[f] = aR[f][m];     /* right edge of cell m */
+            UR[f] = aL[f][m + 1]; /* left edge of cell m+1 */
+          }
+          double a = oracle_face_flux(UL, UR, d, g->gamma, g->de_switch, g->flux_form, F);
+          if (a != a || a > amax) amax = a; /* a NaN speed sticks */
+          for (int f = 0; f < NF; ++f) w->flux[d][f][t2 - NG][t1 - NG][m - 2] = F[f];
+        }
+      }
+    }
+  }
+  *amax_s = amax;
+  double lam = dt / g->dx[s];
+  int bad = 0;
+  for (int k = NG; k < NG + NX; ++k) {
+    for (int j = NG; j < NG + NX; ++j) {
+      for (int i = NG; i < NG + NX; ++i) {
+        int ii = i - NG, jj = j - NG, kk = k - NG;
+        for (int f = 0; f < NF; ++f) {
+          /* cell i has faces i-1/2 (stored index i-3) and i+1/2 (index i-2) */
+          double fxl = w->flux[0][f][kk][jj][ii], fxh = w->flux[0][f][kk][jj][ii + 1];
+          double fyl = w->flux[1][f][kk][ii][jj], fyh = w->flux[1][f][kk][ii][jj + 1];
+          double fzl = w->flux[2][f][jj][ii][kk], fzh = w->flux[2][f][jj][ii][kk + 1];
+          double dU = ((fxl - fxh) + (fyl - fyh)) + (fzl - fzh);
+          size_t o = at(s, f, k, j, i);
+          double Us = Uin[o] + lam * dU;
+          double v = (beta == 1.0) ? Us : U0[o] + beta * (Us - U0[o]);
+          Uout[o] = v;
+          if (!isfinite(v) || (f == F_RHO && !(v > 0.0))) bad = 1;
+        }
+      }
+    }
+  }
+  return bad;
+}
+
+int oracle_stage(const oracle_grid *g, const int32_t *ids, int32_t n_ids, const double *Uin, const double *U0,
+                 double beta, double dt, double *Uout, double *max_speed, double *sub_amax, int nthreads) {
+  if (!g || !Uin || !Uout || !max_speed || n_ids < 0) return ORACLE_ERR_INVALID;
+  if (beta != 1.0 && !U0) return ORACLE_ERR_INVALID;
+  int n = ids ? n_ids : g->n;
+  double amax = 0.0, amax_dx = 0.0;
+  int bad = 0;
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel num_threads(nthreads) reduction(max : amax, amax_dx) reduction(| : bad)
+#endif
+  {
+    work_t *w = (work_t *)malloc(sizeof(work_t));
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 4)
+#endif
+    for (int t = 0; t < n; ++t) {
+      int s = ids ? ids[t] : t;
+      double a = 0.0;
+      bad |= stage_subgrid(g, s, Uin, U0, beta, dt, Uout, &a, w);
+      if (sub_amax) sub_amax[s] = a;
+      if (a != a) bad = 1;
+      if (a > amax) amax = a;
+      if (a / g->dx[s] > amax_dx) amax_dx = a / g->dx[s];
+    }
+    free(w);
+  }
+  (void)nthreads;
+  max_speed[0] = amax;
+  max_speed[1] = amax_dx;
+  return bad ? ORACLE_ERR_NONFINITE : ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Ghost fill                                                                 */
+/* ------------------------------------------------------------------------- */
+
+/* padded coordinate array p[3] = (i, j, k) */
+static size_t at3(int s, int f, const int *p) { return at(s, f, p[2], p[1], p[0]); }
+
+static const int T1[3] = {1, 0, 0}; /* first transverse axis of a face normal to axis a */
+static const int T2[3] = {2, 2, 1}; /* second transverse axis */
+
+static int floor_half(int v) { return v >= 0 ? v / 2 : -((-v + 1) / 2); }
+
+int oracle_fill_ghosts(const oracle_grid *g, double *U) {
+  for (int s = 0; s < g->n; ++s) {
+    for (int face = 0; face < 6; ++face) {
+      int a = face / 2, side = face % 2;
+      int b1 = T1[a], b2 = T2[a];
+      int rel = g->neighbor_rel[s * 6 + face];
+      const int32_t *nb = g->neighbor + ((size_t)s * 6 + face) * 4;
+      for (int f = 0; f < NF; ++f) {
+        for (int layer = 0; layer < NG; ++layer) {
+          /* interior coordinate of the ghost cell along a: -1,-2,-3 or 8,9,10 */
+          int ga = side ? NX + layer : -1 - layer;
+          for (int c2 = 0; c2 < NX; ++c2) {
+            for (int c1 = 0; c1 < NX; ++c1) {
+              int dst[3];
+              dst[a] = ga + NG;
+              dst[b1] = c1 + NG;
+              dst[b2] = c2 + NG;
+              double v;
+              if (nb[0] < 0) { /* outflow: nearest interior cell */
+                int src[3] = {dst[0], dst[1], dst[2]};
+                src[a] = side ? NG + NX - 1 : NG;
+                v = U[at3(s, f, src)];
+              } else if (rel == 0) { /* same level: the neighbour's interior cell */
+                int src[3] = {dst[0], dst[1], dst[2]};
+                src[a] = (side ? ga - NX : ga + NX) + NG;
+                v = U[at3(nb[0], f, src)];
+              } else if (rel < 0) {
+                /* coarser neighbour: value of the coarse cell that contains the
+                 * centre of the fine ghost cell.  In coarse-cell units relative
+                 * to the neighbour's interior origin, this sub-grid's origin is
+                 * at 8 (neighbour on the low side) or -4 (high side) along a,
+                 * and at 4*octant bit along each transverse axis. */
+                int oct = g->octant[s];
+                int src[3];
+                src[a] = (side ? -4 : 8) + floor_half(ga) + NG;
+                src[b1] = 4 * ((oct >> b1) & 1) + floor_half(c1) + NG;
+                src[b2] = 4 * ((oct >> b2) & 1) + floor_half(c2) + NG;
+                v = U[at3(nb[0], f, src)];
+              } else {
+                /* finer neighbours: mean of the 2x2x2 fine cells covering the
+                 * coarse ghost cell, summed in (k, j, i) order */
+                int q1 = c1 >> 2, q2 = c2 >> 2;
+                int fs = nb[q1 + 2 * q2];
+                int base[3];
+                base[a] = 2 * (side ? ga - NX : ga + 4);
+                base[b1] = 2 * (c1 - 4 * q1);
+                base[b2] = 2 * (c2 - 4 * q2);
+                double sum = 0.0;
+                for (int dk = 0; dk < 2; ++dk)
+                  for (int dj = 0; dj < 2; ++dj)
+                    for (int di = 0; di < 2; ++di) {
+                      int src[3] = {base[0] + di + NG, base[1] + dj + NG, base[2] + dk + NG};
+                      sum += U[at3(fs, f, src)];
+                    }
+                v = sum * 0.125;
+              }
+              U[at3(s, f, dst)] = v;
+            }
+          }
+        }
+      }
+    }
+  }
+  return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Totals                                                                     */
+/* ------------------------------------------------------------------------- */
+
+/* Neumaier's improved Kahan summation: add x to (sum, comp). */
+static void neumaier_add(double *sum, double *comp, double x) {
+  double t = *sum + x;
+  if (fabs(*sum) >= fabs(x))
+    *comp += (*sum - t) + x;
+  else
+    *comp += (x - t) + *sum;
+  *sum = t;
+}
+
+void oracle_totals(const oracle_grid *g, const double *U, double *totals) {
+  for (int f = 0; f < NF; ++f) {
+    double S = 0.0, C = 0.0;
+    for (int s = 0; s < g->n; ++s) {
+      double ss = 0.0, sc = 0.0;
+      for (int k = NG; k < NG + NX; ++k)
+        for (int j = NG; j < NG + NX; ++j)
+          for (int i = NG; i < NG + NX; ++i) neumaier_add(&ss, &sc, U[at(s, f, k, j, i)]);
+      double vol = g->dx[s] * g->dx[s] * g->dx[s];
+      neumaier_add(&S, &C, vol * ss);
+      neumaier_add(&S, &C, vol * sc);
+    }
+    totals[f] = S + C;
+  }
+}

@@ -1,0 +1,81 @@
+/* hydro_oracle.h -- plain FP64 CPU oracle for the batched octree hydro step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  It shares no code,
+ * header, table or constant with the CUDA library, and the CUDA library never
+ * calls it.
+ *
+ * What it computes (paper Section IV-C: inviscid Euler equations, finite-volume
+ * central scheme, octree of 8^3 sub-grids; Section V-B.1: PPM reconstruction
+ * kernel and flux kernel; Section V-B.1 compute_fluxes: one Runge-Kutta
+ * sub-step with a global time-step reduction; diagnostics: grid totals):
+ *
+ *   stage:  per sub-grid, per direction, PPM (Colella-Woodward) reconstruction
+ *           of the 11 conserved fields on the 9 faces of every pencil, face EOS
+ *           with dual-energy switch, central-upwind (Kurganov-Noelle-Petrova)
+ *           or central (Kurganov-Tadmor) flux, flux-divergence update and
+ *           Shu-Osher RK blend; the maximum signal speed over all faces.
+ *   ghosts: fill of the 6 face ghost slabs (3 layers) from neighbours: copy,
+ *           coarse-to-fine injection, fine-to-coarse 2x2x2 mean, outflow.
+ *   totals: Neumaier-compensated grid totals of the 11 fields.
+ *
+ * Layout: U[s][f][k][j][i], 14^3 padded cells per field, interior 3..10.
+ * Compile with -O2 -ffp-contract=off (no fused multiply-add, no fast-math).
+ */
+#ifndef HYDRO_ORACLE_H
+#define HYDRO_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  int32_t n;                   /* number of sub-grids */
+  double gamma;                /* ideal-gas adiabatic index */
+  double de_switch;            /* dual-energy eta; <= 0 disables the switch */
+  int32_t flux_form;           /* 0 central-upwind (KNP), 1 central (KT) */
+  const double *dx;            /* [n] cell width */
+  const int32_t *neighbor;     /* [n][6][4] face neighbours, see workloads */
+  const int8_t *neighbor_rel;  /* [n][6] level(neighbour) - level(self) */
+  const int8_t *octant;        /* [n] position in the parent: bit0 x, bit1 y, bit2 z */
+} oracle_grid;
+
+/* status codes */
+#define ORACLE_OK 0
+#define ORACLE_ERR_NONFINITE (-4)
+#define ORACLE_ERR_INVALID (-1)
+
+/* PPM on one pencil of 14 values: fills aL[m], aR[m] for m = 2..11. */
+void oracle_ppm_pencil(const double *q, double *aL, double *aR);
+
+/* Face EOS on one side: returns pressure p and sound speed c, velocity along d. */
+void oracle_face_eos(const double *U, int d, double gamma, double eta, double *u, double *p, double *c);
+
+/* Numerical flux F[11] through a face normal to d from the left/right states.
+ * Returns the face signal speed max(a+, -a-). */
+double oracle_face_flux(const double *UL, const double *UR, int d, double gamma, double eta, int form,
+                        double *F);
+
+/* One RK stage on the listed sub-grids (ids == NULL: all).  Writes only the
+ * interior of Uout for those sub-grids:
+ *   U* = Uin + (dt/dx) dU,   Uout = U0 + beta (U* - U0)   (Uout = U* if beta == 1)
+ * i.e. the Shu-Osher convex blend alpha U0 + beta U* with alpha = 1 - beta.
+ * U0 may be NULL when beta == 1.
+ * max_speed[0] = max amax_s, max_speed[1] = max amax_s/dx_s over the listed
+ * sub-grids; sub_amax (optional, [n]) receives amax_s.  nthreads <= 0 uses the
+ * OpenMP default.  Returns ORACLE_ERR_NONFINITE if an output is not finite or
+ * a density is not positive (outputs are still written). */
+int oracle_stage(const oracle_grid *g, const int32_t *ids, int32_t n_ids, const double *Uin, const double *U0,
+                 double beta, double dt, double *Uout, double *max_speed, double *sub_amax, int nthreads);
+
+/* Fill the six face ghost slabs of every sub-grid from the interiors. */
+int oracle_fill_ghosts(const oracle_grid *g, double *U);
+
+/* Grid totals T_f = sum_s dx_s^3 sum_cells U_f, Neumaier-compensated, fixed order. */
+void oracle_totals(const oracle_grid *g, const double *U, double *totals);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

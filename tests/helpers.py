@@ -1,0 +1,86 @@
+"""Shared test helpers: global<->sub-grid layout moves and a time-step driver.
+
+Only data movement and the lagged-CFL driver live here; no solver arithmetic.
+"""
+import math
+
+import numpy as np
+
+from paper_2210_06437_gb300 import workloads as W
+
+NX, NG, NP, NF = W.NX, W.NG, W.NP, W.NF
+
+
+def scatter(G, nb):
+    """Global array G[f][Z][Y][X] -> padded sub-grid state (x-fastest sub-grid ids), NaN ghosts."""
+    bx, by, bz = nb
+    U = W.empty_state(bx * by * bz)
+    for k in range(bz):
+        for j in range(by):
+            for i in range(bx):
+                s = (k * by + j) * bx + i
+                U[s, :, NG:NG + NX, NG:NG + NX, NG:NG + NX] = G[:, k * NX:(k + 1) * NX, j * NX:(j + 1) * NX,
+                                                              i * NX:(i + 1) * NX]
+    return U
+
+
+def gather(U, nb):
+    bx, by, bz = nb
+    G = np.empty((U.shape[1], bz * NX, by * NX, bx * NX))
+    for k in range(bz):
+        for j in range(by):
+            for i in range(bx):
+                s = (k * by + j) * bx + i
+                G[:, k * NX:(k + 1) * NX, j * NX:(j + 1) * NX, i * NX:(i + 1) * NX] = U[s, :, NG:NG + NX, NG:NG + NX,
+                                                                                      NG:NG + NX]
+    return G
+
+
+def prim_to_global(rho, vx, vy, vz, p, X=None, gamma=W.GAMMA):
+    X = X if X is not None else [np.zeros_like(rho)] * 5
+    return np.stack(W.conserved_from_primitive(rho, vx, vy, vz, p, X, gamma))
+
+
+def random_smooth_global(shape, seed, amp=0.2, vamp=0.3):
+    """Random smooth periodic primitive state on a global grid of shape (Z, Y, X)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    Z, Y, X = shape
+    z, y, x = np.meshgrid(np.arange(Z) / Z, np.arange(Y) / Y, np.arange(X) / X, indexing="ij")
+
+    def smooth():
+        a = rng.uniform(-1, 1, 6)
+        return (np.sin(2 * np.pi * (x + a[0])) * np.cos(2 * np.pi * (y + a[1])) +
+                np.sin(2 * np.pi * (z + a[2])) * np.cos(2 * np.pi * (x + a[3])) +
+                0.5 * np.sin(4 * np.pi * (y + a[4]) + 2 * np.pi * z * a[5]))
+    rho = 1.0 + amp * smooth()
+    p = 1.0 + amp * smooth()
+    v = [vamp * smooth() for _ in range(3)]
+    Xs = [0.5 + 0.3 * smooth() / 2.5 for _ in range(5)]
+    return prim_to_global(rho, v[0], v[1], v[2], p, Xs)
+
+
+def advance(o, U, t_end, cfl, max_steps=100000):
+    """Lagged-CFL SSP-RK3 driver on the oracle: the first dt from a dry stage on the
+    initial state, later ones from stage 1 of the previous step; the last step is cut
+    to land on t_end.  Returns (U, t, steps)."""
+    o.fill_ghosts(U)
+    _, ms, st = o.stage(U, 0.0)
+    assert st == 0
+    t, n = 0.0, 0
+    while t < t_end - 1e-15 and n < max_steps:
+        dt = min(cfl / ms[1], t_end - t)
+        U, ms, st = o.rk3_step(U, dt)
+        assert st == 0
+        t += dt
+        n += 1
+    return U, t, n
+
+
+def exact_total(grid, U, f):
+    """Correctly rounded sum of dx^3 * U_f over all interior cells (math.fsum)."""
+    terms = (U[:, f, NG:NG + NX, NG:NG + NX, NG:NG + NX] * (grid.dx ** 3)[:, None, None, None]).ravel()
+    return math.fsum(terms.tolist()), math.fsum(np.abs(terms).tolist())
+
+
+def quasi_1d_grid(nx_sub, dx, periodic_x):
+    return W.uniform_grid((nx_sub, 1, 1), (0.0, 0.0, 0.0), dx, periodic=(periodic_x, True, True))
