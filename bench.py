@@ -1,0 +1,380 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched octree hydro step on GB300.
+
+One step = one SSP-RK3 time step of the whole hot path over the workload:
+three RK stages (PPM reconstruction, central-upwind flux, maximum-speed
+reduction, flux-divergence update) with a ghost fill after each stage, the
+time step chosen on the device from the previous step's CFL speed, and the
+conservation totals.  The metric is interior cell-updates per second
+(cells x 3 stages / step time).
+
+Workload (default): the largest configuration, a 65536-leaf octree of 8^3
+sub-grids (33.5 M interior cells, two n=1.5 polytropes, 656 Zipf batches).
+The headline value is the mixed FP32/FP64 path; the all-FP64 path is measured
+on the same input and reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 (under torchrun) runs N independent replicas, one per GPU, and reports
+the aggregate; the reference arm times the CPU oracle on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "hydro cell-updates/s (FP64 vs FP32/FP64-mixed batched) at stated error; % HBM roofline"
+BYTES_PER_CELL_STAGE = 374.0     # read interior + 6 face slabs (1664 cells) + write interior (512), 88 B per cell
+FLOPS_PER_CELL_STAGE = 2200.0    # algorithmic operation count per cell-update of one stage
+GHOST_BYTES_PER_CELL = 396.0     # ghost fill: read + write 1152 face-slab cells per 512 interior cells
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 2 FP64 FMA/clk/SM at the 2070 MHz maximum clock
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--config", type=int, default=5, help="workload configuration 1..5")
+    p.add_argument("--skip-e2e", action="store_true")
+    p.add_argument("--skip-fp64", action="store_true")
+    p.add_argument("--skip-cpu", action="store_true")
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower().startswith("active")})
+        busy = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": float(np.median(busy)) if busy else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+def dist_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_rate(w, U, out, target_s=10.0, seed=0):
+    """Oracle cell-updates/s of one RK stage on a bounded random sample of the
+    workload's sub-grids (all host threads); the sample grows until one stage
+    takes at least target_s.  `out` receives only the sampled interiors."""
+    import oracle
+    o = oracle.Oracle(w.grid)
+    rng = np.random.default_rng(seed)
+    n = 32
+    while True:
+        ids = np.sort(rng.choice(w.grid.n, min(n, w.grid.n), replace=False)).astype(np.int32)
+        t0 = time.perf_counter()
+        o.stage(U, 1e-6, Uout=out, ids=ids)
+        t = time.perf_counter() - t0
+        if t >= target_s or n >= w.grid.n:
+            break
+        n = min(w.grid.n, int(n * max(2.0, min(8.0, target_s / max(t, 1e-3)))))
+    return len(ids) * 512 / t, len(ids), t
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2210_06437_gb300 import workloads as W
+    oracle.build()
+    w = W.config(args.config)
+    U = w.state()
+    o = oracle.Oracle(w.grid)
+    o.fill_ghosts(U)
+    # bounded sample: each "step" is three oracle stages on the same sampled sub-grids
+    out = np.empty_like(U)
+    rate, nsamp, t1 = oracle_rate(w, U, out, target_s=3.0)
+    ids = np.sort(np.random.default_rng(1).choice(w.grid.n, nsamp, replace=False)).astype(np.int32)
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        for beta in (1.0, 0.25, 2.0 / 3.0):
+            o.stage(U, 1e-6, U0=U, beta=beta, Uout=out, ids=ids)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+    tstep = float(np.mean(times))
+    value = nsamp * 512 * 3 / tstep
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tstep * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "subgrids": w.grid.n, "cells": w.cells},
+            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+                             "sample": "3 oracle RK stages per step on %d of %d sub-grids of %s, OpenMP over "
+                                       "sub-grids" % (nsamp, w.grid.n, w.name)},
+            "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    rank, world, local = dist_info()
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        pg = dist
+    else:
+        torch.cuda.set_device(0)
+    from paper_2210_06437_gb300 import build, hydro as HY
+    from paper_2210_06437_gb300 import workloads as W
+    if rank == 0 or world == 1:
+        build.build()
+    if pg:
+        pg.barrier()
+    build.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    w = W.config(args.config)
+    U_host = w.state()
+    cells = w.cells
+    hbm, hbm_src = peaks()
+
+    def barrier():
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if not pg:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        return float(t.item())
+
+    U = torch.from_numpy(U_host).to(dev)
+    s1, s2 = torch.empty_like(U), torch.empty_like(U)
+    ids = torch.as_tensor(w.batches.ids, device=dev)
+    offs = w.batches.offsets
+    stream = torch.cuda.current_stream()
+    results = {}
+
+    def run_precision(prec, sampler):
+        g = HY.HydroGrid(w.grid, precision=prec)
+        U.copy_(torch.from_numpy(U_host))
+        g.fill_ghosts(U)
+        ms = torch.zeros(2, dtype=torch.float64, device=dev)
+        g.step(U, 0.0, U_out=s1, ids=ids, batch_offsets=offs, max_speed=ms)   # dry stage: first CFL speed
+        tot = torch.empty(11, dtype=torch.float64, device=dev)
+
+        def one_step():
+            g.rk3_step_cfl(U, 0.4, s1, s2, ms, ids=ids, batch_offsets=offs)
+            g.totals(U, out=tot)
+
+        for _ in range(args.warmup):
+            one_step()
+        g.sync()
+        barrier()
+        if sampler:
+            sampler.start()
+        l0 = g.launches
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            one_step()
+        e1.record(stream)
+        barrier()
+        clocks = sampler.stop() if sampler else None
+        launches = g.launches - l0
+        g.sync()
+        t_step = max_over_ranks(e0.elapsed_time(e1) / 1e3 / args.steps)
+        # per-kernel timing for the roofline: stage (beta = 1), ghost fill, totals
+        reps = 3
+
+        def timed(fn):
+            fn()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / 1e3 / reps
+
+        t_stage = timed(lambda: g.step(U, 1e-9, U_out=s1, ids=ids, batch_offsets=offs, max_speed=s2[0, 0, 0, 0, :2]))
+        t_ghost = timed(lambda: g.fill_ghosts(s1))
+        t_tot = timed(lambda: g.totals(U, out=tot))
+        g.sync()
+        g.close()
+        return dict(t_step=t_step, clocks=clocks, launches=launches, t_stage=t_stage, t_ghost=t_ghost, t_tot=t_tot,
+                    totals=tot.cpu().numpy())
+
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    smi_index = vis.split(",")[local] if vis and len(vis.split(",")) > local else str(local)
+    results["mixed"] = run_precision("mixed", ClockSampler(smi_index) if rank == 0 else None)
+    if not args.skip_fp64:
+        results["fp64"] = run_precision("fp64", None)
+
+    # end-to-end through the public API with host buffers (mixed path)
+    e2e = None
+    if not args.skip_e2e:
+        g = HY.HydroGrid(w.grid, precision="mixed")
+        Uh = torch.empty(U.shape, dtype=torch.float64, pin_memory=True)
+        Uh.copy_(torch.from_numpy(U_host))
+        g.fill_ghosts(U)
+        ms = torch.zeros(2, dtype=torch.float64, device=dev)
+        tot = torch.empty(11, dtype=torch.float64, device=dev)
+        toth = torch.empty(11, dtype=torch.float64, pin_memory=True)
+        U.copy_(Uh)
+        g.fill_ghosts(U)
+        Uh.copy_(U)
+        g.step(U, 0.0, U_out=s1, ids=ids, batch_offsets=offs, max_speed=ms)
+
+        def e2e_step():
+            U.copy_(Uh, non_blocking=True)
+            g.rk3_step_cfl(U, 0.4, s1, s2, ms, ids=ids, batch_offsets=offs)
+            g.totals(U, out=tot)
+            Uh.copy_(U, non_blocking=True)
+            toth.copy_(tot, non_blocking=True)
+
+        for _ in range(max(1, min(args.warmup, 2))):
+            e2e_step()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        barrier()
+        g.sync()
+        t_e2e = max_over_ranks(e0.elapsed_time(e1) / 1e3 / args.steps)
+        nbytes = U.numel() * 8
+        e2e = {"value": cells * 3 * world / t_e2e, "unit": "cell-updates/s", "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes + 88, "ms_per_step": t_e2e * 1e3,
+               "api": "HydroGrid.rk3_step_cfl + totals on a pinned host state copied in and out every step"}
+        g.close()
+        del Uh
+
+    # CPU oracle baseline on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if not args.skip_cpu and rank == 0 and world == 1:
+        import oracle
+        oracle.build()
+        Uc = U_host
+        oracle.Oracle(w.grid).fill_ghosts(Uc)
+        rate, nsamp, t = oracle_rate(w, Uc, np.empty_like(Uc), target_s=10.0)
+        cpu = {"value": rate, "unit": "cell-updates/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "one oracle RK stage on %d randomly sampled of %d sub-grids of %s (%.1f s, OpenMP over "
+                         "sub-grids, all host threads)" % (nsamp, w.grid.n, w.name, t)}
+
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return 0
+    r = results["mixed"]
+    value = cells * 3 * world / r["t_step"]
+    t_st = r["t_stage"]
+    ach = BYTES_PER_CELL_STAGE * cells / t_st / 1e9
+    roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+            "kernel": "stage_kernel<float> (mixed RK stage, beta = 1)", "peak_source": hbm_src,
+            "bytes_per_cell_update": BYTES_PER_CELL_STAGE, "launch_ms": t_st * 1e3}
+    kernels = {
+        "stage_mixed_ms": t_st * 1e3, "ghost_fill_ms": r["t_ghost"] * 1e3, "totals_ms": r["t_tot"] * 1e3,
+        "ghost_fill_gbs": GHOST_BYTES_PER_CELL * cells / r["t_ghost"] / 1e9,
+        "stage_share_of_step": 3 * t_st / r["t_step"], "ghost_share_of_step": 3 * r["t_ghost"] / r["t_step"]}
+    line = {"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["t_step"] * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "%s (config %d): %s" % (w.name, w.index, w.description), "subgrids": w.grid.n,
+                       "cells": cells, "batches": len(offs) - 1, "precision": "mixed",
+                       "step": "SSP-RK3 (3 stages + 3 ghost fills) + totals, device-side CFL dt",
+                       "l2": "inputs larger than L2 (%.1f GB state)" % (U.numel() * 8 / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": r["launches"], "clocks": r["clocks"]}
+    if "fp64" in results:
+        f = results["fp64"]
+        fl = FLOPS_PER_CELL_STAGE * cells / f["t_stage"] / 1e12
+        line["fp64"] = {"value": cells * 3 * world / f["t_step"], "ms_per_step": f["t_step"] * 1e3,
+                        "roofline": {"bound": "alu", "achieved": fl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                     "frac": fl / FP64_PEAK_TFLOPS, "traffic": None,
+                                     "kernel": "stage_kernel<double>", "launch_ms": f["t_stage"] * 1e3,
+                                     "hbm_frac": BYTES_PER_CELL_STAGE * cells / f["t_stage"] / 1e9 / hbm},
+                        "gpu_launches": f["launches"]}
+        line["mixed_speedup_vs_fp64"] = f["t_step"] / r["t_step"]
+    print(json.dumps(line))
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,192 @@
+/* hydro.h -- C ABI of the batched octree hydro step for GB300 (sm_103a).
+ *
+ * The library advances the inviscid Euler equations of an ideal gas on many
+ * 8^3 sub-grids of an octree with a finite-volume central scheme: PPM
+ * reconstruction of the conserved fields on the cell faces, a central-upwind
+ * (Kurganov-Tadmor-type) flux with a maximum-signal-speed reduction, and the
+ * flux-divergence update inside a Runge-Kutta sub-step.  This is the hydro
+ * solver the paper profiles: Section IV-C names the equations (inviscid Euler,
+ * solved by a finite-volume central scheme) and the octree of N^3 sub-grids
+ * with N = 8; Section V-B.1 names the reconstruct (PPM) and flux CUDA kernels
+ * and the compute_fluxes task, which drives one Runge-Kutta substep, reduces
+ * the global time-step and updates the hydrodynamic variables, and the
+ * diagnostics task that forms grid totals; Section VI covers the hydro
+ * ghost-cell exchange.
+ *
+ * Data layout (all state arrays are caller-owned DEVICE memory, float64):
+ *   U[s][f][k][j][i], s < n_subgrids, f < 11, k, j, i < 14 (x fastest);
+ *   each sub-grid is an 8^3 interior (indices 3..10) padded by 3 ghost layers.
+ *   Fields: 0 rho, 1 sx, 2 sy, 3 sz (momentum density), 4 egas (total energy
+ *   density), 5 tau (entropy tracer, e_int = tau^gamma), 6..10 rho*X_k.
+ *   Base pointers must be 16-byte aligned.
+ *
+ * Calls are stream-ordered and asynchronous.  Host-detectable errors (null
+ * pointers, bad sizes or values) are returned at once and nothing is
+ * launched.  Errors found on the device (a non-finite output or a density that
+ * is not positive, a sub-grid id out of range) set a device error word that
+ * the next hydro_sync() returns and clears.  No call aborts the process or
+ * traps the GPU.
+ */
+#ifndef GB300_HYDRO_H
+#define GB300_HYDRO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HYDRO_OK = 0,
+  HYDRO_ERR_INVALID = -1,   /* bad argument (host) or bad sub-grid id (device) */
+  HYDRO_ERR_CUDA = -2,      /* a CUDA runtime call failed; see hydro_last_error */
+  HYDRO_ERR_NOMEM = -3,     /* device or host allocation failed in hydro_create */
+  HYDRO_ERR_NONFINITE = -4, /* an updated value is not finite, or a density <= 0 */
+  HYDRO_ERR_TIMEOUT = -5,   /* reserved: a bounded device wait gave up */
+  HYDRO_ERR_STATE = -6      /* call not valid in the handle's current state */
+} hydro_status;
+
+typedef enum {
+  HYDRO_FP64 = 0,  /* every step of the path in float64 */
+  HYDRO_MIXED = 1  /* reconstruction and flux in float32; accumulation of the
+                      conserved variables, the speed reduction and totals in
+                      float64-accurate arithmetic */
+} hydro_precision;
+
+typedef enum {
+  HYDRO_FLUX_KNP = 0, /* central-upwind, one-sided speeds a+ >= 0 >= a- */
+  HYDRO_FLUX_KT = 1   /* central Kurganov-Tadmor, a+ = -a- = max |u| + c */
+} hydro_flux_form;
+
+/* Grid descriptor.  All arrays are HOST memory, read and copied to the device
+ * by hydro_create (the caller may free them afterwards).
+ *   neighbor[s][face][q], faces ordered -x,+x,-y,+y,-z,+z:
+ *     neighbor_rel == 0 : q = 0 is the same-level neighbour (periodic wrap is
+ *                         expressed here), or -1 for a domain boundary, which
+ *                         is filled as outflow (copy of the nearest interior
+ *                         cell);
+ *     neighbor_rel == -1: q = 0 is the one-level-coarser neighbour; octant[s]
+ *                         gives this sub-grid's position in its parent (bit0 x,
+ *                         bit1 y, bit2 z);
+ *     neighbor_rel == +1: q = t1 + 2*t2 are the four one-level-finer
+ *                         neighbours across the face, t1/t2 their offsets
+ *                         along the first/second transverse axis (x-face: y,z;
+ *                         y-face: x,z; z-face: x,y).
+ * The octree must be 2:1 balanced across faces. */
+typedef struct {
+  int32_t n_subgrids;          /* >= 1 */
+  int32_t n_fields;            /* must be 11 */
+  int32_t nx;                  /* interior cells per edge, must be 8 */
+  int32_t ghost;               /* ghost layers, must be 3 */
+  double gamma;                /* adiabatic index, > 1 (5/3 in the workloads) */
+  double de_switch;            /* dual-energy switch eta in [0, 1); 0 disables */
+  int32_t precision;           /* hydro_precision */
+  int32_t flux_form;           /* hydro_flux_form */
+  const double *dx;            /* [n_subgrids] cell width, > 0 */
+  const int32_t *neighbor;     /* [n_subgrids][6][4] */
+  const int8_t *neighbor_rel;  /* [n_subgrids][6], values -1, 0, +1 */
+  const int8_t *octant;        /* [n_subgrids], 0..7 */
+} hydro_grid_desc;
+
+/* A list of sub-grids to advance, cut into batches (the uneven leaf batches of
+ * the octree).  All batches of one call are processed by one persistent
+ * launch that pulls sub-grids from a device work queue. */
+typedef struct {
+  const int32_t *subgrid_ids;   /* DEVICE [n_items], ids in [0, n_subgrids), unique */
+  int32_t n_items;              /* >= 0 */
+  const int32_t *batch_offsets; /* HOST [n_batches + 1], non-decreasing, 0 .. n_items;
+                                   may be NULL (one batch) */
+  int32_t n_batches;            /* >= 0 */
+} hydro_batch;
+
+typedef struct hydro_handle hydro_handle;
+
+/* Create a handle for one grid on the current CUDA device: validates and
+ * copies the descriptor, allocates the handle's device scratch (work-queue
+ * counter, error word, reduction partials).  Returns HYDRO_OK and *out, or an
+ * error with *out = NULL. */
+int hydro_create(const hydro_grid_desc *desc, hydro_handle **out);
+
+/* One Runge-Kutta stage on the batch (Section V-B.1: reconstruct, flux,
+ * global speed reduction, update), for each listed sub-grid s:
+ *   U* = U_in + (dt/dx_s) * dU,
+ *   dU = ((Fx(i-1/2) - Fx(i+1/2)) + (Fy(j-1/2) - Fy(j+1/2))) + (Fz(k-1/2) - Fz(k+1/2)),
+ *   U_out = U0 + beta * (U* - U0)      (U_out = U* when beta == 1),
+ * which is the Shu-Osher blend (1 - beta) U0 + beta U*.  SSP-RK3 uses
+ * beta = 1, 1/4, 2/3 with U0 the state at the start of the step.
+ *   U_in   DEVICE padded state; its face ghost slabs must be filled (edge and
+ *          corner ghost cells are never read);
+ *   U0     DEVICE padded state, read at interior cells; may be NULL iff beta == 1;
+ *   U_out  DEVICE padded state; only the interiors of the listed sub-grids are
+ *          written; must not alias U_in; may alias U0;
+ *   dt     >= 0 and finite; beta in (0, 1];
+ *   d_max_speed  DEVICE double[2], overwritten with the maximum over the
+ *          listed sub-grids and their faces of max(a+, -a-) (the CFL signal
+ *          speed of the INPUT state) and of that speed divided by dx_s;
+ *   stream cudaStream_t (NULL = legacy default stream). */
+int hydro_step(hydro_handle *h, const hydro_batch *batch, const double *U_in, const double *U0, double beta,
+               double dt, double *U_out, double *d_max_speed, void *stream);
+
+/* Fill the six face ghost slabs (3 layers each) of every sub-grid of U from
+ * the neighbours' interiors (Section VI: hydro boundary exchange): copy from a
+ * same-level neighbour; coarse neighbour: value of the coarse cell containing
+ * the ghost-cell centre; fine neighbours: mean of the 2x2x2 fine cells, summed
+ * in (k, j, i) order and scaled by 1/8; domain boundary: copy of the nearest
+ * interior cell.  Edge and corner ghost cells are left untouched. */
+int hydro_fill_ghosts(hydro_handle *h, double *U, void *stream);
+
+/* One SSP-RK3 step (three stages, Section I: three hydro iterations per
+ * time-step) with ghost fills between stages, replayed from a CUDA graph that
+ * the handle captures on first use for each (batch, U, scratch) combination.
+ *   U        DEVICE padded state with filled ghosts; overwritten by the new
+ *            state, ghosts filled;
+ *   scratch1, scratch2  DEVICE padded states of the same size (contents
+ *            destroyed);
+ *   d_max_speed DEVICE double[2]: the max speeds of the first stage, i.e. of
+ *            the state at the start of the step. */
+int hydro_rk3_step(hydro_handle *h, const hydro_batch *batch, double *U, double *scratch1, double *scratch2,
+                   double dt, double *d_max_speed, void *stream);
+
+/* As hydro_rk3_step, with the time step chosen on the device from the CFL
+ * condition (the paper's global time-step reduction, Section V-B.1):
+ *   dt = cfl / d_max_speed[1]
+ * where d_max_speed holds, on entry, the speeds of the previous step's first
+ * stage (or of a dry hydro_step with dt = 0 before the first step); on exit it
+ * holds this step's first-stage speeds, so successive calls chain without a
+ * host round trip.  If d_dt_out is not NULL the dt used is written there
+ * (DEVICE double).  cfl in (0, 1]. */
+int hydro_rk3_step_cfl(hydro_handle *h, const hydro_batch *batch, double *U, double *scratch1, double *scratch2,
+                       double cfl, double *d_max_speed, double *d_dt_out, void *stream);
+
+/* Grid totals (diagnostics): d_totals[f] = sum_s dx_s^3 * sum_interior U_f,
+ * compensated and in a fixed order, so the result is deterministic.
+ *   U DEVICE padded state; d_totals DEVICE double[11]. */
+int hydro_totals(hydro_handle *h, const double *U, double *d_totals, void *stream);
+
+/* Wait for the handle's work on the stream of its last call, then return and
+ * clear the device error word: HYDRO_OK, HYDRO_ERR_NONFINITE or
+ * HYDRO_ERR_INVALID (bad sub-grid id), or HYDRO_ERR_CUDA. */
+int hydro_sync(hydro_handle *h);
+
+/* Text of the last error on this handle (static storage of the handle). */
+const char *hydro_last_error(const hydro_handle *h);
+
+/* Number of kernel launches issued by this handle so far (instrumentation). */
+int64_t hydro_launch_count(const hydro_handle *h);
+
+/* Set a tuning parameter (see hydro_param); returns HYDRO_ERR_INVALID for an
+ * unknown key or value out of range. */
+int hydro_set_param(hydro_handle *h, int32_t key, int32_t value);
+
+typedef enum {
+  HYDRO_PARAM_STAGE_CTAS_PER_SM = 0, /* persistent CTAs per SM for the stage kernel, 1..8 (0 = auto) */
+  HYDRO_PARAM_GHOST_THREADS = 1      /* threads per CTA of the ghost-fill kernel, 64..1024 */
+} hydro_param;
+
+/* Release the handle and its device scratch (waits for its work first). */
+void hydro_destroy(hydro_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

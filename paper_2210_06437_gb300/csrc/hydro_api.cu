@@ -1,0 +1,425 @@
+// hydro_api.cu -- the C ABI declared in include/hydro.h.
+//
+// Host side: validates every argument before anything is launched, owns the
+// device copy of the grid descriptor and the handle's scratch (work-queue
+// counters, error word, totals partials, per-stage speed scratch), sizes the
+// persistent stage launch from the occupancy of the kernel, and replays a full
+// SSP-RK3 step from a CUDA graph captured once per (batch, buffers) set.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "hydro.h"
+#include "hydro_internal.cuh"
+
+using namespace hydro;
+
+namespace {
+
+struct GraphEntry {
+  const int32_t* ids;
+  int32_t n_items;
+  double* U;
+  double* s1;
+  double* s2;
+  double* dms;
+  cudaGraphExec_t exec;
+  int kernels;
+};
+
+}  // namespace
+
+struct hydro_handle {
+  int n = 0;
+  int precision = 0;
+  int form = 0;
+  double gamma = 5.0 / 3.0;
+  double eta = 1e-3;
+  int device = 0;
+  int sm_count = 0;
+  int ctas_per_sm = 0;
+  int occupancy = 1;  // resident stage CTAs per SM for this precision
+  int ghost_threads = 256;
+  double* d_dx = nullptr;
+  int32_t* d_nb = nullptr;
+  int8_t* d_rel = nullptr;
+  int8_t* d_oct = nullptr;
+  unsigned int* d_queue = nullptr;     // [4] work-queue counters
+  int* d_err = nullptr;                // device error word
+  double* d_partial = nullptr;         // [n][11][2] totals partials
+  double* d_dt = nullptr;              // [1] time step read by graph replays
+  unsigned long long* d_ms_tmp = nullptr;  // [2] speeds of RK stages 2 and 3
+  cudaStream_t cap_stream = nullptr;
+  cudaStream_t last_stream = nullptr;
+  int64_t launches = 0;
+  std::vector<GraphEntry> graphs;
+  char msg[512] = {0};
+};
+
+namespace {
+
+int fail(hydro_handle* h, int code, const char* fmt, ...) {
+  if (h) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(h->msg, sizeof(h->msg), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+int cuda_fail(hydro_handle* h, cudaError_t e, const char* what) {
+  return fail(h, HYDRO_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(h, expr)                                   \
+  do {                                                      \
+    cudaError_t e_ = (expr);                                \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #expr);  \
+  } while (0)
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+void free_all(hydro_handle* h) {
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
+  cudaFree(h->d_dx);
+  cudaFree(h->d_nb);
+  cudaFree(h->d_rel);
+  cudaFree(h->d_oct);
+  cudaFree(h->d_queue);
+  cudaFree(h->d_err);
+  cudaFree(h->d_partial);
+  cudaFree(h->d_dt);
+  cudaFree(h->d_ms_tmp);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+}
+
+__global__ void set_scalar(double* p, double v) { *p = v; }
+
+// dt = cfl / max(a/dx) of the previous first stage; a zero or non-finite speed
+// gives dt = 0 (no motion) rather than an infinite step.
+__global__ void cfl_dt(double* dt, const double* max_speed, double cfl, double* dt_out) {
+  const double m = max_speed[1];
+  const double v = (m > 0.0 && m <= 1.7976931348623157e308) ? cfl / m : 0.0;
+  *dt = v;
+  if (dt_out) *dt_out = v;
+}
+
+int check_batch(hydro_handle* h, const hydro_batch* b) {
+  if (!b) return fail(h, HYDRO_ERR_INVALID, "batch is NULL");
+  if (b->n_items < 0) return fail(h, HYDRO_ERR_INVALID, "batch n_items < 0");
+  if (b->n_items > 0 && !b->subgrid_ids) return fail(h, HYDRO_ERR_INVALID, "batch subgrid_ids is NULL");
+  if (b->batch_offsets) {
+    if (b->n_batches < 1) return fail(h, HYDRO_ERR_INVALID, "batch_offsets given with n_batches < 1");
+    if (b->batch_offsets[0] != 0 || b->batch_offsets[b->n_batches] != b->n_items)
+      return fail(h, HYDRO_ERR_INVALID, "batch_offsets must run from 0 to n_items");
+    for (int i = 0; i < b->n_batches; ++i)
+      if (b->batch_offsets[i + 1] < b->batch_offsets[i])
+        return fail(h, HYDRO_ERR_INVALID, "batch_offsets decrease at %d", i);
+  } else if (b->n_batches < 0) {
+    return fail(h, HYDRO_ERR_INVALID, "n_batches < 0");
+  }
+  return HYDRO_OK;
+}
+
+int stage_grid(hydro_handle* h, int n_items) {
+  int per_sm = h->ctas_per_sm > 0 ? h->ctas_per_sm : h->occupancy;
+  int grid = h->sm_count * per_sm;
+  return n_items < grid ? (n_items > 0 ? n_items : 1) : grid;
+}
+
+// Enqueue one stage (no validation).  queue_slot selects the counter.
+int enqueue_stage(hydro_handle* h, const int32_t* ids, int n_items, const double* Uin, const double* U0,
+                  double beta, double dt, const double* dt_dev, double* Uout, unsigned long long* ms, int queue_slot,
+                  cudaStream_t st) {
+  CUDA_TRY(h, cudaMemsetAsync(ms, 0, 2 * sizeof(unsigned long long), st));
+  if (n_items == 0) return HYDRO_OK;
+  CUDA_TRY(h, cudaMemsetAsync(h->d_queue + queue_slot, 0, sizeof(unsigned int), st));
+  StageArgs a;
+  a.Uin = Uin;
+  a.U0 = U0;
+  a.Uout = Uout;
+  a.ids = ids;
+  a.n_items = n_items;
+  a.n_sub = h->n;
+  a.dx = h->d_dx;
+  a.beta = beta;
+  a.dt = dt;
+  a.dt_dev = dt_dev;
+  a.gamma = h->gamma;
+  a.eta = h->eta;
+  a.form = h->form;
+  a.queue = h->d_queue + queue_slot;
+  a.err = h->d_err;
+  a.max_speed = ms;
+  const int grid = stage_grid(h, n_items);
+  cudaError_t e = h->precision == HYDRO_MIXED ? launch_stage_mixed(a, grid, st) : launch_stage_fp64(a, grid, st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "stage kernel launch");
+  h->launches += 1;
+  return HYDRO_OK;
+}
+
+int enqueue_ghosts(hydro_handle* h, double* U, cudaStream_t st) {
+  GhostArgs g;
+  g.U = U;
+  g.n_sub = h->n;
+  g.nb = h->d_nb;
+  g.rel = h->d_rel;
+  g.oct = h->d_oct;
+  cudaError_t e = launch_ghost_fill(g, h->ghost_threads, st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "ghost kernel launch");
+  h->launches += 1;
+  return HYDRO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hydro_create(const hydro_grid_desc* d, hydro_handle** out) {
+  if (!out) return HYDRO_ERR_INVALID;
+  *out = nullptr;
+  if (!d) return HYDRO_ERR_INVALID;
+  if (d->n_subgrids < 1 || d->n_fields != NF || d->nx != NX || d->ghost != NG) return HYDRO_ERR_INVALID;
+  if (!(d->gamma > 1.0) || !std::isfinite(d->gamma)) return HYDRO_ERR_INVALID;
+  if (!(d->de_switch >= 0.0 && d->de_switch < 1.0)) return HYDRO_ERR_INVALID;
+  if (d->precision != HYDRO_FP64 && d->precision != HYDRO_MIXED) return HYDRO_ERR_INVALID;
+  if (d->flux_form != HYDRO_FLUX_KNP && d->flux_form != HYDRO_FLUX_KT) return HYDRO_ERR_INVALID;
+  if (!d->dx || !d->neighbor || !d->neighbor_rel || !d->octant) return HYDRO_ERR_INVALID;
+  const int n = d->n_subgrids;
+  for (int s = 0; s < n; ++s) {
+    if (!(d->dx[s] > 0.0) || !std::isfinite(d->dx[s])) return HYDRO_ERR_INVALID;
+    if (d->octant[s] < 0 || d->octant[s] > 7) return HYDRO_ERR_INVALID;
+    for (int f = 0; f < 6; ++f) {
+      const int rel = d->neighbor_rel[s * 6 + f];
+      const int32_t* nb = d->neighbor + ((size_t)s * 6 + f) * 4;
+      if (rel < -1 || rel > 1) return HYDRO_ERR_INVALID;
+      if (nb[0] < -1 || nb[0] >= n) return HYDRO_ERR_INVALID;
+      if (rel != 0 && nb[0] < 0) return HYDRO_ERR_INVALID;
+      if (rel == 1)
+        for (int q = 1; q < 4; ++q)
+          if (nb[q] < 0 || nb[q] >= n) return HYDRO_ERR_INVALID;
+    }
+  }
+  hydro_handle* h = new (std::nothrow) hydro_handle();
+  if (!h) return HYDRO_ERR_NOMEM;
+  h->n = n;
+  h->precision = d->precision;
+  h->form = d->flux_form;
+  h->gamma = d->gamma;
+  h->eta = d->de_switch;
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+  if (e != cudaSuccess) {
+    delete h;
+    return HYDRO_ERR_CUDA;
+  }
+  bool ok = true;
+  ok = ok && cudaMalloc(&h->d_dx, sizeof(double) * n) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->d_nb, sizeof(int32_t) * n * 24) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->d_rel, n * 6) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->d_oct, n) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->d_queue, 4 * sizeof(unsigned int)) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->d_err, sizeof(int)) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->d_partial, sizeof(double) * n * NF * 2) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->d_dt, sizeof(double)) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->d_ms_tmp, 2 * sizeof(unsigned long long)) == cudaSuccess;
+  if (!ok) {
+    free_all(h);
+    delete h;
+    cudaGetLastError();
+    return HYDRO_ERR_NOMEM;
+  }
+  ok = ok && cudaMemcpy(h->d_dx, d->dx, sizeof(double) * n, cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && cudaMemcpy(h->d_nb, d->neighbor, sizeof(int32_t) * n * 24, cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && cudaMemcpy(h->d_rel, d->neighbor_rel, n * 6, cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && cudaMemcpy(h->d_oct, d->octant, n, cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && cudaMemset(h->d_err, 0, sizeof(int)) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+  h->occupancy = h->precision == HYDRO_MIXED ? stage_blocks_per_sm_mixed() : stage_blocks_per_sm_fp64();
+  if (!ok) {
+    free_all(h);
+    delete h;
+    return HYDRO_ERR_CUDA;
+  }
+  *out = h;
+  return HYDRO_OK;
+}
+
+int hydro_step(hydro_handle* h, const hydro_batch* batch, const double* U_in, const double* U0, double beta,
+               double dt, double* U_out, double* d_max_speed, void* stream) {
+  if (!h) return HYDRO_ERR_INVALID;
+  int rc = check_batch(h, batch);
+  if (rc) return rc;
+  if (!U_in || !U_out || !d_max_speed) return fail(h, HYDRO_ERR_INVALID, "NULL state or speed pointer");
+  if (U_in == U_out) return fail(h, HYDRO_ERR_INVALID, "U_out must not alias U_in");
+  if (!aligned(U_in, 16) || !aligned(U_out, 16) || (U0 && !aligned(U0, 16)) || !aligned(d_max_speed, 8))
+    return fail(h, HYDRO_ERR_INVALID, "misaligned pointer");
+  if (!(beta > 0.0 && beta <= 1.0)) return fail(h, HYDRO_ERR_INVALID, "beta must be in (0, 1]");
+  if (beta != 1.0 && !U0) return fail(h, HYDRO_ERR_INVALID, "U0 is required when beta != 1");
+  if (!(dt >= 0.0) || !std::isfinite(dt)) return fail(h, HYDRO_ERR_INVALID, "dt must be finite and >= 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  return enqueue_stage(h, batch->subgrid_ids, batch->n_items, U_in, beta == 1.0 ? nullptr : U0, beta, dt, nullptr,
+                       U_out, reinterpret_cast<unsigned long long*>(d_max_speed), 0, st);
+}
+
+int hydro_fill_ghosts(hydro_handle* h, double* U, void* stream) {
+  if (!h) return HYDRO_ERR_INVALID;
+  if (!U || !aligned(U, 16)) return fail(h, HYDRO_ERR_INVALID, "NULL or misaligned state");
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  return enqueue_ghosts(h, U, st);
+}
+
+}  // extern "C"
+
+namespace {
+
+int rk3_common(hydro_handle* h, const hydro_batch* batch, double* U, double* scratch1, double* scratch2,
+               double dt, double cfl, double* d_max_speed, double* d_dt_out, void* stream) {
+  if (!h) return HYDRO_ERR_INVALID;
+  int rc = check_batch(h, batch);
+  if (rc) return rc;
+  if (!U || !scratch1 || !scratch2 || !d_max_speed) return fail(h, HYDRO_ERR_INVALID, "NULL pointer");
+  if (U == scratch1 || U == scratch2 || scratch1 == scratch2)
+    return fail(h, HYDRO_ERR_INVALID, "U, scratch1, scratch2 must be distinct");
+  if (!aligned(U, 16) || !aligned(scratch1, 16) || !aligned(scratch2, 16) || !aligned(d_max_speed, 8) ||
+      (d_dt_out && !aligned(d_dt_out, 8)))
+    return fail(h, HYDRO_ERR_INVALID, "misaligned pointer");
+  if (cfl > 0.0) {
+    if (!(cfl <= 1.0)) return fail(h, HYDRO_ERR_INVALID, "cfl must be in (0, 1]");
+  } else if (!(dt >= 0.0) || !std::isfinite(dt)) {
+    return fail(h, HYDRO_ERR_INVALID, "dt must be finite and >= 0");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  GraphEntry* g = nullptr;
+  for (auto& e : h->graphs)
+    if (e.ids == batch->subgrid_ids && e.n_items == batch->n_items && e.U == U && e.s1 == scratch1 &&
+        e.s2 == scratch2 && e.dms == d_max_speed)
+      g = &e;
+  if (!g) {
+    // capture the three stages and the ghost fills on the handle's private stream
+    const int64_t before = h->launches;
+    CUDA_TRY(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaStream_t cs = h->cap_stream;
+    unsigned long long* ms = reinterpret_cast<unsigned long long*>(d_max_speed);
+    const int32_t* ids = batch->subgrid_ids;
+    const int ni = batch->n_items;
+    rc = enqueue_stage(h, ids, ni, U, nullptr, 1.0, 0.0, h->d_dt, scratch1, ms, 0, cs);
+    if (!rc) rc = enqueue_ghosts(h, scratch1, cs);
+    if (!rc) rc = enqueue_stage(h, ids, ni, scratch1, U, 0.25, 0.0, h->d_dt, scratch2, h->d_ms_tmp, 1, cs);
+    if (!rc) rc = enqueue_ghosts(h, scratch2, cs);
+    if (!rc) rc = enqueue_stage(h, ids, ni, scratch2, U, 2.0 / 3.0, 0.0, h->d_dt, U, h->d_ms_tmp, 2, cs);
+    if (!rc) rc = enqueue_ghosts(h, U, cs);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    const int kernels = (int)(h->launches - before);
+    h->launches = before;
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    GraphEntry ne;
+    ne.ids = batch->subgrid_ids;
+    ne.n_items = batch->n_items;
+    ne.U = U;
+    ne.s1 = scratch1;
+    ne.s2 = scratch2;
+    ne.dms = d_max_speed;
+    ne.kernels = kernels;
+    e = cudaGraphInstantiate(&ne.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+    if (h->graphs.size() >= 16) {
+      cudaGraphExecDestroy(h->graphs.front().exec);
+      h->graphs.erase(h->graphs.begin());
+    }
+    h->graphs.push_back(ne);
+    g = &h->graphs.back();
+  }
+  if (cfl > 0.0)
+    cfl_dt<<<1, 1, 0, st>>>(h->d_dt, d_max_speed, cfl, d_dt_out);
+  else
+    set_scalar<<<1, 1, 0, st>>>(h->d_dt, dt);
+  CUDA_TRY(h, cudaGetLastError());
+  CUDA_TRY(h, cudaGraphLaunch(g->exec, st));
+  h->launches += 1 + g->kernels;
+  return HYDRO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hydro_rk3_step(hydro_handle* h, const hydro_batch* batch, double* U, double* scratch1, double* scratch2,
+                   double dt, double* d_max_speed, void* stream) {
+  return rk3_common(h, batch, U, scratch1, scratch2, dt, 0.0, d_max_speed, nullptr, stream);
+}
+
+int hydro_rk3_step_cfl(hydro_handle* h, const hydro_batch* batch, double* U, double* scratch1, double* scratch2,
+                       double cfl, double* d_max_speed, double* d_dt_out, void* stream) {
+  if (!(cfl > 0.0)) return h ? fail(h, HYDRO_ERR_INVALID, "cfl must be in (0, 1]") : HYDRO_ERR_INVALID;
+  return rk3_common(h, batch, U, scratch1, scratch2, 0.0, cfl, d_max_speed, d_dt_out, stream);
+}
+
+int hydro_totals(hydro_handle* h, const double* U, double* d_totals, void* stream) {
+  if (!h) return HYDRO_ERR_INVALID;
+  if (!U || !d_totals || !aligned(U, 16) || !aligned(d_totals, 8))
+    return fail(h, HYDRO_ERR_INVALID, "NULL or misaligned pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  cudaError_t e = launch_totals(U, h->n, h->d_dx, h->d_partial, d_totals, st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "totals kernel launch");
+  h->launches += 2;
+  return HYDRO_OK;
+}
+
+int hydro_sync(hydro_handle* h) {
+  if (!h) return HYDRO_ERR_INVALID;
+  CUDA_TRY(h, cudaStreamSynchronize(h->last_stream));
+  int err = 0;
+  CUDA_TRY(h, cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  CUDA_TRY(h, cudaMemset(h->d_err, 0, sizeof(int)));
+  if (err & ERRBIT_BAD_ID) return fail(h, HYDRO_ERR_INVALID, "a sub-grid id was out of range");
+  if (err & ERRBIT_NONFINITE) return fail(h, HYDRO_ERR_NONFINITE, "non-finite value or non-positive density");
+  return HYDRO_OK;
+}
+
+const char* hydro_last_error(const hydro_handle* h) { return h ? h->msg : "NULL handle"; }
+
+int64_t hydro_launch_count(const hydro_handle* h) { return h ? h->launches : 0; }
+
+int hydro_set_param(hydro_handle* h, int32_t key, int32_t value) {
+  if (!h) return HYDRO_ERR_INVALID;
+  if (key == HYDRO_PARAM_STAGE_CTAS_PER_SM) {
+    if (value < 0 || value > 8) return fail(h, HYDRO_ERR_INVALID, "ctas per SM out of range");
+    h->ctas_per_sm = value;
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+    return HYDRO_OK;
+  }
+  if (key == HYDRO_PARAM_GHOST_THREADS) {
+    if (value < 64 || value > 1024 || value % 32) return fail(h, HYDRO_ERR_INVALID, "ghost threads out of range");
+    h->ghost_threads = value;
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+    return HYDRO_OK;
+  }
+  return fail(h, HYDRO_ERR_INVALID, "unknown parameter %d", key);
+}
+
+void hydro_destroy(hydro_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->last_stream);
+  free_all(h);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,97 @@
+// hydro_ghost.cu -- face ghost-slab fill of all sub-grids (paper Section VI:
+// the hydro boundary exchange, done here as a direct device gather from the
+// neighbours' interiors, the on-device analogue of the paper's direct memory
+// access between sub-grids of the same locality).
+//
+// One thread per (sub-grid, face, field, layer, row, column) ghost cell,
+// column fastest, so the 8 cells of a row are contiguous for y/z faces.
+//   same level : copy of the neighbour's interior cell;
+//   coarser    : value of the coarse cell containing the ghost-cell centre;
+//   finer      : mean of the 2x2x2 fine cells, summed in (k, j, i) order, * 1/8;
+//   boundary   : copy of the nearest interior cell (outflow).
+// Reads only interior cells and writes only ghost cells, so the result does
+// not depend on the order in which threads run.
+#include "hydro_internal.cuh"
+
+namespace hydro {
+namespace {
+
+__device__ __forceinline__ size_t cell_at(int s, int f, int i, int j, int k) {
+  return field_offset(s, f) + (size_t)k * NP2 + j * NP + i;
+}
+
+__global__ void ghost_kernel(const GhostArgs a) {
+  const size_t total = (size_t)a.n_sub * 6 * NF * NG * NX * NX;
+  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
+    const int c1 = (int)(g & 7);
+    const int c2 = (int)((g >> 3) & 7);
+    size_t rest = g >> 6;
+    const int layer = (int)(rest % NG);
+    rest /= NG;
+    const int f = (int)(rest % NF);
+    rest /= NF;
+    const int face = (int)(rest % 6);
+    const int s = (int)(rest / 6);
+    const int ax = face >> 1, side = face & 1;
+    const int b1 = ax == 0 ? 1 : 0;   // first transverse axis
+    const int b2 = ax == 2 ? 1 : 2;   // second transverse axis
+    const int ga = side ? NX + layer : -1 - layer;  // interior coordinate of the ghost along ax
+    int dst[3];
+    dst[ax] = ga + NG;
+    dst[b1] = c1 + NG;
+    dst[b2] = c2 + NG;
+    const int32_t* nb = a.nb + ((size_t)s * 6 + face) * 4;
+    const int rel = a.rel[s * 6 + face];
+    double v;
+    if (nb[0] < 0) {
+      int src[3] = {dst[0], dst[1], dst[2]};
+      src[ax] = side ? NG + NX - 1 : NG;
+      v = a.U[cell_at(s, f, src[0], src[1], src[2])];
+    } else if (rel == 0) {
+      int src[3] = {dst[0], dst[1], dst[2]};
+      src[ax] = (side ? ga - NX : ga + NX) + NG;
+      v = a.U[cell_at(nb[0], f, src[0], src[1], src[2])];
+    } else if (rel < 0) {
+      const int oc = a.oct[s];
+      const int fa = ga >= 0 ? ga / 2 : -((1 - ga) / 2);  // floor(ga / 2)
+      int src[3];
+      src[ax] = (side ? -4 : 8) + fa + NG;
+      src[b1] = 4 * ((oc >> b1) & 1) + (c1 >> 1) + NG;
+      src[b2] = 4 * ((oc >> b2) & 1) + (c2 >> 1) + NG;
+      v = a.U[cell_at(nb[0], f, src[0], src[1], src[2])];
+    } else {
+      const int q1 = c1 >> 2, q2 = c2 >> 2;
+      const int fs = nb[q1 + 2 * q2];
+      int base[3];
+      base[ax] = 2 * (side ? ga - NX : ga + 4) + NG;
+      base[b1] = 2 * (c1 - 4 * q1) + NG;
+      base[b2] = 2 * (c2 - 4 * q2) + NG;
+      double sum = 0.0;
+#pragma unroll
+      for (int dk = 0; dk < 2; ++dk)
+#pragma unroll
+        for (int dj = 0; dj < 2; ++dj)
+#pragma unroll
+          for (int di = 0; di < 2; ++di) sum = __dadd_rn(sum, a.U[cell_at(fs, f, base[0] + di, base[1] + dj, base[2] + dk)]);
+      v = __dmul_rn(sum, 0.125);
+    }
+    a.U[cell_at(s, f, dst[0], dst[1], dst[2])] = v;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_ghost_fill(const GhostArgs& a, int threads, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t total = (size_t)a.n_sub * 6 * NF * NG * NX * NX;
+  size_t blocks = (total + threads - 1) / threads;
+  const size_t cap = (size_t)sms * (2048 / threads) * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  ghost_kernel<<<(unsigned)blocks, threads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace hydro

@@ -1,0 +1,65 @@
+// hydro_internal.cuh -- shared definitions of the CUDA library (not part of the ABI).
+//
+// Sub-grid layout (identical to the ABI): U[s][f][k][j][i], 14^3 padded cells
+// per field, interior 3..10, 11 fields (rho, sx, sy, sz, egas, tau, rhoX1..5).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hydro {
+
+constexpr int NX = 8;            // interior cells per edge
+constexpr int NG = 3;            // ghost layers
+constexpr int NP = NX + 2 * NG;  // padded edge (14)
+constexpr int NP2 = NP * NP;
+constexpr int NP3 = NP * NP * NP;
+constexpr int NF = 11;           // conserved fields
+constexpr int NFACE = 9;         // faces per pencil that the update needs (2+1/2 .. 10+1/2)
+constexpr int NPEN = NX * NX;    // pencils per direction
+constexpr int FACES_DIR = NPEN * NFACE;  // 576
+constexpr int CELLS = NX * NX * NX;      // 512
+constexpr int F_RHO = 0, F_SX = 1, F_EGAS = 4, F_TAU = 5;
+
+// device error word bits
+constexpr int ERRBIT_NONFINITE = 1;
+constexpr int ERRBIT_BAD_ID = 2;
+
+__host__ __device__ inline size_t field_offset(int s, int f) { return ((size_t)s * NF + f) * NP3; }
+
+struct StageArgs {
+  const double* Uin;
+  const double* U0;     // nullptr when beta == 1
+  double* Uout;
+  const int32_t* ids;
+  int32_t n_items;
+  int32_t n_sub;
+  const double* dx;
+  double beta;
+  double dt;
+  const double* dt_dev;  // when non-null, dt is read from device memory
+  double gamma;
+  double eta;
+  int32_t form;          // 0 KNP, 1 KT
+  unsigned int* queue;   // work-queue counter, zero at launch
+  int* err;
+  unsigned long long* max_speed;  // [2] ordered bits of non-negative doubles
+};
+
+struct GhostArgs {
+  double* U;
+  int32_t n_sub;
+  const int32_t* nb;   // [n][6][4]
+  const int8_t* rel;   // [n][6]
+  const int8_t* oct;   // [n]
+};
+
+// launchers (defined in the .cu files)
+cudaError_t launch_stage_fp64(const StageArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_stage_mixed(const StageArgs& a, int grid, cudaStream_t st);
+int stage_blocks_per_sm_fp64();
+int stage_blocks_per_sm_mixed();
+cudaError_t launch_ghost_fill(const GhostArgs& a, int threads, cudaStream_t st);
+cudaError_t launch_totals(const double* U, int n, const double* dx, double* partial, double* totals,
+                          cudaStream_t st);
+
+}  // namespace hydro

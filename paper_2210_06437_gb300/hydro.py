@@ -1,0 +1,226 @@
+"""Python binding of the C ABI in include/hydro.h (ctypes; argument marshalling only).
+
+PyTorch provides device memory and streams; every step of the hydro path runs
+in the CUDA library ``libhydro.so`` built in-tree by ``build.py``.  There is no
+CPU fallback: if the library or a GPU is missing, constructing a HydroGrid
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhydro.so")
+
+NF, NP, NX, NG = 11, 14, 8, 3
+HYDRO_FP64, HYDRO_MIXED = 0, 1
+HYDRO_FLUX_KNP, HYDRO_FLUX_KT = 0, 1
+PARAM_STAGE_CTAS_PER_SM, PARAM_GHOST_THREADS = 0, 1
+RK3_BETA = (1.0, 0.25, 2.0 / 3.0)
+
+STATUS = {0: "HYDRO_OK", -1: "HYDRO_ERR_INVALID", -2: "HYDRO_ERR_CUDA", -3: "HYDRO_ERR_NOMEM",
+          -4: "HYDRO_ERR_NONFINITE", -5: "HYDRO_ERR_TIMEOUT", -6: "HYDRO_ERR_STATE"}
+
+# every symbol include/hydro.h declares
+EXPORTS = ("hydro_create", "hydro_step", "hydro_fill_ghosts", "hydro_rk3_step", "hydro_rk3_step_cfl", "hydro_totals",
+           "hydro_sync", "hydro_last_error", "hydro_launch_count", "hydro_set_param", "hydro_destroy")
+
+
+class HydroError(RuntimeError):
+    def __init__(self, code, msg=""):
+        super().__init__("%s (%d): %s" % (STATUS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("n_subgrids", ctypes.c_int32), ("n_fields", ctypes.c_int32), ("nx", ctypes.c_int32),
+                ("ghost", ctypes.c_int32), ("gamma", ctypes.c_double), ("de_switch", ctypes.c_double),
+                ("precision", ctypes.c_int32), ("flux_form", ctypes.c_int32), ("dx", ctypes.c_void_p),
+                ("neighbor", ctypes.c_void_p), ("neighbor_rel", ctypes.c_void_p), ("octant", ctypes.c_void_p)]
+
+
+class Batch(ctypes.Structure):
+    _fields_ = [("subgrid_ids", ctypes.c_void_p), ("n_items", ctypes.c_int32),
+                ("batch_offsets", ctypes.c_void_p), ("n_batches", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libhydro.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libhydro.so is missing: run paper_2210_06437_gb300.build.build() (nvcc, sm_103a)")
+    L = ctypes.CDLL(path)
+    vp, i32, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+    L.hydro_create.argtypes = [ctypes.POINTER(GridDesc), ctypes.POINTER(vp)]
+    L.hydro_step.argtypes = [vp, ctypes.POINTER(Batch), vp, vp, dbl, dbl, vp, vp, vp]
+    L.hydro_fill_ghosts.argtypes = [vp, vp, vp]
+    L.hydro_rk3_step.argtypes = [vp, ctypes.POINTER(Batch), vp, vp, vp, dbl, vp, vp]
+    L.hydro_rk3_step_cfl.argtypes = [vp, ctypes.POINTER(Batch), vp, vp, vp, dbl, vp, vp, vp]
+    L.hydro_totals.argtypes = [vp, vp, vp, vp]
+    L.hydro_sync.argtypes = [vp]
+    L.hydro_last_error.argtypes = [vp]
+    L.hydro_last_error.restype = ctypes.c_char_p
+    L.hydro_launch_count.argtypes = [vp]
+    L.hydro_launch_count.restype = ctypes.c_int64
+    L.hydro_set_param.argtypes = [vp, i32, i32]
+    L.hydro_destroy.argtypes = [vp]
+    L.hydro_destroy.restype = None
+    for name in EXPORTS:
+        if name not in ("hydro_last_error", "hydro_launch_count", "hydro_destroy"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class HydroGrid:
+    """A grid handle on the current CUDA device.
+
+    ``grid`` is a workloads.Grid-like object with arrays dx, neighbor,
+    neighbor_rel, octant and attributes n, gamma, de_switch."""
+
+    def __init__(self, grid, precision: str = "fp64", flux_form: int = HYDRO_FLUX_KNP,
+                 gamma: Optional[float] = None, de_switch: Optional[float] = None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("HydroGrid needs a CUDA device; there is no CPU path")
+        self.lib = load_library()
+        self.n = int(grid.n)
+        self.precision = precision
+        self._dx = np.ascontiguousarray(grid.dx, np.float64)
+        self._nb = np.ascontiguousarray(grid.neighbor, np.int32)
+        self._rel = np.ascontiguousarray(grid.neighbor_rel, np.int8)
+        self._oct = np.ascontiguousarray(grid.octant, np.int8)
+        d = GridDesc(self.n, NF, NX, NG, grid.gamma if gamma is None else gamma,
+                     grid.de_switch if de_switch is None else de_switch,
+                     HYDRO_MIXED if precision == "mixed" else HYDRO_FP64, flux_form,
+                     self._dx.ctypes.data, self._nb.ctypes.data, self._rel.ctypes.data, self._oct.ctypes.data)
+        h = ctypes.c_void_p()
+        rc = self.lib.hydro_create(ctypes.byref(d), ctypes.byref(h))
+        if rc != 0:
+            raise HydroError(rc, "hydro_create")
+        self.h = h
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self._all = torch.arange(self.n, dtype=torch.int32, device=self.device)
+        self._ms = torch.zeros(2, dtype=torch.float64, device=self.device)
+
+    # -- helpers ------------------------------------------------------------
+    def _check(self, rc):
+        if rc != 0:
+            raise HydroError(rc, self.lib.hydro_last_error(self.h).decode())
+
+    def _batch(self, ids, offsets):
+        import torch
+        if ids is None:
+            ids = self._all
+        elif not isinstance(ids, torch.Tensor) or ids.device.type != "cuda":
+            ids = torch.as_tensor(np.asarray(ids, np.int32), device=self.device)
+        assert ids.dtype == torch.int32 and ids.is_contiguous()
+        b = Batch(ids.data_ptr() if ids.numel() else None, ids.numel(), None, 0)
+        keep = [ids]
+        if offsets is not None:
+            off = np.ascontiguousarray(offsets, np.int32)
+            b.batch_offsets = off.ctypes.data
+            b.n_batches = len(off) - 1
+            keep.append(off)
+        return b, keep
+
+    def empty_state(self):
+        import torch
+        return torch.empty((self.n, NF, NP, NP, NP), dtype=torch.float64, device=self.device)
+
+    def _state(self, U):
+        import torch
+        assert isinstance(U, torch.Tensor) and U.dtype == torch.float64 and U.is_cuda and U.is_contiguous()
+        assert tuple(U.shape) == (self.n, NF, NP, NP, NP)
+        return U
+
+    # -- ABI calls ----------------------------------------------------------
+    def step(self, U_in, dt, U0=None, beta=1.0, U_out=None, ids=None, batch_offsets=None, max_speed=None,
+             stream=None):
+        """One RK stage (hydro_step).  Returns (U_out, max_speed tensor[2])."""
+        self._state(U_in)
+        if U_out is None:
+            U_out = U_in.clone()
+        self._state(U_out)
+        ms = self._ms if max_speed is None else max_speed
+        b, keep = self._batch(ids, batch_offsets)
+        self._check(self.lib.hydro_step(self.h, ctypes.byref(b), _ptr(U_in), _ptr(U0), float(beta), float(dt),
+                                        _ptr(U_out), _ptr(ms), _stream_ptr(stream)))
+        return U_out, ms
+
+    def fill_ghosts(self, U, stream=None):
+        self._state(U)
+        self._check(self.lib.hydro_fill_ghosts(self.h, _ptr(U), _stream_ptr(stream)))
+        return U
+
+    def rk3_step(self, U, dt, scratch1, scratch2, ids=None, batch_offsets=None, max_speed=None, stream=None):
+        """One SSP-RK3 step in place on U (hydro_rk3_step, graph replay).  Returns max_speed[2]."""
+        for t in (U, scratch1, scratch2):
+            self._state(t)
+        ms = self._ms if max_speed is None else max_speed
+        b, keep = self._batch(ids, batch_offsets)
+        self._keep = keep  # the captured graph refers to these device ids
+        self._check(self.lib.hydro_rk3_step(self.h, ctypes.byref(b), _ptr(U), _ptr(scratch1), _ptr(scratch2),
+                                            float(dt), _ptr(ms), _stream_ptr(stream)))
+        return ms
+
+    def rk3_step_cfl(self, U, cfl, scratch1, scratch2, max_speed, ids=None, batch_offsets=None, dt_out=None,
+                     stream=None):
+        """One SSP-RK3 step with dt = cfl / max_speed[1] chosen on the device
+        (hydro_rk3_step_cfl).  max_speed must hold the previous first-stage
+        speeds on entry; it holds this step's on exit."""
+        for t in (U, scratch1, scratch2):
+            self._state(t)
+        b, keep = self._batch(ids, batch_offsets)
+        self._keep = keep
+        self._check(self.lib.hydro_rk3_step_cfl(self.h, ctypes.byref(b), _ptr(U), _ptr(scratch1), _ptr(scratch2),
+                                                float(cfl), _ptr(max_speed), _ptr(dt_out), _stream_ptr(stream)))
+        return max_speed
+
+    def totals(self, U, out=None, stream=None):
+        import torch
+        self._state(U)
+        out = torch.empty(NF, dtype=torch.float64, device=self.device) if out is None else out
+        self._check(self.lib.hydro_totals(self.h, _ptr(U), _ptr(out), _stream_ptr(stream)))
+        return out
+
+    def sync(self):
+        """Wait and return the device status; raises HydroError on a device-side error."""
+        self._check(self.lib.hydro_sync(self.h))
+
+    def set_param(self, key, value):
+        self._check(self.lib.hydro_set_param(self.h, key, value))
+
+    @property
+    def launches(self) -> int:
+        return int(self.lib.hydro_launch_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hydro_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,319 @@
+"""GPU parity: the CUDA library through its C ABI against the CPU oracle.
+
+Error metric, per field over the compared interior cells:
+  err_f = max|x_f - r_f| / S_f,
+  S_f = max|r_f| for rho, egas, tau and the passive scalars,
+  S_f = max over cells of max(|s|, rho c) for the three momentum components
+        (the momentum-density scale: on a static or slow state the momentum
+        made in one stage is a difference of face pressures, some 100x below
+        the pressure; both paths show that amplification in max|x-r|/max|r|);
+a field whose reference is identically zero must be exactly zero.
+Tolerances: FP64 path <= 1e-12, mixed path <= 1e-5, for one stage and one
+full SSP-RK3 step from the same FP64 input.  Ghost fills are compared bit for
+bit (pure copies and fixed-order means).
+"""
+import numpy as np
+import pytest
+
+from paper_2210_06437_gb300 import workloads as W
+from tests import helpers as H
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "mixed": 1e-5}
+NG, NX = 3, 8
+IN = (slice(None), slice(None), slice(NG, NG + NX), slice(NG, NG + NX), slice(NG, NG + NX))
+
+
+@pytest.fixture(scope="module")
+def hydro():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2210_06437_gb300 import build, hydro as HY
+    build.build()
+    return HY
+
+
+def field_scales(ri, gamma=5.0 / 3.0):
+    """S_f of the module docstring from reference interiors ri [m,11,8,8,8]."""
+    S = np.abs(ri).max(axis=(0, 2, 3, 4))
+    rho = ri[:, 0]
+    s2 = ri[:, 1] ** 2 + ri[:, 2] ** 2 + ri[:, 3] ** 2
+    p = (gamma - 1.0) * np.maximum(ri[:, 4] - 0.5 * s2 / rho, 0.0)
+    S[1:4] = max(np.sqrt(s2).max(), np.sqrt(gamma * rho * p).max())
+    return S
+
+
+def field_errors(x, r, plain=False):
+    """Per-field errors of interior cells (arrays [m,11,14,14,14]); plain=True
+    divides every field by its own max|r_f|."""
+    xi, ri = x[IN], r[IN]
+    d = np.abs(xi - ri).max(axis=(0, 2, 3, 4))
+    S = np.abs(ri).max(axis=(0, 2, 3, 4)) if plain else field_scales(ri)
+    out = np.where(S > 0, d / np.where(S > 0, S, 1.0), np.where(d == 0, 0.0, np.inf))
+    return out
+
+
+def _dev(U):
+    return torch.from_numpy(U).cuda()
+
+
+def _host(t):
+    return t.cpu().numpy()
+
+
+# ---------------------------------------------------------------------------
+# ghost fill
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("cfg", [1, 2, 3])
+def test_ghost_fill_bit_exact(hydro, oracle_mod, cfg):
+    w = W.config(cfg)
+    U = w.state()
+    g = hydro.HydroGrid(w.grid)
+    Ud = _dev(U)
+    g.fill_ghosts(Ud)
+    g.sync()
+    oracle_mod.Oracle(w.grid).fill_ghosts(U)
+    got = _host(Ud)
+    # NaN canaries at edges/corners must be untouched on both sides
+    assert np.array_equal(got, U, equal_nan=True)
+
+
+# ---------------------------------------------------------------------------
+# one stage and one RK3 step vs the oracle
+# ---------------------------------------------------------------------------
+
+def _filled(oracle_mod, w):
+    U = w.state()
+    oracle_mod.Oracle(w.grid).fill_ghosts(U)
+    return U
+
+
+def _dt(oracle_mod, w, U, cfl=0.4):
+    _, ms, st = oracle_mod.Oracle(w.grid).stage(U, 0.0)
+    assert st == 0
+    return cfl / ms[1], ms
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("cfg", [1, 2, 3])
+def test_one_stage_matches_oracle(hydro, oracle_mod, cfg, prec):
+    w = W.config(cfg)
+    U = _filled(oracle_mod, w)
+    dt, ms_ref = _dt(oracle_mod, w, U)
+    o = oracle_mod.Oracle(w.grid)
+    # stage 2 of RK3: exercises U0 and the blend
+    U0 = U.copy()
+    U0[IN] *= 1.0 + 1e-3 * np.sin(np.arange(U0[IN].size).reshape(U0[IN].shape))
+    ref, ms_o, st = o.stage(U, dt, U0=U0, beta=0.25)
+    assert st == 0
+    g = hydro.HydroGrid(w.grid, precision=prec)
+    Ud, U0d = _dev(U), _dev(U0)
+    out = Ud.clone()
+    out, ms = g.step(Ud, dt, U0=U0d, beta=0.25, U_out=out)
+    g.sync()
+    got = _host(out)
+    err = field_errors(got, ref)
+    assert np.all(err <= TOL[prec]), (err, field_errors(got, ref, plain=True))
+    if prec == "fp64":
+        assert np.all(field_errors(got, ref, plain=True) <= TOL[prec])
+    np.testing.assert_allclose(ms.cpu().numpy(), ms_o, rtol=1e-14 if prec == "fp64" else 1e-6)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("cfg", [1, 2, 3])
+def test_rk3_step_matches_oracle(hydro, oracle_mod, cfg, prec):
+    w = W.config(cfg)
+    U = _filled(oracle_mod, w)
+    dt, _ = _dt(oracle_mod, w, U)
+    ref, ms_o, st = oracle_mod.Oracle(w.grid).rk3_step(U, dt)
+    assert st == 0
+    g = hydro.HydroGrid(w.grid, precision=prec)
+    Ud = _dev(U)
+    s1, s2 = torch.empty_like(Ud), torch.empty_like(Ud)
+    ids = torch.as_tensor(w.batches.ids, device="cuda")
+    ms = g.rk3_step(Ud, dt, s1, s2, ids=ids, batch_offsets=w.batches.offsets)
+    g.sync()
+    got = _host(Ud)
+    err = field_errors(got, ref)
+    assert np.all(err <= TOL[prec]), (err, field_errors(got, ref, plain=True))
+    np.testing.assert_allclose(ms.cpu().numpy(), ms_o, rtol=1e-14 if prec == "fp64" else 1e-6)
+    # ghosts were refilled by the step: compare them too (to the stage tolerance)
+    if prec == "fp64":
+        mask = ~np.isnan(ref)
+        assert np.array_equal(np.isnan(got), ~mask)
+        d = np.abs(got[mask] - ref[mask]).max()
+        assert d <= 1e-12 * np.abs(ref[mask]).max()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("cfg", [4, 5])
+def test_full_size_sampled_subgrids(hydro, oracle_mod, cfg, prec):
+    """Full-size configs in the benchmark's launch configuration: the GPU runs one
+    RK stage on every sub-grid of every batch; the oracle recomputes 48 sampled
+    sub-grids."""
+    w = W.config(cfg)
+    U = _filled(oracle_mod, w)
+    o = oracle_mod.Oracle(w.grid)
+    rng = np.random.default_rng(cfg)
+    sample = np.sort(rng.choice(w.grid.n, 48, replace=False)).astype(np.int32)
+    _, ms0, st = o.stage(U, 0.0, ids=sample)
+    dt = 0.4 / ms0[1]
+    ref1, _, st = o.stage(U, dt, ids=sample)
+    assert st == 0
+    g = hydro.HydroGrid(w.grid, precision=prec)
+    Ud = _dev(U)
+    del U
+    out = torch.empty_like(Ud)
+    ids = torch.as_tensor(w.batches.ids, device="cuda")
+    out, ms = g.step(Ud, dt, U_out=out, ids=ids, batch_offsets=w.batches.offsets)
+    g.sync()
+    sidx = torch.as_tensor(sample, device="cuda", dtype=torch.long)
+    got = out.index_select(0, sidx).cpu().numpy()
+    err = field_errors(got, ref1[sample])
+    assert np.all(err <= TOL[prec]), (err, field_errors(got, ref1[sample], plain=True))
+    # the global max speed bounds every sampled sub-grid's speed
+    assert ms.cpu().numpy()[1] >= ms0[1] * (1 - 1e-6)
+
+
+# ---------------------------------------------------------------------------
+# invariants on the GPU
+# ---------------------------------------------------------------------------
+
+NB = (2, 2, 2)
+
+
+def _gpu_step(hydro, G, prec, dt=0.004, rk3=True, nb=NB):
+    g = hydro.HydroGrid(W.uniform_grid(nb, (0, 0, 0), 1.0 / 16), precision=prec)
+    Ud = _dev(H.scatter(G, nb))
+    g.fill_ghosts(Ud)
+    if rk3:
+        g.rk3_step(Ud, dt, torch.empty_like(Ud), torch.empty_like(Ud))
+        out = Ud
+    else:
+        out, _ = g.step(Ud, dt, U_out=torch.empty_like(Ud))
+    g.sync()
+    return H.gather(_host(out), nb)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_uniform_state_bit_exact_gpu(hydro, prec):
+    rng = np.random.default_rng(5)
+    rho, p = rng.uniform(0.1, 3), rng.uniform(0.1, 3)
+    v = rng.uniform(-1, 1, 3)
+    X = rng.uniform(0, 1, 5)
+    sh = (16, 16, 16)
+    G = H.prim_to_global(*(np.full(sh, x) for x in (rho, *v, p)), [np.full(sh, x) for x in X])
+    assert np.array_equal(_gpu_step(hydro, G, prec), G)
+
+
+def _mirror(G, axis):
+    M = np.flip(G, axis=3 - axis).copy()
+    M[1 + axis] *= -1.0
+    return M
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_mirror_symmetry_bit_exact_gpu(hydro, prec, axis):
+    G = H.random_smooth_global((16, 16, 16), 61 + axis)
+    out = _gpu_step(hydro, G, prec)
+    outm = _gpu_step(hydro, _mirror(G, axis), prec)
+    assert np.array_equal(_mirror(out, axis), outm)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_conservation_gpu(hydro, prec):
+    w = W.config(2)
+    g = hydro.HydroGrid(w.grid, precision=prec)
+    Ud = _dev(w.state())
+    g.fill_ghosts(Ud)
+    before = _host(Ud)
+    g.rk3_step(Ud, 2e-3, torch.empty_like(Ud), torch.empty_like(Ud))
+    g.sync()
+    after = _host(Ud)
+    for f in range(W.NF):
+        b, ab = H.exact_total(w.grid, before, f)
+        a, _ = H.exact_total(w.grid, after, f)
+        assert abs(a - b) <= 1e-13 * ab, (f, a - b, ab)
+
+
+def test_totals_match_oracle(hydro, oracle_mod):
+    w = W.config(3)
+    U = w.state()
+    g = hydro.HydroGrid(w.grid)
+    t = g.totals(_dev(U)).cpu().numpy()
+    g.sync()
+    for f in range(W.NF):
+        ex, ab = H.exact_total(w.grid, U, f)
+        assert abs(t[f] - ex) <= 1e-15 * ab
+
+
+# ---------------------------------------------------------------------------
+# batches, edge cases and device-side error reporting
+# ---------------------------------------------------------------------------
+
+def test_ragged_batches_and_subsets(hydro, oracle_mod):
+    w = W.config(3)
+    U = _filled(oracle_mod, w)
+    g = hydro.HydroGrid(w.grid)
+    Ud = _dev(U)
+    rng = np.random.default_rng(9)
+    sub = rng.permutation(w.grid.n)[:777].astype(np.int32)
+    out = torch.full_like(Ud, 7.0)
+    out, ms = g.step(Ud, 1e-3, U_out=out, ids=sub, batch_offsets=[0, 1, 300, 300, 777])
+    g.sync()
+    ref, ms_o, _ = oracle_mod.Oracle(w.grid).stage(U, 1e-3, ids=sub)
+    got = _host(out)
+    assert np.all(field_errors(got[sub], ref[sub]) <= 1e-12)
+    others = np.setdiff1d(np.arange(w.grid.n), sub)
+    assert np.all(got[others] == 7.0)        # untouched
+    assert np.all(got[sub][:, :, 0] == 7.0)  # ghosts of processed sub-grids untouched
+    np.testing.assert_allclose(ms.cpu().numpy(), ms_o, rtol=1e-14)
+
+
+def test_empty_batch(hydro):
+    w = W.config(1)
+    g = hydro.HydroGrid(w.grid)
+    Ud = _dev(w.state())
+    out = torch.full_like(Ud, 3.0)
+    ms = torch.full((2,), 5.0, dtype=torch.float64, device="cuda")
+    g.step(Ud, 1e-3, U_out=out, ids=torch.empty(0, dtype=torch.int32, device="cuda"), max_speed=ms)
+    g.sync()
+    assert torch.all(out == 3.0)
+    assert torch.all(ms == 0.0)
+
+
+def test_device_errors_are_reported(hydro, oracle_mod):
+    w = W.config(1)
+    U = _filled(oracle_mod, w)
+    g = hydro.HydroGrid(w.grid)
+    Ud = _dev(U)
+    bad = torch.tensor([0, 99], dtype=torch.int32, device="cuda")
+    g.step(Ud, 1e-3, U_out=torch.empty_like(Ud), ids=bad)
+    with pytest.raises(hydro.HydroError) as e:
+        g.sync()
+    assert e.value.code == -1
+    U2 = U.copy()
+    U2[3, 0, 5, 5, 5] = np.nan
+    g.step(_dev(U2), 1e-3, U_out=torch.empty_like(Ud))
+    with pytest.raises(hydro.HydroError) as e:
+        g.sync()
+    assert e.value.code == -4
+    g.sync()  # the error word was cleared
+
+
+def test_host_argument_errors(hydro):
+    w = W.config(1)
+    g = hydro.HydroGrid(w.grid)
+    Ud = _dev(w.state())
+    with pytest.raises(hydro.HydroError):
+        g.step(Ud, -1.0, U_out=torch.empty_like(Ud))
+    with pytest.raises(hydro.HydroError):
+        g.step(Ud, 1e-3, U_out=Ud)
+    with pytest.raises(hydro.HydroError):
+        g.step(Ud, 1e-3, U_out=torch.empty_like(Ud), beta=0.5)  # U0 missing
+    with pytest.raises(hydro.HydroError):
+        g.step(Ud, 1e-3, U_out=torch.empty_like(Ud), batch_offsets=[0, 5])  # offsets do not reach n
