@@ -424,7 +424,10 @@ def _init_polytrope(perturb: bool):
             if perturb:
                 rho = rho * (1.0 + 0.01 * rng.uniform(-1.0, 1.0, rho.shape))
             R = np.sqrt(x * x + y * y)
-            vphi = np.where(rho > 1e-9, 0.5 * (R / 0.2) / (1.0 + (R / 0.2) ** 2) ** 0.75, 0.0)
+            # softened Keplerian profile, tapered smoothly to rest in the
+            # low-density envelope (a hard cut at the surface makes face
+            # velocities s/rho of the conserved-variable reconstruction blow up)
+            vphi = 0.5 * (R / 0.2) / (1.0 + (R / 0.2) ** 2) ** 0.75 * (rho / (rho + 1e-2))
             Rs = np.where(R > 0, R, 1.0)
             vx = np.where(R > 0, -vphi * y / Rs, 0.0)
             vy = np.where(R > 0, vphi * x / Rs, 0.0)
