@@ -114,8 +114,9 @@ int hydro_create(const hydro_grid_desc *desc, hydro_handle **out);
  *   U_out = U0 + beta * (U* - U0)      (U_out = U* when beta == 1),
  * which is the Shu-Osher blend (1 - beta) U0 + beta U*.  SSP-RK3 uses
  * beta = 1, 1/4, 2/3 with U0 the state at the start of the step.
- *   U_in   DEVICE padded state; its face ghost slabs must be filled (edge and
- *          corner ghost cells are never read);
+ *   U_in   DEVICE padded state; only interior cells are read: each face
+ *          halo is gathered from the neighbours' interiors by the rules of
+ *          hydro_fill_ghosts, so the ghost cells of U_in need not be filled;
  *   U0     DEVICE padded state, read at interior cells; may be NULL iff beta == 1;
  *   U_out  DEVICE padded state; only the interiors of the listed sub-grids are
  *          written; must not alias U_in; may alias U0;
@@ -136,10 +137,12 @@ int hydro_step(hydro_handle *h, const hydro_batch *batch, const double *U_in, co
 int hydro_fill_ghosts(hydro_handle *h, double *U, void *stream);
 
 /* One SSP-RK3 step (three stages, Section I: three hydro iterations per
- * time-step) with ghost fills between stages, replayed from a CUDA graph that
- * the handle captures on first use for each (batch, U, scratch) combination.
- *   U        DEVICE padded state with filled ghosts; overwritten by the new
- *            state, ghosts filled;
+ * time-step), replayed from a CUDA graph that the handle captures on first use
+ * for each (batch, U, scratch) combination.  The stages gather their halos
+ * from the neighbours' interiors, so no ghost fill runs between stages.
+ *   U        DEVICE padded state; its interior is overwritten by the new state
+ *            (ghost cells are neither read nor updated: call hydro_fill_ghosts
+ *            when they are wanted);
  *   scratch1, scratch2  DEVICE padded states of the same size (contents
  *            destroyed);
  *   d_max_speed DEVICE double[2]: the max speeds of the first stage, i.e. of

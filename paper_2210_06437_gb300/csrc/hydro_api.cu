@@ -147,6 +147,9 @@ int enqueue_stage(hydro_handle* h, const int32_t* ids, int n_items, const double
   a.n_items = n_items;
   a.n_sub = h->n;
   a.dx = h->d_dx;
+  a.nb = h->d_nb;
+  a.rel = h->d_rel;
+  a.oct = h->d_oct;
   a.beta = beta;
   a.dt = dt;
   a.dt_dev = dt_dev;
@@ -311,12 +314,11 @@ int rk3_common(hydro_handle* h, const hydro_batch* batch, double* U, double* scr
     unsigned long long* ms = reinterpret_cast<unsigned long long*>(d_max_speed);
     const int32_t* ids = batch->subgrid_ids;
     const int ni = batch->n_items;
+    // the stage kernel gathers halos from the neighbours' interiors itself, so
+    // no ghost fill is needed between stages
     rc = enqueue_stage(h, ids, ni, U, nullptr, 1.0, 0.0, h->d_dt, scratch1, ms, 0, cs);
-    if (!rc) rc = enqueue_ghosts(h, scratch1, cs);
     if (!rc) rc = enqueue_stage(h, ids, ni, scratch1, U, 0.25, 0.0, h->d_dt, scratch2, h->d_ms_tmp, 1, cs);
-    if (!rc) rc = enqueue_ghosts(h, scratch2, cs);
     if (!rc) rc = enqueue_stage(h, ids, ni, scratch2, U, 2.0 / 3.0, 0.0, h->d_dt, U, h->d_ms_tmp, 2, cs);
-    if (!rc) rc = enqueue_ghosts(h, U, cs);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &graph);
     const int kernels = (int)(h->launches - before);

@@ -1,24 +1,33 @@
 // hydro_stage.cu -- one Runge-Kutta stage of the octree hydro step on GB300.
 //
 // Persistent kernel: CTAs pull sub-grid ids from a device work queue (one
-// atomic counter per launch), so any number of uneven leaf batches runs in
-// one launch.  Per sub-grid and per direction d:
-//   A. PPM (Colella & Woodward 1984) of every field along each of the 64
-//      pencils, sliding window in registers: one task = (field, pencil);
-//      writes the left/right face states of the 9 faces the update needs;
-//   B. one task per face: face EOS with dual-energy switch, one-sided
-//      (central-upwind, Kurganov-Noelle-Petrova) or symmetric (Kurganov-
-//      Tadmor) signal speeds, numerical flux of the 11 fields;
-//   C. every thread owns two interior cells and accumulates the flux
-//      difference of direction d, in x, y, z order.
-// Then U* = U + dt/dx dU and U_out = U0 + beta (U* - U0).  The face signal
-// speeds are reduced with warp shuffles and one ordered-bits atomicMax per
-// sub-grid (paper Section V-B.1: reconstruct kernel, flux kernel, and the
-// global time-step reduction of compute_fluxes).
+// atomic counter per launch), so every uneven leaf batch of a call runs in one
+// launch.  For each sub-grid:
+//   * the 8^3 interior of the 11 fields is staged once into shared memory;
+//   * for each direction d the two 3-layer halo slabs are gathered straight
+//     from the neighbours' interiors (same level: asynchronous cp.async copies
+//     issued while the previous direction computes; coarser neighbour:
+//     injection; finer neighbours: 2x2x2 mean; domain boundary: outflow copy)
+//     -- the on-device form of the paper's direct neighbour access for the
+//     hydro boundary exchange (Section VI), so no ghost-fill pass is needed
+//     between stages and ghost cells of the input are never read;
+//   * PPM (Colella & Woodward 1984) per (field, pencil), sliding window in
+//     registers, writes the 9 face states of each pencil (Section V-B.1
+//     reconstruct kernel);
+//   * one thread per face: EOS with dual-energy switch, central-upwind or
+//     central speeds, numerical flux of all fields (flux kernel);
+//   * each thread owns two cells and sums their flux differences in x, y, z
+//     order;
+// then U* = U + dt/dx dU, U_out = U0 + beta (U* - U0), and the sub-grid's
+// largest face speed joins the global maximum (compute_fluxes' time-step
+// reduction) through one ordered-bits atomicMax.
 //
-// Two instantiations: T = double (all FP64) and T = float (mixed: FP32
-// reconstruction and flux; flux differences accumulated exactly as a float
-// pair and the conserved update done in FP64).
+// T = double: every step in FP64.  T = float (mixed): FP64 inputs are rounded
+// to FP32 once, by integer operations (GB300 runs FP64 and f32<->f64
+// conversions at about 2 per clock per SM, the FP32/INT pipes at 128), the
+// reconstruction and flux run in FP32, the six flux terms of every cell are
+// summed error-free as a float pair (TwoSum cascade), and the conserved update
+// is done in FP64 (2 FP64 operations per value in stage 1, 4 with the blend).
 #include <cmath>
 
 #include "hydro_internal.cuh"
@@ -27,6 +36,38 @@ namespace hydro {
 namespace {
 
 constexpr int THREADS = 256;
+constexpr int SJ = 9, SK = 72;   // shared-memory strides of the interior tile (2-way bank conflicts at most)
+constexpr int ISZ = 8 * SK;      // elements per field of the interior tile
+constexpr int HALO = 3 * NPEN;   // cells per halo slab (3 layers x 64 pencils)
+
+// ---------------------------------------------------------------------------
+// precision traits
+// ---------------------------------------------------------------------------
+
+// FP64 -> FP32 with integer operations: round to nearest on the magnitude
+// (ties away from zero); values below the FP32 normal range become signed
+// zero, larger finite values infinity, NaN stays NaN.
+__device__ __forceinline__ float f64_to_f32(double x) {
+  const unsigned lo = (unsigned)__double2loint(x), hi = (unsigned)__double2hiint(x);
+  const unsigned mag = hi & 0x7fffffffu;
+  unsigned r = __funnelshift_l(lo, hi, 3) + ((lo >> 28) & 1u) - 0xC0000000u;
+  if (mag - 0x38100000u >= 0x0FE00000u) {
+    r = mag < 0x38100000u ? 0u : ((mag > 0x7ff00000u || (mag == 0x7ff00000u && lo)) ? 0x7fc00000u : 0x7f800000u);
+  }
+  return __uint_as_float(r | (hi & 0x80000000u));
+}
+
+// FP32 -> FP64, exact, with integer operations (FP32 subnormals become zero).
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned b = __float_as_uint(f), mag = b & 0x7fffffffu;
+  unsigned hi = (mag >> 3) + 0x38000000u, lo = b << 29;
+  if (mag - 0x00800000u >= 0x7f000000u) {
+    const bool small = mag < 0x00800000u;
+    hi = small ? 0u : (0x7ff00000u | (mag >> 3));
+    lo = small ? 0u : lo;
+  }
+  return __hiloint2double((int)(hi | (b & 0x80000000u)), (int)lo);
+}
 
 template <typename T>
 struct Arith;
@@ -57,7 +98,7 @@ struct Arith<float> {
   static __device__ __forceinline__ float pow_(float x, float y) { return __powf(x, y); }
   static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
   static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
-  static __device__ __forceinline__ float from64(double x) { return __double2float_rn(x); }
+  static __device__ __forceinline__ float from64(double x) { return f64_to_f32(x); }
   static constexpr float tiny = 1e-30f;
 };
 
@@ -133,10 +174,10 @@ __device__ __forceinline__ void face_eos(const T (&U)[NF], int d, T gamma, T eta
 }
 
 // Numerical flux written as F = wl*UL + wr*UR for every field plus pressure
-// terms on the normal momentum and the energy; algebraically the central-
+// terms on the normal momentum and the energy: algebraically the central-
 // upwind flux ((a+ FL - a- FR) + a+ a- (UR - UL)) / (a+ - a-).  Products are
 // rounded separately (no contraction) so that mirrored faces give exactly
-// negated or equal fluxes.
+// negated or equal fluxes.  Returns max(a+, -a-).
 template <typename T>
 __device__ __forceinline__ T face_flux(const T (&UL)[NF], const T (&UR)[NF], int d, T gamma, T eta, int form,
                                        T (&F)[NF]) {
@@ -175,8 +216,15 @@ __device__ __forceinline__ T face_flux(const T (&UL)[NF], const T (&UR)[NF], int
 }
 
 // ---------------------------------------------------------------------------
-// accumulators
+// accumulators and update
 // ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bp = __fadd_rn(s, -a);
+  float ap = __fadd_rn(s, -bp);
+  e = __fadd_rn(__fadd_rn(a, -ap), __fadd_rn(b, -bp));
+}
 
 template <typename T>
 struct Acc;
@@ -186,57 +234,251 @@ struct Acc<double> {
   double v;
   __device__ __forceinline__ void set_diff(double lo, double hi) { v = lo - hi; }
   __device__ __forceinline__ void add_diff(double lo, double hi) { v = v + (lo - hi); }
-  __device__ __forceinline__ double value() const { return v; }
+  // U* = u + lam dU;  out = u0 + beta (U* - u0)
+  __device__ __forceinline__ double update(double u, double u0, double lam, float, float, double beta,
+                                           bool blend) const {
+    double us = fma(lam, v, u);
+    return blend ? fma(beta, us - u0, u0) : us;
+  }
 };
 
-// Float pair (hi + lo) carrying the flux-difference sum exactly enough for
-// conservation to FP64 round-off: error-free TwoSum (Knuth) of each term.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  float bp = __fadd_rn(s, -a);
-  float ap = __fadd_rn(s, -bp);
-  e = __fadd_rn(__fadd_rn(a, -ap), __fadd_rn(b, -bp));
-}
-
+// Float pair (s + c) holding the running flux-difference sum: the difference
+// of a direction's two face fluxes is formed exactly first (so a mirrored cell,
+// which sees the two terms swapped and negated, gets the same pair), then added
+// through an error-free TwoSum; the six-term sum is exact to about 2^-48.
 template <>
 struct Acc<float> {
-  float hi, lo;
-  __device__ __forceinline__ void set_diff(float a, float b) { two_sum(a, -b, hi, lo); }
+  float s, c;
+  __device__ __forceinline__ void set_diff(float a, float b) { two_sum(a, -b, s, c); }
   __device__ __forceinline__ void add_diff(float a, float b) {
-    float d, e, s, t;
+    float d, e, t, e2;
     two_sum(a, -b, d, e);
-    two_sum(hi, d, s, t);
-    t = __fadd_rn(t, __fadd_rn(lo, e));
-    hi = __fadd_rn(s, t);
-    lo = __fadd_rn(t, -__fadd_rn(hi, -s));
+    two_sum(s, d, t, e2);
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(e, e2));
   }
-  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+  // lam dU formed as a float pair (lh + ll)(s + c), then added in FP64.
+  __device__ __forceinline__ double update(double u, double u0, double, float lh, float ll, double beta,
+                                           bool blend) const {
+    float p = __fmul_rn(lh, s);
+    float e = fmaf(lh, s, -p);
+    e = fmaf(lh, c, e);
+    e = fmaf(ll, s, e);
+    double us = (u + f32_to_f64(p)) + f32_to_f64(e);
+    return blend ? fma(beta, us - u0, u0) : us;
+  }
 };
 
-__device__ __forceinline__ bool finite64(double v) {
-  return (((unsigned long long)__double_as_longlong(v) >> 52) & 0x7ff) != 0x7ff;
+__device__ __forceinline__ bool bad64(double v, bool density) {
+  const unsigned hi = (unsigned)__double2hiint(v);
+  const bool nonfinite = (hi & 0x7ff00000u) == 0x7ff00000u;
+  const bool nonpos = density && (((int)hi < 0) || ((hi | (unsigned)__double2loint(v)) == 0u));
+  return nonfinite || nonpos;
 }
 
-__device__ __forceinline__ double warp_max(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    double w = __shfl_xor_sync(0xffffffffu, v, o);
-    v = (w > v || w != w) ? w : v;
+// ---------------------------------------------------------------------------
+// halo gather
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void cp_async8(double* dst, const double* src) {  // 8-byte global -> shared copy
+  const unsigned a = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(a), "l"(src));
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::); }
+
+struct Nbr {
+  int32_t id[6][4];
+  int rel[6];
+  int oct;
+};
+
+__device__ __forceinline__ int pad_offset(int i, int j, int k) { return k * NP2 + j * NP + i; }
+
+// Offset within a field of padded cell coordinates given along (D, b1, b2).
+template <int D>
+__device__ __forceinline__ int offset_dbb(int cd, int c1, int c2) {
+  return D == 0 ? pad_offset(cd, c1, c2) : (D == 1 ? pad_offset(c1, cd, c2) : pad_offset(c1, c2, cd));
+}
+
+// Gather the two halo slabs of direction D of sub-grid s into halo[f][side][l*64 + p]
+// (FP64); l is the slab layer (pencil position m = l or 11 + l), p = t2*8 + t1.
+// Threads 0..191 each own one (l, p) and walk the 11 fields of both slabs;
+// every copy of a single cell (same level, coarser neighbour, outflow) is an
+// asynchronous cp.async, the 2x2x2 means are computed in place.
+template <int D>
+__device__ __forceinline__ void gather_halo(const double* __restrict__ U, int s, const Nbr& nb, double* halo) {
+  const int q = threadIdx.x;
+  if (q >= HALO) return;
+  int l, p;
+  if (D == 0) {  // x slabs: consecutive threads walk the 3 contiguous cells of a row
+    p = q / 3;
+    l = q - 3 * p;
+  } else {
+    l = q >> 6;
+    p = q & 63;
   }
-  return v;
+  const int t1 = p & 7, t2 = p >> 3;
+  const int b1 = D == 0 ? 1 : 0;
+  const int b2 = D == 2 ? 1 : 2;
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const int face = 2 * D + side;
+    const int ga = side ? NX + l : l - NG;  // interior coordinate of the ghost cell along D
+    double* dst = halo + side * HALO + l * NPEN + p;
+    const int n0 = nb.id[face][0];
+    const int rel = nb.rel[face];
+    if (rel <= 0) {
+      // one source cell per ghost cell: copy
+      int src_s, off;
+      if (n0 >= 0 && rel == 0) {
+        src_s = n0;
+        off = offset_dbb<D>((side ? ga - NX : ga + NX) + NG, t1 + NG, t2 + NG);
+      } else if (n0 < 0) {
+        src_s = s;
+        off = offset_dbb<D>(side ? NG + NX - 1 : NG, t1 + NG, t2 + NG);
+      } else {
+        const int fa = ga >= 0 ? ga / 2 : -((1 - ga) / 2);
+        src_s = n0;
+        off = offset_dbb<D>((side ? -4 : 8) + fa + NG, 4 * ((nb.oct >> b1) & 1) + (t1 >> 1) + NG,
+                            4 * ((nb.oct >> b2) & 1) + (t2 >> 1) + NG);
+      }
+      const double* src = U + field_offset(src_s, 0) + off;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) cp_async8(dst + f * 2 * HALO, src + (size_t)f * NP3);
+    } else {
+      // finer neighbours: mean of the 2x2x2 fine cells, summed in (k, j, i) order
+      const int q1 = t1 >> 2, q2 = t2 >> 2;
+      const int fs = nb.id[face][q1 + 2 * q2];
+      const int cd = 2 * (side ? ga - NX : ga + 4) + NG;
+      const int c1 = 2 * (t1 - 4 * q1) + NG, c2 = 2 * (t2 - 4 * q2) + NG;
+      int c[3];
+      c[D] = cd;
+      c[b1] = c1;
+      c[b2] = c2;
+      const double* src = U + field_offset(fs, 0) + pad_offset(c[0], c[1], c[2]);
+#pragma unroll 1
+      for (int f = 0; f < NF; ++f) {
+        const double* g = src + (size_t)f * NP3;
+        double sum = 0.0;
+#pragma unroll
+        for (int dk = 0; dk < 2; ++dk)
+#pragma unroll
+          for (int dj = 0; dj < 2; ++dj)
+#pragma unroll
+            for (int di = 0; di < 2; ++di) sum = __dadd_rn(sum, g[dk * NP2 + dj * NP + di]);
+        dst[f * 2 * HALO] = __dmul_rn(sum, 0.125);
+      }
+    }
+  }
+}
+
+// interior tile index of pencil position n (0..7) of pencil p in direction d
+__device__ __forceinline__ int tile_index(int d, int p, int n) {
+  const int t1 = p & 7, t2 = p >> 3;
+  return d == 0 ? t2 * SK + t1 * SJ + n : (d == 1 ? t2 * SK + n * SJ + t1 : n * SK + t2 * SJ + t1);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(THREADS, 2) stage_kernel(const StageArgs a) {
+struct StageSmem {
+  static constexpr size_t interior = sizeof(T) * NF * ISZ;
+  static constexpr size_t halo = sizeof(double) * NF * 2 * HALO;
+  static constexpr size_t faces = sizeof(T) * 2 * NF * FACES_DIR;
+  static constexpr size_t total = interior + halo + faces;
+};
+
+template <typename T>
+struct Shared {
+  T* tile;       // [NF][ISZ] interior, T
+  double* halo;  // [NF][2][HALO] current direction's halo slabs, FP64
+  T* fsl;        // [NF][576] left face states, then fluxes
+  T* fsr;        // [NF][576] right face states
+};
+
+// One direction of the stage: PPM of every (field, pencil), the next
+// direction's halo gather (issued once the halo buffer is free), the face
+// fluxes and the flux differences of the two owned cells.
+template <typename T, int D>
+__device__ __forceinline__ void direction_pass(const Shared<T>& sh, const StageArgs& a, int s, const Nbr& nb,
+                                               Acc<T> (&acc)[2][NF], T& amax, T gamma, T eta) {
+  const int tid = threadIdx.x;
+  cp_async_wait_all();
+  __syncthreads();  // this direction's halo (and, for x, the interior tile) is in place
+  // A: PPM, one (field, pencil) task per iteration
+#pragma unroll 1
+  for (int task = tid; task < NF * NPEN; task += THREADS) {
+    const int f = task >> 6, p = task & 63;
+    T q[NP];
+    const double* hl = sh.halo + (f * 2) * HALO + p;
+#pragma unroll
+    for (int m = 0; m < NG; ++m) q[m] = Arith<T>::from64(hl[m * NPEN]);
+#pragma unroll
+    for (int n = 0; n < NX; ++n) q[NG + n] = sh.tile[f * ISZ + tile_index(D, p, n)];
+#pragma unroll
+    for (int m = 0; m < NG; ++m) q[NG + NX + m] = Arith<T>::from64(hl[HALO + m * NPEN]);
+    T ul[NFACE], ur[NFACE];
+    ppm_pencil(q, ul, ur);
+#pragma unroll
+    for (int m = 0; m < NFACE; ++m) {
+      sh.fsl[f * FACES_DIR + p * NFACE + m] = ul[m];
+      sh.fsr[f * FACES_DIR + p * NFACE + m] = ur[m];
+    }
+  }
+  __syncthreads();
+  // the halo buffer is free: start gathering the next direction's slabs
+  if (D < 2) gather_halo<(D < 2 ? D + 1 : 2)>(a.Uin, s, nb, sh.halo);
+  // B: one face per iteration
+#pragma unroll 1
+  for (int fc = tid; fc < FACES_DIR; fc += THREADS) {
+    T UL[NF], UR[NF], F[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      UL[f] = sh.fsl[f * FACES_DIR + fc];
+      UR[f] = sh.fsr[f * FACES_DIR + fc];
+    }
+    T sp = face_flux(UL, UR, D, gamma, eta, a.form, F);
+    amax = (sp > amax || sp != sp) ? sp : amax;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) sh.fsl[f * FACES_DIR + fc] = F[f];
+  }
+  __syncthreads();
+  // C: flux differences of direction D for the two owned cells
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int c = tid + r * THREADS;
+    const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
+    const int p = D == 0 ? (k * 8 + j) : (D == 1 ? (k * 8 + i) : (j * 8 + i));
+    const int id = D == 0 ? i : (D == 1 ? j : k);
+    const int base = p * NFACE + id;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      T lo = sh.fsl[f * FACES_DIR + base], hi = sh.fsl[f * FACES_DIR + base + 1];
+      if (D == 0)
+        acc[r][f].set_diff(lo, hi);
+      else
+        acc[r][f].add_diff(lo, hi);
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(const StageArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* fsl = reinterpret_cast<T*>(smem_raw);  // [NF][576] left states, then fluxes
-  T* fsr = fsl + NF * FACES_DIR;             // [NF][576] right states
+  Shared<T> sh;
+  sh.tile = reinterpret_cast<T*>(smem_raw);
+  sh.halo = reinterpret_cast<double*>(smem_raw + StageSmem<T>::interior);
+  sh.fsl = reinterpret_cast<T*>(smem_raw + StageSmem<T>::interior + StageSmem<T>::halo);
+  sh.fsr = sh.fsl + NF * FACES_DIR;
   __shared__ int s_item;
-  __shared__ double s_red[THREADS / 32];
+  __shared__ Nbr s_nb;
+  __shared__ double s_lam;
+  __shared__ float s_lh, s_ll;
+  __shared__ unsigned long long s_red[THREADS / 32];
 
   const int tid = threadIdx.x;
   const T gamma = T(a.gamma), eta = T(a.eta);
   const double dt = a.dt_dev ? *a.dt_dev : a.dt;
+  const bool blend = a.beta != 1.0;
   int bad = 0;
 
   for (;;) {
@@ -250,70 +492,39 @@ __global__ void __launch_bounds__(THREADS, 2) stage_kernel(const StageArgs a) {
       __syncthreads();
       continue;
     }
+    if (tid < 24) s_nb.id[tid >> 2][tid & 3] = a.nb[(size_t)s * 24 + tid];
+    if (tid < 6) s_nb.rel[tid] = a.rel[s * 6 + tid];
+    if (tid == 0) {
+      s_nb.oct = a.oct[s];
+      const double lam = dt / a.dx[s];
+      s_lam = lam;
+      s_lh = (float)lam;
+      s_ll = (float)(lam - (double)(float)lam);
+    }
+    // interior of all fields, FP64 -> T
     const double* Us = a.Uin + field_offset(s, 0);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int c = tid + r * THREADS;
+      const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
+      const int g = (k + NG) * NP2 + (j + NG) * NP + (i + NG);
+      const int t = k * SK + j * SJ + i;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) sh.tile[f * ISZ + t] = Arith<T>::from64(Us[(size_t)f * NP3 + g]);
+    }
+    __syncthreads();  // s_nb and lambda ready
+    const Nbr& nb = s_nb;
+    gather_halo<0>(a.Uin, s, nb, sh.halo);
+
     Acc<T> acc[2][NF];
     T amax = T(0);
-
-#pragma unroll 1
-    for (int d = 0; d < 3; ++d) {
-      // pencil p = t2*8 + t1 -> (i,j,k) strides of the transverse and normal axes
-      const int sn = d == 0 ? 1 : (d == 1 ? NP : NP2);
-      const int s1 = d == 0 ? NP : 1;
-      const int s2 = d == 2 ? NP : NP2;
-      // A: PPM, one (field, pencil) task per thread iteration
-#pragma unroll 1
-      for (int task = tid; task < NF * NPEN; task += THREADS) {
-        const int f = task / NPEN, p = task % NPEN;
-        const double* src = Us + (size_t)f * NP3 + (NG + (p & 7)) * s1 + (NG + (p >> 3)) * s2;
-        T q[NP];
-#pragma unroll
-        for (int m = 0; m < NP; ++m) q[m] = Arith<T>::from64(src[m * sn]);
-        T ul[NFACE], ur[NFACE];
-        ppm_pencil(q, ul, ur);
-#pragma unroll
-        for (int m = 0; m < NFACE; ++m) {
-          fsl[f * FACES_DIR + p * NFACE + m] = ul[m];
-          fsr[f * FACES_DIR + p * NFACE + m] = ur[m];
-        }
-      }
-      __syncthreads();
-      // B: one face per thread iteration
-#pragma unroll 1
-      for (int fc = tid; fc < FACES_DIR; fc += THREADS) {
-        T UL[NF], UR[NF], F[NF];
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-          UL[f] = fsl[f * FACES_DIR + fc];
-          UR[f] = fsr[f * FACES_DIR + fc];
-        }
-        T sp = face_flux(UL, UR, d, gamma, eta, a.form, F);
-        amax = (sp > amax || sp != sp) ? sp : amax;
-#pragma unroll
-        for (int f = 0; f < NF; ++f) fsl[f * FACES_DIR + fc] = F[f];
-      }
-      __syncthreads();
-      // C: flux differences of direction d for the two owned cells
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        const int c = tid + r * THREADS;
-        const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
-        const int p = d == 0 ? (k * 8 + j) : (d == 1 ? (k * 8 + i) : (j * 8 + i));
-        const int id = d == 0 ? i : (d == 1 ? j : k);
-        const int base = p * NFACE + id;
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-          T lo = fsl[f * FACES_DIR + base], hi = fsl[f * FACES_DIR + base + 1];
-          if (d == 0)
-            acc[r][f].set_diff(lo, hi);
-          else
-            acc[r][f].add_diff(lo, hi);
-        }
-      }
-      __syncthreads();
-    }
+    direction_pass<T, 0>(sh, a, s, nb, acc, amax, gamma, eta);
+    direction_pass<T, 1>(sh, a, s, nb, acc, amax, gamma, eta);
+    direction_pass<T, 2>(sh, a, s, nb, acc, amax, gamma, eta);
 
     // update of the owned cells
-    const double lam = dt / a.dx[s];
+    const double lam = s_lam;
+    const float lh = s_lh, ll = s_ll;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       const int c = tid + r * THREADS;
@@ -322,29 +533,38 @@ __global__ void __launch_bounds__(THREADS, 2) stage_kernel(const StageArgs a) {
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         const size_t o = field_offset(s, f) + cell;
-        double ustar = fma(lam, acc[r][f].value(), a.Uin[o]);
-        double v = ustar;
-        if (a.beta != 1.0) {
-          double u0 = a.U0[o];
-          v = fma(a.beta, ustar - u0, u0);
-        }
+        const double u = a.Uin[o];
+        const double u0 = blend ? a.U0[o] : 0.0;
+        const double v = acc[r][f].update(u, u0, lam, lh, ll, a.beta, blend);
         a.Uout[o] = v;
-        bad |= !finite64(v) || (f == F_RHO && !(v > 0.0));
+        bad |= bad64(v, f == F_RHO);
       }
     }
 
-    // max signal speed of this sub-grid
-    double m = warp_max((double)amax);
-    if ((tid & 31) == 0) s_red[tid >> 5] = m;
-    __syncthreads();
-    if (tid < 32) {
-      double v = tid < THREADS / 32 ? s_red[tid] : 0.0;
-      v = warp_max(v);
-      if (tid == 0) {
-        const unsigned long long mask = 0x7fffffffffffffffull;
-        atomicMax(&a.max_speed[0], (unsigned long long)__double_as_longlong(v) & mask);
-        atomicMax(&a.max_speed[1], (unsigned long long)__double_as_longlong(v / a.dx[s]) & mask);
+    // largest face speed of this sub-grid (non-negative values order as their bits)
+    unsigned long long bits;
+    if (sizeof(T) == 4) {
+      unsigned b = __float_as_uint((float)amax) & 0x7fffffffu;
+      b = __reduce_max_sync(0xffffffffu, b);
+      bits = b;
+    } else {
+      bits = (unsigned long long)__double_as_longlong((double)amax) & 0x7fffffffffffffffull;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, bits, o);
+        bits = w > bits ? w : bits;
       }
+    }
+    if ((tid & 31) == 0) s_red[tid >> 5] = bits;
+    __syncthreads();
+    if (tid == 0) {
+      unsigned long long m = 0;
+#pragma unroll
+      for (int w = 0; w < THREADS / 32; ++w) m = s_red[w] > m ? s_red[w] : m;
+      const double v = sizeof(T) == 4 ? (double)__uint_as_float((unsigned)m) : __longlong_as_double((long long)m);
+      const unsigned long long mask = 0x7fffffffffffffffull;
+      atomicMax(&a.max_speed[0], (unsigned long long)__double_as_longlong(v) & mask);
+      atomicMax(&a.max_speed[1], (unsigned long long)__double_as_longlong(v / a.dx[s]) & mask);
     }
     __syncthreads();
   }
@@ -352,28 +572,24 @@ __global__ void __launch_bounds__(THREADS, 2) stage_kernel(const StageArgs a) {
 }
 
 template <typename T>
-size_t stage_smem() {
-  return sizeof(T) * 2 * NF * FACES_DIR;
-}
-
-template <typename T>
 cudaError_t launch(const StageArgs& a, int grid, cudaStream_t st) {
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(stage_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)stage_smem<T>());
+                                         (int)StageSmem<T>::total);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  stage_kernel<T><<<grid, THREADS, stage_smem<T>(), st>>>(a);
+  stage_kernel<T><<<grid, THREADS, StageSmem<T>::total, st>>>(a);
   return cudaGetLastError();
 }
 
 template <typename T>
 int blocks_per_sm() {
   int n = 0;
-  cudaFuncSetAttribute(stage_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stage_smem<T>());
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<T>, THREADS, stage_smem<T>()) != cudaSuccess)
+  cudaFuncSetAttribute(stage_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)StageSmem<T>::total);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<T>, THREADS, StageSmem<T>::total) !=
+      cudaSuccess)
     return 1;
   return n > 0 ? n : 1;
 }

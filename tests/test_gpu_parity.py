@@ -110,7 +110,9 @@ def test_one_stage_matches_oracle(hydro, oracle_mod, cfg, prec):
     ref, ms_o, st = o.stage(U, dt, U0=U0, beta=0.25)
     assert st == 0
     g = hydro.HydroGrid(w.grid, precision=prec)
-    Ud, U0d = _dev(U), _dev(U0)
+    # the GPU input keeps its NaN ghost canaries: the stage kernel gathers the
+    # halos from the neighbours' interiors and must never read a ghost cell
+    Ud, U0d = _dev(w.state()), _dev(U0)
     out = Ud.clone()
     out, ms = g.step(Ud, dt, U0=U0d, beta=0.25, U_out=out)
     g.sync()
@@ -131,16 +133,17 @@ def test_rk3_step_matches_oracle(hydro, oracle_mod, cfg, prec):
     ref, ms_o, st = oracle_mod.Oracle(w.grid).rk3_step(U, dt)
     assert st == 0
     g = hydro.HydroGrid(w.grid, precision=prec)
-    Ud = _dev(U)
+    Ud = _dev(w.state())   # NaN ghosts: never read by the stages
     s1, s2 = torch.empty_like(Ud), torch.empty_like(Ud)
     ids = torch.as_tensor(w.batches.ids, device="cuda")
     ms = g.rk3_step(Ud, dt, s1, s2, ids=ids, batch_offsets=w.batches.offsets)
+    g.fill_ghosts(Ud)      # the step leaves ghosts alone; fill them to compare
     g.sync()
     got = _host(Ud)
     err = field_errors(got, ref)
     assert np.all(err <= TOL[prec]), (err, field_errors(got, ref, plain=True))
     np.testing.assert_allclose(ms.cpu().numpy(), ms_o, rtol=1e-14 if prec == "fp64" else 1e-6)
-    # ghosts were refilled by the step: compare them too (to the stage tolerance)
+    # filled ghosts agree too (to the stage tolerance)
     if prec == "fp64":
         mask = ~np.isnan(ref)
         assert np.array_equal(np.isnan(got), ~mask)
@@ -164,8 +167,8 @@ def test_full_size_sampled_subgrids(hydro, oracle_mod, cfg, prec):
     ref1, _, st = o.stage(U, dt, ids=sample)
     assert st == 0
     g = hydro.HydroGrid(w.grid, precision=prec)
-    Ud = _dev(U)
     del U
+    Ud = _dev(w.state())
     out = torch.empty_like(Ud)
     ids = torch.as_tensor(w.batches.ids, device="cuda")
     out, ms = g.step(Ud, dt, U_out=out, ids=ids, batch_offsets=w.batches.offsets)
