@@ -166,6 +166,26 @@ int hydro_rk3_step_cfl(hydro_handle *h, const hydro_batch *batch, double *U, dou
  *   U DEVICE padded state; d_totals DEVICE double[11]. */
 int hydro_totals(hydro_handle *h, const double *U, double *d_totals, void *stream);
 
+/* Allocation-free variant of hydro_totals for callers that cannot allocate
+ * device memory (no cudaMalloc available to them: an allocator callback, a
+ * framework that owns all device memory, a process with its memory reserved up
+ * front).  The paper has no counterpart of this entry point.
+ *   U         DEVICE padded state of n_subgrids sub-grids (16-byte aligned);
+ *   d_dx      DEVICE double[n_subgrids], the cell width of each sub-grid;
+ *   d_totals  DEVICE double[11], receives the same totals as hydro_totals;
+ *   n_subgrids in [1, HYDRO_TOTALS_NOALLOC_MAX_SUBGRIDS]; a larger value is
+ *             rejected with HYDRO_ERR_INVALID before anything is launched.
+ * Needs no handle and allocates nothing: the partial sums live in one fixed
+ * device array inside the library (HYDRO_TOTALS_NOALLOC_MAX_SUBGRIDS * 11 * 2
+ * doubles, 11.5 MB, held on every GPU that loads the library until the process
+ * exits).  The first call on a device looks up that array's device address
+ * with the device current; make that first call before any stream capture.
+ * All calls share the array: calls whose work overlaps on the GPU (different
+ * streams, or the same stream from several threads without ordering) race and
+ * must not be issued.  Returns HYDRO_OK, HYDRO_ERR_INVALID or HYDRO_ERR_CUDA. */
+#define HYDRO_TOTALS_NOALLOC_MAX_SUBGRIDS 65536
+int hydro_totals_noalloc(const double *U, const double *d_dx, int32_t n_subgrids, double *d_totals, void *stream);
+
 /* Wait for the handle's work on the stream of its last call, then return and
  * clear the device error word: HYDRO_OK, HYDRO_ERR_NONFINITE or
  * HYDRO_ERR_INVALID (bad sub-grid id), or HYDRO_ERR_CUDA. */

@@ -107,3 +107,61 @@ cudaError_t launch_totals(const double* U, int n, const double* dx, double* part
 }
 
 }  // namespace hydro
+
+// ---------------------------------------------------------------------------
+// Allocation-free totals.
+//
+// Some callers cannot allocate device memory: code running where cudaMalloc is
+// unavailable or forbidden, such as inside a host allocator callback, a
+// framework that owns every device allocation, or a process whose memory is
+// fully reserved up front.  hydro_totals_noalloc serves them: the caller passes
+// the state, the cell widths and the output, and the per-sub-grid partial sums
+// live in the fixed array below, which is part of the loaded module (every
+// GPU that loads the library holds its 11.5 MB until the process exits).
+// ---------------------------------------------------------------------------
+
+#include <mutex>
+
+#include "hydro.h"
+
+namespace {
+
+static __device__ __align__(256) double g_noalloc_partial[(size_t)HYDRO_TOTALS_NOALLOC_MAX_SUBGRIDS * hydro::NF * 2];
+
+std::mutex g_noalloc_mu;
+constexpr int kMaxDevices = 64;
+double* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (with that device current) and cached.
+cudaError_t noalloc_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_partial);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" int hydro_totals_noalloc(const double* U, const double* d_dx, int32_t n_subgrids, double* d_totals,
+                                    void* stream) {
+  if (!U || !d_dx || !d_totals) return HYDRO_ERR_INVALID;
+  if (((uintptr_t)U % 16) || ((uintptr_t)d_dx % 8) || ((uintptr_t)d_totals % 8)) return HYDRO_ERR_INVALID;
+  if (n_subgrids < 1 || n_subgrids > HYDRO_TOTALS_NOALLOC_MAX_SUBGRIDS) return HYDRO_ERR_INVALID;
+  double* scratch = nullptr;
+  if (noalloc_scratch(&scratch) != cudaSuccess) return HYDRO_ERR_CUDA;
+  // every partial the final pass reads is written first by the partial pass,
+  // so the stale contents of the shared array never reach the result
+  if (hydro::launch_totals(U, n_subgrids, d_dx, scratch, d_totals, (cudaStream_t)stream) != cudaSuccess)
+    return HYDRO_ERR_CUDA;
+  return HYDRO_OK;
+}

@@ -27,7 +27,9 @@ STATUS = {0: "HYDRO_OK", -1: "HYDRO_ERR_INVALID", -2: "HYDRO_ERR_CUDA", -3: "HYD
 
 # every symbol include/hydro.h declares
 EXPORTS = ("hydro_create", "hydro_step", "hydro_fill_ghosts", "hydro_rk3_step", "hydro_rk3_step_cfl", "hydro_totals",
-           "hydro_sync", "hydro_last_error", "hydro_launch_count", "hydro_set_param", "hydro_destroy")
+           "hydro_totals_noalloc", "hydro_sync", "hydro_last_error", "hydro_launch_count", "hydro_set_param",
+           "hydro_destroy")
+TOTALS_NOALLOC_MAX_SUBGRIDS = 65536
 
 
 class HydroError(RuntimeError):
@@ -66,6 +68,7 @@ def load_library(path: str = LIB_PATH):
     L.hydro_rk3_step.argtypes = [vp, ctypes.POINTER(Batch), vp, vp, vp, dbl, vp, vp]
     L.hydro_rk3_step_cfl.argtypes = [vp, ctypes.POINTER(Batch), vp, vp, vp, dbl, vp, vp, vp]
     L.hydro_totals.argtypes = [vp, vp, vp, vp]
+    L.hydro_totals_noalloc.argtypes = [vp, vp, i32, vp, vp]
     L.hydro_sync.argtypes = [vp]
     L.hydro_last_error.argtypes = [vp]
     L.hydro_last_error.restype = ctypes.c_char_p
