@@ -49,7 +49,7 @@ struct hydro_handle {
   int8_t* d_oct = nullptr;
   unsigned int* d_queue = nullptr;     // [4] work-queue counters
   int* d_err = nullptr;                // device error word
-  double* d_partial = nullptr;         // [n][11][2] totals partials
+  double* d_partial = nullptr;         // totals scratch (per-sub-grid and per-chunk partials)
   double* d_dt = nullptr;              // [1] time step read by graph replays
   unsigned long long* d_ms_tmp = nullptr;  // [2] speeds of RK stages 2 and 3
   cudaStream_t cap_stream = nullptr;
@@ -228,7 +228,7 @@ int hydro_create(const hydro_grid_desc* d, hydro_handle** out) {
   ok = ok && cudaMalloc(&h->d_oct, n) == cudaSuccess;
   ok = ok && cudaMalloc(&h->d_queue, 4 * sizeof(unsigned int)) == cudaSuccess;
   ok = ok && cudaMalloc(&h->d_err, sizeof(int)) == cudaSuccess;
-  ok = ok && cudaMalloc(&h->d_partial, sizeof(double) * n * NF * 2) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->d_partial, sizeof(double) * totals_scratch_doubles(n)) == cudaSuccess;
   ok = ok && cudaMalloc(&h->d_dt, sizeof(double)) == cudaSuccess;
   ok = ok && cudaMalloc(&h->d_ms_tmp, 2 * sizeof(unsigned long long)) == cudaSuccess;
   if (!ok) {
@@ -379,7 +379,7 @@ int hydro_totals(hydro_handle* h, const double* U, double* d_totals, void* strea
   h->last_stream = st;
   cudaError_t e = launch_totals(U, h->n, h->d_dx, h->d_partial, d_totals, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "totals kernel launch");
-  h->launches += 2;
+  h->launches += 3;
   return HYDRO_OK;
 }
 

@@ -62,7 +62,9 @@ cudaError_t launch_stage_mixed(const StageArgs& a, int grid, cudaStream_t st);
 int stage_blocks_per_sm_fp64();
 int stage_blocks_per_sm_mixed();
 cudaError_t launch_ghost_fill(const GhostArgs& a, int threads, cudaStream_t st);
-cudaError_t launch_totals(const double* U, int n, const double* dx, double* partial, double* totals,
+// scratch doubles needed by launch_totals for n sub-grids
+size_t totals_scratch_doubles(int n);
+cudaError_t launch_totals(const double* U, int n, const double* dx, double* scratch, double* totals,
                           cudaStream_t st);
 
 }  // namespace hydro

@@ -1,19 +1,27 @@
 // hydro_totals.cu -- grid totals T_f = sum_s dx_s^3 sum_interior U_f
-// (paper Section V-B.1, diagnostics_actions_type: total mass and other grid
-// sums), compensated and deterministic.
+// (paper Section V-B.1: the diagnostics task forms total mass and other grid
+// sums), exact per sub-grid and deterministic.
 //
-// Pass 1: one CTA per sub-grid; each thread sums two cells per field with
-// Neumaier's compensation, then a fixed-shape tree merges (sum, comp) pairs
-// with an error-free TwoSum; the partial dx^3 * (sum, comp) goes to scratch.
-// Pass 2: one CTA per field sums the partials of all sub-grids in a fixed
-// order (strided per thread, then a fixed tree).  No atomics, so the result
-// is bit-reproducible.
+// GB300 runs FP64 arithmetic at about 2 operations per clock per SM, so the
+// bulk of the summation uses integer operations instead:
+//   pass 1: one warp per (sub-grid, field) reads the 512 interior values,
+//           finds their largest binary exponent E and adds the significands
+//           as signed 128-bit fixed-point numbers with 63 guard bits below the
+//           last bit of a value of exponent E (values more than 63 binades
+//           below E keep their leading bits only).  The integer sum is exact
+//           and independent of order; it becomes a double-double once, scaled
+//           by dx^3, and is stored as the sub-grid's partial (hi, lo);
+//   pass 2: per field and chunk of sub-grids, a Neumaier-compensated sum of
+//           the partials in a fixed order;
+//   pass 3: per field, the chunk sums combined in a fixed order.
+// No atomics anywhere, so the result is bit-reproducible.
 #include "hydro_internal.cuh"
 
 namespace hydro {
 namespace {
 
 constexpr int TT = 256;
+constexpr int CHUNKS = 128;  // sub-grid chunks of pass 2
 
 struct Pair {
   double s, c;
@@ -28,18 +36,21 @@ __device__ __forceinline__ void neumaier(Pair& p, double x) {
   p.s = t;
 }
 
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
+  s = a + b;
+  double bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
+
 __device__ __forceinline__ Pair merge(Pair a, Pair b) {
-  double s = a.s + b.s;
-  double bp = s - a.s;
-  double e = (a.s - (s - bp)) + (b.s - bp);
   Pair r;
-  r.s = s;
+  double e;
+  two_sum(a.s, b.s, r.s, e);
   r.c = (a.c + b.c) + e;
   return r;
 }
 
-__device__ __forceinline__ Pair block_merge(Pair p, Pair* sh) {
-  const int tid = threadIdx.x;
+__device__ __forceinline__ Pair warp_merge(Pair p) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     Pair q;
@@ -47,62 +58,132 @@ __device__ __forceinline__ Pair block_merge(Pair p, Pair* sh) {
     q.c = __shfl_down_sync(0xffffffffu, p.c, o);
     p = merge(p, q);
   }
-  if ((tid & 31) == 0) sh[tid >> 5] = p;
-  __syncthreads();
-  if (tid < 32) {
-    p = tid < TT / 32 ? sh[tid] : Pair{0.0, 0.0};
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      Pair q;
-      q.s = __shfl_down_sync(0xffffffffu, p.s, o);
-      q.c = __shfl_down_sync(0xffffffffu, p.c, o);
-      p = merge(p, q);
-    }
-  }
-  __syncthreads();
-  return p;  // valid in thread 0
+  return p;  // valid in lane 0
 }
 
-__global__ void __launch_bounds__(TT) totals_partial(const double* __restrict__ U, const double* __restrict__ dx,
-                                                     double* __restrict__ partial) {
-  __shared__ Pair sh[TT / 32];
-  const int s = blockIdx.x;
-  const double vol = dx[s] * dx[s] * dx[s];
-  for (int f = 0; f < NF; ++f) {
-    Pair p{0.0, 0.0};
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const int c = threadIdx.x + r * TT;
-      const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
-      neumaier(p, U[field_offset(s, f) + (size_t)(k + NG) * NP2 + (j + NG) * NP + (i + NG)]);
-    }
-    p = block_merge(p, sh);
-    if (threadIdx.x == 0) {
-      partial[((size_t)s * NF + f) * 2 + 0] = vol * p.s;
-      partial[((size_t)s * NF + f) * 2 + 1] = vol * p.c;
-    }
+// exact value of a signed 128-bit integer times 2^e2 as a double-double
+__device__ __forceinline__ void i128_to_dd(__int128 v, int e2, double& hi, double& lo) {
+  const bool neg = v < 0;
+  const unsigned __int128 a = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
+  const double w3 = ldexp((double)(unsigned)(a >> 96), 96 + e2);
+  const double w2 = ldexp((double)(unsigned)(a >> 64), 64 + e2);
+  const double w1 = ldexp((double)(unsigned)(a >> 32), 32 + e2);
+  const double w0 = ldexp((double)(unsigned)a, e2);
+  double s, e1, e2s, e3;
+  two_sum(w3, w2, s, e1);
+  two_sum(s, w1, s, e2s);
+  two_sum(s, w0, s, e3);
+  double l = (e1 + e2s) + e3;
+  hi = s + l;
+  lo = l - (hi - s);
+  if (neg) {
+    hi = -hi;
+    lo = -lo;
   }
 }
 
-__global__ void __launch_bounds__(TT) totals_final(const double* __restrict__ partial, int n,
-                                                   double* __restrict__ totals) {
+__global__ void __launch_bounds__(TT) totals_subgrid(const double* __restrict__ U, const double* __restrict__ dx,
+                                                     int n, double* __restrict__ partial) {
+  const int gw = blockIdx.x * (TT / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (gw >= n * NF) return;
+  const int s = gw / NF, f = gw - s * NF;
+  const double* base = U + field_offset(s, f) + NG * NP2 + NG * NP + NG;
+  unsigned long long b[16];
+  unsigned emax = 1;  // zero and subnormals count as exponent 1
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int c = lane + 32 * r;
+    b[r] = (unsigned long long)__double_as_longlong(base[(c >> 6) * NP2 + ((c >> 3) & 7) * NP + (c & 7)]);
+    const unsigned e = (unsigned)(b[r] >> 52) & 0x7ffu;
+    emax = e > emax ? e : emax;
+  }
+  emax = __reduce_max_sync(0xffffffffu, emax);
+  __int128 acc = 0;
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    unsigned e = (unsigned)(b[r] >> 52) & 0x7ffu;
+    unsigned long long m = b[r] & 0x000fffffffffffffull;
+    if (e)
+      m |= 0x0010000000000000ull;
+    else
+      e = 1;
+    const int sh = 63 - (int)(emax - e);  // bit position of the significand's last bit
+    unsigned __int128 F;
+    if (sh >= 0)
+      F = (unsigned __int128)m << sh;
+    else
+      F = sh > -64 ? (unsigned __int128)(m >> (-sh)) : (unsigned __int128)0;
+    acc += (b[r] >> 63) ? -(__int128)F : (__int128)F;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long lo = __shfl_down_sync(0xffffffffu, (unsigned long long)acc, o);
+    const unsigned long long hi = __shfl_down_sync(0xffffffffu, (unsigned long long)((unsigned __int128)acc >> 64), o);
+    acc += (__int128)(((unsigned __int128)hi << 64) | lo);
+  }
+  if (lane == 0) {
+    double hi, lo;
+    if (emax == 0x7ffu) {  // a non-finite value: make the total non-finite
+      hi = __longlong_as_double(0x7ff8000000000000ll);
+      lo = 0.0;
+    } else {
+      i128_to_dd(acc, (int)emax - 1075 - 63, hi, lo);
+    }
+    const double v = dx[s] * dx[s] * dx[s];
+    const double p = hi * v;
+    const double e = fma(hi, v, -p) + lo * v;
+    partial[((size_t)s * NF + f) * 2 + 0] = p;
+    partial[((size_t)s * NF + f) * 2 + 1] = e;
+  }
+}
+
+// pass 2: block (f, chunk) sums the partials of its contiguous range of sub-grids
+__global__ void __launch_bounds__(TT) totals_chunks(const double* __restrict__ partial, int n,
+                                                    double* __restrict__ chunk) {
   __shared__ Pair sh[TT / 32];
-  const int f = blockIdx.x;
+  const int f = blockIdx.x, ch = blockIdx.y;
+  const int a = (int)((long long)n * ch / CHUNKS), b = (int)((long long)n * (ch + 1) / CHUNKS);
   Pair p{0.0, 0.0};
-  for (int s = threadIdx.x; s < n; s += TT) {
+  for (int s = a + (int)threadIdx.x; s < b; s += TT) {
     neumaier(p, partial[((size_t)s * NF + f) * 2 + 0]);
     neumaier(p, partial[((size_t)s * NF + f) * 2 + 1]);
   }
-  p = block_merge(p, sh);
+  p = warp_merge(p);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = p;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Pair q = sh[0];
+    for (int w = 1; w < TT / 32; ++w) q = merge(q, sh[w]);
+    chunk[((size_t)f * CHUNKS + ch) * 2 + 0] = q.s;
+    chunk[((size_t)f * CHUNKS + ch) * 2 + 1] = q.c;
+  }
+}
+
+// pass 3: one warp per field combines the chunk sums
+__global__ void totals_final(const double* __restrict__ chunk, double* __restrict__ totals) {
+  const int f = blockIdx.x;
+  Pair p{0.0, 0.0};
+  for (int c = (int)threadIdx.x; c < CHUNKS; c += 32) {
+    neumaier(p, chunk[((size_t)f * CHUNKS + c) * 2 + 0]);
+    neumaier(p, chunk[((size_t)f * CHUNKS + c) * 2 + 1]);
+  }
+  p = warp_merge(p);
   if (threadIdx.x == 0) totals[f] = p.s + p.c;
 }
 
 }  // namespace
 
-cudaError_t launch_totals(const double* U, int n, const double* dx, double* partial, double* totals,
+size_t totals_scratch_doubles(int n) { return (size_t)n * NF * 2 + (size_t)NF * CHUNKS * 2; }
+
+cudaError_t launch_totals(const double* U, int n, const double* dx, double* scratch, double* totals,
                           cudaStream_t st) {
-  totals_partial<<<n, TT, 0, st>>>(U, dx, partial);
-  totals_final<<<NF, TT, 0, st>>>(partial, n, totals);
+  double* partial = scratch;
+  double* chunk = scratch + (size_t)n * NF * 2;
+  const int warps = n * NF;
+  totals_subgrid<<<(warps + TT / 32 - 1) / (TT / 32), TT, 0, st>>>(U, dx, n, partial);
+  totals_chunks<<<dim3(NF, CHUNKS), TT, 0, st>>>(partial, n, chunk);
+  totals_final<<<NF, 32, 0, st>>>(chunk, totals);
   return cudaGetLastError();
 }
 
@@ -126,7 +207,8 @@ cudaError_t launch_totals(const double* U, int n, const double* dx, double* part
 
 namespace {
 
-static __device__ __align__(256) double g_noalloc_partial[(size_t)HYDRO_TOTALS_NOALLOC_MAX_SUBGRIDS * hydro::NF * 2];
+static __device__ __align__(256) double g_noalloc_partial[(size_t)HYDRO_TOTALS_NOALLOC_MAX_SUBGRIDS * hydro::NF * 2 +
+                                                          (size_t)hydro::NF * 128 * 2];
 
 std::mutex g_noalloc_mu;
 constexpr int kMaxDevices = 64;
