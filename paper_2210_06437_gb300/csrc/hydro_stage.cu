@@ -302,13 +302,14 @@ __device__ __forceinline__ int offset_dbb(int cd, int c1, int c2) {
 
 // Gather the two halo slabs of direction D of sub-grid s into halo[f][side][l*64 + p]
 // (FP64); l is the slab layer (pencil position m = l or 11 + l), p = t2*8 + t1.
-// Threads 0..191 each own one (l, p) and walk the 11 fields of both slabs;
+// 192 threads each own one (l, p) and walk the 11 fields of both slabs;
 // every copy of a single cell (same level, coarser neighbour, outflow) is an
 // asynchronous cp.async, the 2x2x2 means are computed in place.
 template <int D>
 __device__ __forceinline__ void gather_halo(const double* __restrict__ U, int s, const Nbr& nb, double* halo) {
-  const int q = threadIdx.x;
-  if (q >= HALO) return;
+  // threads 64..255: they have one face task fewer than threads 0..63
+  const int q = (int)threadIdx.x - (THREADS - HALO);
+  if (q < 0) return;
   int l, p;
   if (D == 0) {  // x slabs: consecutive threads walk the 3 contiguous cells of a row
     p = q / 3;
@@ -356,7 +357,7 @@ __device__ __forceinline__ void gather_halo(const double* __restrict__ U, int s,
       c[b1] = c1;
       c[b2] = c2;
       const double* src = U + field_offset(fs, 0) + pad_offset(c[0], c[1], c[2]);
-#pragma unroll 1
+#pragma unroll 4
       for (int f = 0; f < NF; ++f) {
         const double* g = src + (size_t)f * NP3;
         double sum = 0.0;

@@ -465,7 +465,8 @@ _CACHE: Dict[int, Workload] = {}
 
 
 def config(index: int) -> Workload:
-    """Configurations 1..5 of the benchmark ladder (grid, batches, recipe)."""
+    """Configurations 1..5 of the benchmark ladder (grid, batches, recipe); 6 is a
+    reduced copy of 5 for profiling."""
     if index in _CACHE:
         return _CACHE[index]
     if index == 1:
@@ -494,7 +495,16 @@ def config(index: int) -> Workload:
         b = zipf_batches(g.n, 1.1, 1024, rng)
         w = Workload("binary64k", 5, g, b, steps=5, cfl=0.4, precision="both", init=_init_binary,
                      description="65536-leaf octree (levels 0-4), two polytropes, mass ratio 0.7")
+    elif index == 6:
+        # a reduced copy of configuration 5 (same domain, recipe and leaf-batch law,
+        # 4096 leaves, levels 0-4) whose state fits in a few GB: the size used for
+        # hardware-counter profiles of the kernels
+        rng = _rng(index)
+        g = octree_grid((8, 4, 4), (-4.0, -2.0, -2.0), (4.0, 2.0, 2.0), 4, 567, binary_density, rng)
+        b = zipf_batches(g.n, 1.1, 1024, rng)
+        w = Workload("binary4k", 6, g, b, steps=5, cfl=0.4, precision="both", init=_init_binary,
+                     description="4097-leaf reduced binary octree (levels 0-4) for profiling")
     else:
-        raise ValueError("configs are numbered 1..5")
+        raise ValueError("configs are numbered 1..6")
     _CACHE[index] = w
     return w
