@@ -40,6 +40,22 @@ BYTES_PER_CELL_STAGE = 374.0     # read interior + 6 face slabs (1664 cells) + w
 FLOPS_PER_CELL_STAGE = 2200.0    # algorithmic operation count per cell-update of one stage
 GHOST_BYTES_PER_CELL = 396.0     # ghost fill: read + write 1152 face-slab cells per 512 interior cells
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 2 FP64 FMA/clk/SM at the 2070 MHz maximum clock
+# DRAM bytes (read + write) per cell-update of the mixed stage kernel from one ncu capture
+# (profiles/stage_mixed_binary4k.md), valid only for the kernel source it was taken on.
+STAGE_TRAFFIC = {"sha256_prefix": "89bd2f9e4bc72290", "bytes_per_cell": 413.8,
+                 "source": "ncu capture on the 4097-leaf reduced binary octree, scaled by cells"}
+
+
+def stage_traffic_bytes(cells):
+    """Measured DRAM traffic of one mixed stage launch, or None if the kernel
+    source changed since the counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "paper_2210_06437_gb300", "csrc", "hydro_stage.cu")
+    with open(path, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    if not sha.startswith(STAGE_TRAFFIC["sha256_prefix"]):
+        return None
+    return STAGE_TRAFFIC["bytes_per_cell"] * cells
 
 
 def parse():
@@ -113,6 +129,22 @@ class ClockSampler:
 
 def dist_info():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def max_over_ranks(dist, x: float, device) -> float:
+    """Largest value of x over all ranks (the step time of the slowest replica)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(cells_per_rank: int, stages: int, world: int, seconds_max: float) -> float:
+    """Whole-job cell-updates/s: every rank advances its own replica of the
+    workload, and the job takes as long as the slowest rank."""
+    return cells_per_rank * stages * world / seconds_max
 
 
 # ---------------------------------------------------------------------------
@@ -212,12 +244,8 @@ def main():
             pg.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if not pg:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        return float(t.item())
+    def ranks_max(x):
+        return max_over_ranks(pg, x, dev)
 
     U = torch.from_numpy(U_host).to(dev)
     s1, s2 = torch.empty_like(U), torch.empty_like(U)
@@ -226,10 +254,13 @@ def main():
     stream = torch.cuda.current_stream()
     results = {}
 
+    from paper_2210_06437_gb300 import tune as TU
+
     def run_precision(prec, sampler):
         g = HY.HydroGrid(w.grid, precision=prec)
         U.copy_(torch.from_numpy(U_host))
         g.fill_ghosts(U)
+        tuned = TU.tune(g, U, s1, ids=ids, batch_offsets=offs)   # launch shapes, outside the timed region
         ms = torch.zeros(2, dtype=torch.float64, device=dev)
         g.step(U, 0.0, U_out=s1, ids=ids, batch_offsets=offs, max_speed=ms)   # dry stage: first CFL speed
         tot = torch.empty(11, dtype=torch.float64, device=dev)
@@ -254,7 +285,7 @@ def main():
         clocks = sampler.stop() if sampler else None
         launches = g.launches - l0
         g.sync()
-        t_step = max_over_ranks(e0.elapsed_time(e1) / 1e3 / args.steps)
+        t_step = ranks_max(e0.elapsed_time(e1) / 1e3 / args.steps)
         # per-kernel timing for the roofline: stage (beta = 1), ghost fill, totals
         reps = 3
 
@@ -275,7 +306,7 @@ def main():
         g.sync()
         g.close()
         return dict(t_step=t_step, clocks=clocks, launches=launches, t_stage=t_stage, t_ghost=t_ghost, t_tot=t_tot,
-                    totals=tot.cpu().numpy())
+                    totals=tot.cpu().numpy(), tuned=tuned)
 
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     smi_index = vis.split(",")[local] if vis and len(vis.split(",")) > local else str(local)
@@ -315,9 +346,9 @@ def main():
         e1.record(stream)
         barrier()
         g.sync()
-        t_e2e = max_over_ranks(e0.elapsed_time(e1) / 1e3 / args.steps)
+        t_e2e = ranks_max(e0.elapsed_time(e1) / 1e3 / args.steps)
         nbytes = U.numel() * 8
-        e2e = {"value": cells * 3 * world / t_e2e, "unit": "cell-updates/s", "h2d_bytes_per_step": nbytes,
+        e2e = {"value": aggregate_rate(cells, 3, world, t_e2e), "unit": "cell-updates/s", "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes + 88, "ms_per_step": t_e2e * 1e3,
                "api": "HydroGrid.rk3_step_cfl + totals on a pinned host state copied in and out every step"}
         g.close()
@@ -340,10 +371,12 @@ def main():
             pg.destroy_process_group()
         return 0
     r = results["mixed"]
-    value = cells * 3 * world / r["t_step"]
+    value = aggregate_rate(cells, 3, world, r["t_step"])
     t_st = r["t_stage"]
     ach = BYTES_PER_CELL_STAGE * cells / t_st / 1e9
-    roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+    traffic = stage_traffic_bytes(cells)
+    roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": traffic,
+            "traffic_source": STAGE_TRAFFIC["source"] if traffic else "kernel changed since the last capture",
             "kernel": "stage_kernel<float> (mixed RK stage, beta = 1)", "peak_source": hbm_src,
             "bytes_per_cell_update": BYTES_PER_CELL_STAGE, "launch_ms": t_st * 1e3}
     kernels = {
@@ -359,13 +392,14 @@ def main():
                        "cells": cells, "batches": len(offs) - 1, "precision": "mixed",
                        "step": "SSP-RK3 (3 stages with fused halo gather) + totals, device-side CFL dt",
                        "l2": "inputs larger than L2 (%.1f GB state)" % (U.numel() * 8 / 1e9),
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "tuned": r["tuned"]},
             "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": r["launches"], "clocks": r["clocks"]}
     if "fp64" in results:
         f = results["fp64"]
         fl = FLOPS_PER_CELL_STAGE * cells / f["t_stage"] / 1e12
-        line["fp64"] = {"value": cells * 3 * world / f["t_step"], "ms_per_step": f["t_step"] * 1e3,
+        line["fp64"] = {"value": aggregate_rate(cells, 3, world, f["t_step"]), "ms_per_step": f["t_step"] * 1e3,
                         "roofline": {"bound": "alu", "achieved": fl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                                      "frac": fl / FP64_PEAK_TFLOPS, "traffic": None,
                                      "kernel": "stage_kernel<double>", "launch_ms": f["t_stage"] * 1e3,

@@ -320,3 +320,21 @@ def test_host_argument_errors(hydro):
         g.step(Ud, 1e-3, U_out=torch.empty_like(Ud), beta=0.5)  # U0 missing
     with pytest.raises(hydro.HydroError):
         g.step(Ud, 1e-3, U_out=torch.empty_like(Ud), batch_offsets=[0, 5])  # offsets do not reach n
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_autotuned_launch_keeps_parity(hydro, oracle_mod, prec, tmp_path, monkeypatch):
+    from paper_2210_06437_gb300 import tune
+    monkeypatch.setenv("HYDRO_TUNE_CACHE", str(tmp_path / "tune.json"))
+    w = W.config(2)
+    U = _filled(oracle_mod, w)
+    dt, _ = _dt(oracle_mod, w, U)
+    g = hydro.HydroGrid(w.grid, precision=prec)
+    Ud = _dev(U)
+    best = tune.tune(g, Ud, torch.empty_like(Ud), reps=2)
+    assert set(best) == set(tune.SPACE)
+    assert tune.load_cache()            # the result was cached
+    out, _ = g.step(Ud, dt, U_out=torch.empty_like(Ud))
+    g.sync()
+    ref, _, _ = oracle_mod.Oracle(w.grid).stage(U, dt)
+    assert np.all(field_errors(_host(out), ref) <= TOL[prec])
