@@ -44,6 +44,7 @@ struct hydro_handle {
   int occupancy = 1;  // resident stage CTAs per SM for this precision
   int ghost_threads = 256;
   double* d_dx = nullptr;
+  double* d_inv_dx = nullptr;
   int32_t* d_nb = nullptr;
   int8_t* d_rel = nullptr;
   int8_t* d_oct = nullptr;
@@ -87,6 +88,7 @@ void free_all(hydro_handle* h) {
   for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
   h->graphs.clear();
   cudaFree(h->d_dx);
+  cudaFree(h->d_inv_dx);
   cudaFree(h->d_nb);
   cudaFree(h->d_rel);
   cudaFree(h->d_oct);
@@ -147,6 +149,7 @@ int enqueue_stage(hydro_handle* h, const int32_t* ids, int n_items, const double
   a.n_items = n_items;
   a.n_sub = h->n;
   a.dx = h->d_dx;
+  a.inv_dx = h->d_inv_dx;
   a.nb = h->d_nb;
   a.rel = h->d_rel;
   a.oct = h->d_oct;
@@ -223,6 +226,7 @@ int hydro_create(const hydro_grid_desc* d, hydro_handle** out) {
   }
   bool ok = true;
   ok = ok && cudaMalloc(&h->d_dx, sizeof(double) * n) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->d_inv_dx, sizeof(double) * n) == cudaSuccess;
   ok = ok && cudaMalloc(&h->d_nb, sizeof(int32_t) * n * 24) == cudaSuccess;
   ok = ok && cudaMalloc(&h->d_rel, n * 6) == cudaSuccess;
   ok = ok && cudaMalloc(&h->d_oct, n) == cudaSuccess;
@@ -238,6 +242,11 @@ int hydro_create(const hydro_grid_desc* d, hydro_handle** out) {
     return HYDRO_ERR_NOMEM;
   }
   ok = ok && cudaMemcpy(h->d_dx, d->dx, sizeof(double) * n, cudaMemcpyHostToDevice) == cudaSuccess;
+  if (ok) {
+    std::vector<double> inv(n);
+    for (int s = 0; s < n; ++s) inv[s] = 1.0 / d->dx[s];
+    ok = cudaMemcpy(h->d_inv_dx, inv.data(), sizeof(double) * n, cudaMemcpyHostToDevice) == cudaSuccess;
+  }
   ok = ok && cudaMemcpy(h->d_nb, d->neighbor, sizeof(int32_t) * n * 24, cudaMemcpyHostToDevice) == cudaSuccess;
   ok = ok && cudaMemcpy(h->d_rel, d->neighbor_rel, n * 6, cudaMemcpyHostToDevice) == cudaSuccess;
   ok = ok && cudaMemcpy(h->d_oct, d->octant, n, cudaMemcpyHostToDevice) == cudaSuccess;

@@ -34,6 +34,7 @@ struct StageArgs {
   int32_t n_items;
   int32_t n_sub;
   const double* dx;
+  const double* inv_dx;  // [n] 1/dx
   const int32_t* nb;   // [n][6][4] face neighbours
   const int8_t* rel;   // [n][6]
   const int8_t* oct;   // [n]

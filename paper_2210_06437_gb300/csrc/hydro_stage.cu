@@ -242,6 +242,51 @@ struct Acc<double> {
   }
 };
 
+// RN64(s + c) for a float pair with |c| <= ulp(s)/2, by integer operations.
+// The exact sum has the bits of s followed, after a gap, by those of c; it is
+// exact in FP64 when c starts at most 29 binades below the end of s, and is
+// rounded to nearest (ties to even) otherwise.
+__device__ __forceinline__ double pair_to_f64(float s, float c) {
+  const unsigned bs = __float_as_uint(s), bc = __float_as_uint(c);
+  const int es = (int)((bs >> 23) & 0xffu), ec = (int)((bc >> 23) & 0xffu);
+  if (es == 0 || es == 0xff || ec == 0) return f32_to_f64(s);  // zero/subnormal/non-finite s, or c ~ 0
+  // significands as integers in units of 2^(es-150) (s) and 2^(ec-150) (c)
+  const unsigned long long ms = (unsigned long long)((bs & 0x7fffffu) | 0x800000u);
+  const unsigned long long mc = (unsigned long long)((bc & 0x7fffffu) | 0x800000u);
+  const int gap = es - ec;  // >= 24 for a normalized pair
+  // value / 2^(es-150) = ms + sign*mc*2^-gap; scale by 2^39 to keep 63 bits:
+  // A = ms << 39 (at most 2^63), B = mc << 39 >> gap (with sticky bit)
+  unsigned long long A = ms << 39;
+  unsigned long long B;
+  if (gap >= 63) {
+    B = 1;  // only a sticky bit survives
+  } else {
+    const unsigned long long full = mc << 39;
+    B = full >> gap;
+    if ((B << gap) != full) B |= 1;  // sticky
+  }
+  const bool same = ((bs ^ bc) & 0x80000000u) == 0;
+  unsigned long long M = same ? A + B : A - B;  // A > B always
+  int e = es;  // M is in units of 2^(es-150-39) = 2^(es-189)
+  // normalize M so that its leading bit is bit 63 or 62
+  const int lz = __clzll((long long)M);
+  M <<= lz;
+  e -= lz;  // now M in units of 2^(e-189), leading bit at 63
+  // round to 53 bits: keep bits 63..11, rounding bits 10..0
+  const unsigned long long rem = M & 0x7ffull;
+  unsigned long long m53 = M >> 11;
+  if (rem > 0x400ull || (rem == 0x400ull && (m53 & 1ull))) ++m53;
+  if (m53 >> 53) {  // rounding carried out
+    m53 >>= 1;
+    ++e;
+  }
+  // value = m53 * 2^(e-189+11) with m53 in [2^52, 2^53): biased FP64 exponent
+  const long long e64 = (long long)e - 189 + 11 + 52 + 1023;
+  const unsigned long long bits =
+      ((unsigned long long)(bs & 0x80000000u) << 32) | ((unsigned long long)e64 << 52) | (m53 & 0xfffffffffffffull);
+  return __longlong_as_double((long long)bits);
+}
+
 // Float pair (s + c) holding the running flux-difference sum: the difference
 // of a direction's two face fluxes is formed exactly first (so a mirrored cell,
 // which sees the two terms swapped and negated, gets the same pair), then added
@@ -257,14 +302,13 @@ struct Acc<float> {
     s = t;
     c = __fadd_rn(c, __fadd_rn(e, e2));
   }
-  // lam dU formed as a float pair (lh + ll)(s + c), then added in FP64.
-  __device__ __forceinline__ double update(double u, double u0, double, float lh, float ll, double beta,
+  // dU = RN64(s + c) (integer assembly), then U* = fma(lam, dU, u): one FP64
+  // operation in stage 1, three with the blend.
+  __device__ __forceinline__ double update(double u, double u0, double lam, float, float, double beta,
                                            bool blend) const {
-    float p = __fmul_rn(lh, s);
-    float e = fmaf(lh, s, -p);
-    e = fmaf(lh, c, e);
-    e = fmaf(ll, s, e);
-    double us = (u + f32_to_f64(p)) + f32_to_f64(e);
+    float hi = __fadd_rn(s, c);                 // renormalize: |lo| <= ulp(hi)/2
+    float lo = __fadd_rn(c, -__fadd_rn(hi, -s));
+    double us = fma(lam, pair_to_f64(hi, lo), u);
     return blend ? fma(beta, us - u0, u0) : us;
   }
 };
@@ -395,15 +439,63 @@ struct Shared {
   T* fsr;        // [NF][576] right face states
 };
 
+// Work item and what its processing needs: sub-grid id (-1: queue exhausted,
+// -2: bad id), neighbour table, dt/dx and 1/dx.
+struct Meta {
+  Nbr nb;
+  int item;
+  int s;
+  double lam, idx;
+  float lh, ll;
+};
+
+// Warp 7 (threads 224..255, one PPM task fewer than threads 0..191) takes the
+// next work item from the queue and reads its neighbour table into m.
+__device__ __forceinline__ void prefetch_meta(const StageArgs& a, double dt, Meta& m) {
+  const int lane = threadIdx.x & 31;
+  int item = 0;
+  if (lane == 0) item = (int)atomicAdd(a.queue, 1u);
+  item = __shfl_sync(0xffffffffu, item, 0);
+  int s = -1;
+  if (item < a.n_items) {
+    s = a.ids[item];
+    if (s < 0 || s >= a.n_sub) {
+      if (lane == 0) atomicOr(a.err, ERRBIT_BAD_ID);
+      s = -2;
+    }
+  }
+  if (s >= 0) {
+    if (lane < 24) m.nb.id[lane >> 2][lane & 3] = a.nb[(size_t)s * 24 + lane];
+    if (lane < 6) m.nb.rel[lane] = a.rel[s * 6 + lane];
+    if (lane == 0) {
+      m.nb.oct = a.oct[s];
+      const double idx = a.inv_dx[s];
+      const double lam = dt * idx;
+      m.lam = lam;
+      m.idx = idx;
+      m.lh = (float)lam;
+      m.ll = (float)(lam - (double)(float)lam);
+    }
+  }
+  if (lane == 0) {
+    m.item = item;
+    m.s = s;
+  }
+}
+
 // One direction of the stage: PPM of every (field, pencil), the next
-// direction's halo gather (issued once the halo buffer is free), the face
-// fluxes and the flux differences of the two owned cells.
+// direction's halo gather (issued once the halo buffer is free; after z, the
+// next sub-grid's x halo), the face fluxes and the flux differences of the two
+// owned cells.  During z, warp 7 also prefetches the next work item.
 template <typename T, int D>
-__device__ __forceinline__ void direction_pass(const Shared<T>& sh, const StageArgs& a, int s, const Nbr& nb,
-                                               Acc<T> (&acc)[2][NF], T& amax, T gamma, T eta) {
+__device__ __forceinline__ void direction_pass(const Shared<T>& sh, const StageArgs& a, const Meta& cur,
+                                               Meta& nxt, double dt, Acc<T> (&acc)[2][NF], T& amax, T gamma,
+                                               T eta) {
   const int tid = threadIdx.x;
-  cp_async_wait_all();
-  __syncthreads();  // this direction's halo (and, for x, the interior tile) is in place
+  if (D > 0) {
+    cp_async_wait_all();
+    __syncthreads();  // this direction's halo is in place
+  }
   // A: PPM, one (field, pencil) task per iteration
 #pragma unroll 1
   for (int task = tid; task < NF * NPEN; task += THREADS) {
@@ -424,9 +516,13 @@ __device__ __forceinline__ void direction_pass(const Shared<T>& sh, const StageA
       sh.fsr[f * FACES_DIR + p * NFACE + m] = ur[m];
     }
   }
+  if (D == 2 && (tid >> 5) == THREADS / 32 - 1) prefetch_meta(a, dt, nxt);
   __syncthreads();
-  // the halo buffer is free: start gathering the next direction's slabs
-  if (D < 2) gather_halo<(D < 2 ? D + 1 : 2)>(a.Uin, s, nb, sh.halo);
+  // the halo buffer is free: start gathering the next slabs
+  if (D < 2)
+    gather_halo<(D < 2 ? D + 1 : 2)>(a.Uin, cur.s, cur.nb, sh.halo);
+  else if (nxt.s >= 0)
+    gather_halo<0>(a.Uin, nxt.s, nxt.nb, sh.halo);
   // B: one face per iteration
 #pragma unroll 1
   for (int fc = tid; fc < FACES_DIR; fc += THREADS) {
@@ -470,10 +566,7 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(
   sh.halo = reinterpret_cast<double*>(smem_raw + StageSmem<T>::interior);
   sh.fsl = reinterpret_cast<T*>(smem_raw + StageSmem<T>::interior + StageSmem<T>::halo);
   sh.fsr = sh.fsl + NF * FACES_DIR;
-  __shared__ int s_item;
-  __shared__ Nbr s_nb;
-  __shared__ double s_lam;
-  __shared__ float s_lh, s_ll;
+  __shared__ Meta s_meta[2];
   __shared__ unsigned long long s_red[THREADS / 32];
 
   const int tid = threadIdx.x;
@@ -482,25 +575,24 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(
   const bool blend = a.beta != 1.0;
   int bad = 0;
 
+  // prologue: the first work item, its neighbour table and x halo
+  if ((tid >> 5) == THREADS / 32 - 1) prefetch_meta(a, dt, s_meta[0]);
+  __syncthreads();
+  if (s_meta[0].s >= 0) gather_halo<0>(a.Uin, s_meta[0].s, s_meta[0].nb, sh.halo);
+  int par = 0;
   for (;;) {
-    if (tid == 0) s_item = (int)atomicAdd(a.queue, 1u);
-    __syncthreads();
-    const int item = s_item;
+    const Meta& cur = s_meta[par];
+    Meta& nxt = s_meta[par ^ 1];
+    const int item = cur.item;
     if (item >= a.n_items) break;
-    const int s = a.ids[item];
-    if (s < 0 || s >= a.n_sub) {
-      if (tid == 0) atomicOr(a.err, ERRBIT_BAD_ID);
+    const int s = cur.s;
+    if (s < 0) {  // bad id: skip it
       __syncthreads();
+      if ((tid >> 5) == THREADS / 32 - 1) prefetch_meta(a, dt, nxt);
+      __syncthreads();
+      if (nxt.s >= 0) gather_halo<0>(a.Uin, nxt.s, nxt.nb, sh.halo);
+      par ^= 1;
       continue;
-    }
-    if (tid < 24) s_nb.id[tid >> 2][tid & 3] = a.nb[(size_t)s * 24 + tid];
-    if (tid < 6) s_nb.rel[tid] = a.rel[s * 6 + tid];
-    if (tid == 0) {
-      s_nb.oct = a.oct[s];
-      const double lam = dt / a.dx[s];
-      s_lam = lam;
-      s_lh = (float)lam;
-      s_ll = (float)(lam - (double)(float)lam);
     }
     // interior of all fields, FP64 -> T
     const double* Us = a.Uin + field_offset(s, 0);
@@ -513,19 +605,18 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(
 #pragma unroll
       for (int f = 0; f < NF; ++f) sh.tile[f * ISZ + t] = Arith<T>::from64(Us[(size_t)f * NP3 + g]);
     }
-    __syncthreads();  // s_nb and lambda ready
-    const Nbr& nb = s_nb;
-    gather_halo<0>(a.Uin, s, nb, sh.halo);
+    cp_async_wait_all();
+    __syncthreads();  // interior tile and x halo in place
 
     Acc<T> acc[2][NF];
     T amax = T(0);
-    direction_pass<T, 0>(sh, a, s, nb, acc, amax, gamma, eta);
-    direction_pass<T, 1>(sh, a, s, nb, acc, amax, gamma, eta);
-    direction_pass<T, 2>(sh, a, s, nb, acc, amax, gamma, eta);
+    direction_pass<T, 0>(sh, a, cur, nxt, dt, acc, amax, gamma, eta);
+    direction_pass<T, 1>(sh, a, cur, nxt, dt, acc, amax, gamma, eta);
+    direction_pass<T, 2>(sh, a, cur, nxt, dt, acc, amax, gamma, eta);
 
     // update of the owned cells
-    const double lam = s_lam;
-    const float lh = s_lh, ll = s_ll;
+    const double lam = cur.lam;
+    const float lh = cur.lh, ll = cur.ll;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       const int c = tid + r * THREADS;
@@ -544,7 +635,7 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(
 
     // largest face speed of this sub-grid (non-negative values order as their bits)
     unsigned long long bits;
-    if (sizeof(T) == 4) {
+    if constexpr (sizeof(T) == 4) {
       unsigned b = __float_as_uint((float)amax) & 0x7fffffffu;
       b = __reduce_max_sync(0xffffffffu, b);
       bits = b;
@@ -562,13 +653,18 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(
       unsigned long long m = 0;
 #pragma unroll
       for (int w = 0; w < THREADS / 32; ++w) m = s_red[w] > m ? s_red[w] : m;
-      const double v = sizeof(T) == 4 ? (double)__uint_as_float((unsigned)m) : __longlong_as_double((long long)m);
+      double v;
+      if constexpr (sizeof(T) == 4)
+        v = (double)__uint_as_float((unsigned)m);
+      else
+        v = __longlong_as_double((long long)m);
       const unsigned long long mask = 0x7fffffffffffffffull;
       atomicMax(&a.max_speed[0], (unsigned long long)__double_as_longlong(v) & mask);
-      atomicMax(&a.max_speed[1], (unsigned long long)__double_as_longlong(v / a.dx[s]) & mask);
+      atomicMax(&a.max_speed[1], (unsigned long long)__double_as_longlong(v * cur.idx) & mask);
     }
-    __syncthreads();
+    par ^= 1;
   }
+  cp_async_wait_all();
   if (bad) atomicOr(a.err, ERRBIT_NONFINITE);
 }
 
