@@ -1,0 +1,160 @@
+"""Partition of an octree grid over ranks, with proxy slots and a halo exchange.
+
+Sub-grids are numbered in Morton order, so each rank owns one contiguous
+range of leaves, balanced by leaf count.  A rank's local state holds its owned
+sub-grids first and then one proxy slot per remote sub-grid that an owned
+sub-grid reads across a face (same-level, coarser or finer neighbour).  Before
+every RK stage, ``exchange`` copies the current interiors of those remote
+sub-grids into the proxy slots (point-to-point send/recv; the only data-path
+communication the sharded step needs); the stage then runs on the local grid
+exactly as on a single domain, because it reads neighbours' interiors only.
+The maximum signal speed is combined with ``allreduce(MAX)``.
+
+Index logic and data movement only; no solver arithmetic.  One process per
+GPU would run the CUDA library on the local grid; on CPU ranks the same plan
+drives the oracle, which is how the tests validate it.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Dict, List
+
+import numpy as np
+
+from .workloads import Grid, NF, NG, NP, NX
+
+
+@dataclasses.dataclass
+class Partition:
+    rank: int
+    world: int
+    owned: np.ndarray      # global ids owned by this rank (contiguous Morton range)
+    proxies: np.ndarray    # global ids of remote sub-grids held as proxy slots
+    local: Grid            # descriptor of owned + proxy slots, local numbering
+    owner: np.ndarray      # rank owning each global sub-grid
+    send: Dict[int, np.ndarray]  # rank -> global ids this rank sends there each stage
+    recv: Dict[int, np.ndarray]  # rank -> global ids received from there (in proxy order)
+
+    @property
+    def n_owned(self) -> int:
+        return len(self.owned)
+
+    def local_index(self, gids: np.ndarray) -> np.ndarray:
+        """Local slot of global ids (owned or proxy)."""
+        lut = self._lut
+        out = lut[np.asarray(gids)]
+        assert np.all(out >= 0)
+        return out
+
+
+def ranges(n: int, world: int) -> List[range]:
+    """Contiguous, count-balanced ranges of the Morton-ordered leaves."""
+    return [range(n * r // world, n * (r + 1) // world) for r in range(world)]
+
+
+def _needed(grid: Grid, ids: np.ndarray) -> np.ndarray:
+    """Global ids read across the faces of the sub-grids ids."""
+    nb = grid.neighbor[ids]                       # [m,6,4]
+    rel = grid.neighbor_rel[ids]                  # [m,6]
+    used = np.zeros_like(nb, dtype=bool)
+    used[:, :, 0] = nb[:, :, 0] >= 0
+    used[:, :, 1:] = (rel == 1)[:, :, None]
+    return np.unique(nb[used])
+
+
+def build(grid: Grid, rank: int, world: int) -> Partition:
+    rs = ranges(grid.n, world)
+    owner = np.empty(grid.n, np.int32)
+    for r, rg in enumerate(rs):
+        owner[rg.start:rg.stop] = r
+    owned = np.arange(rs[rank].start, rs[rank].stop, dtype=np.int32)
+    need = _needed(grid, owned)
+    proxies = need[owner[need] != rank].astype(np.int32)
+    gids = np.concatenate([owned, proxies])
+    lut = np.full(grid.n, -1, np.int64)
+    lut[gids] = np.arange(len(gids))
+    m = len(gids)
+    nb = np.full((m, 6, 4), -1, np.int32)
+    rel = np.zeros((m, 6), np.int8)
+    o_nb = grid.neighbor[owned]
+    nb[:len(owned)] = np.where(o_nb >= 0, lut[np.maximum(o_nb, 0)], -1)
+    rel[:len(owned)] = grid.neighbor_rel[owned]
+    # proxy slots are never advanced; their descriptor rows only need to be valid
+    local = Grid(n=m, dx=grid.dx[gids].copy(), origin=grid.origin[gids].copy(), level=grid.level[gids].copy(),
+                 octant=grid.octant[gids].copy(), neighbor=nb, neighbor_rel=rel, periodic=grid.periodic,
+                 gamma=grid.gamma, de_switch=grid.de_switch)
+    # symmetric plan: rank r sends to rank q the sub-grids q holds as proxies
+    send, recv = {}, {}
+    for q in range(world):
+        if q == rank:
+            continue
+        qn = _needed(grid, np.arange(rs[q].start, rs[q].stop, dtype=np.int32))
+        s = qn[owner[qn] == rank]
+        if len(s):
+            send[q] = s.astype(np.int32)
+        rcv = proxies[owner[proxies] == q]
+        if len(rcv):
+            recv[q] = rcv
+    p = Partition(rank=rank, world=world, owned=owned, proxies=proxies, local=local, owner=owner, send=send,
+                  recv=recv)
+    p._lut = lut
+    return p
+
+
+INTERIOR = (slice(None), slice(None), slice(NG, NG + NX), slice(NG, NG + NX), slice(NG, NG + NX))
+
+
+def scatter_global(p: Partition, U_global: np.ndarray) -> np.ndarray:
+    """Local state (owned + proxies) cut from a global padded state."""
+    return np.ascontiguousarray(U_global[np.concatenate([p.owned, p.proxies])])
+
+
+def exchange(p: Partition, U_local, dist) -> None:
+    """Fill the proxy interiors of U_local (numpy or torch, [m,11,14,14,14])
+    with the owners' current interiors.  dist is torch.distributed."""
+    import torch
+    is_np = isinstance(U_local, np.ndarray)
+    T = torch.from_numpy(U_local) if is_np else U_local
+    reqs, bufs = [], []
+    for q, gids in sorted(p.send.items()):
+        li = torch.as_tensor(p.local_index(gids), device=T.device)
+        buf = T[li][:, :, NG:NG + NX, NG:NG + NX, NG:NG + NX].contiguous()
+        bufs.append(buf)
+        reqs.append(dist.isend(buf, dst=q))
+    recvs = []
+    for q, gids in sorted(p.recv.items()):
+        buf = torch.empty((len(gids), NF, NX, NX, NX), dtype=T.dtype, device=T.device)
+        recvs.append((gids, buf))
+        reqs.append(dist.irecv(buf, src=q))
+    for r in reqs:
+        r.wait()
+    for gids, buf in recvs:
+        li = torch.as_tensor(p.local_index(gids), device=T.device)
+        T[li, :, NG:NG + NX, NG:NG + NX, NG:NG + NX] = buf
+
+
+def allreduce_max(x: np.ndarray, dist) -> np.ndarray:
+    import torch
+    t = torch.as_tensor(np.asarray(x, np.float64).copy())
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.numpy()
+
+
+def gather_owned(p: Partition, U_local: np.ndarray, dist, root: int = 0):
+    """Owned interiors of every rank assembled on root as a global array
+    (other ranks return None)."""
+    import torch
+    mine = torch.from_numpy(np.ascontiguousarray(U_local[:p.n_owned][INTERIOR]))
+    if p.rank != root:
+        dist.send(mine, dst=root)
+        return None
+    out = [None] * p.world
+    out[root] = mine
+    for q in range(p.world):
+        if q == root:
+            continue
+        n_q = len(ranges(len(p.owner), p.world)[q])
+        buf = torch.empty((n_q, NF, NX, NX, NX), dtype=torch.float64)
+        dist.recv(buf, src=q)
+        out[q] = buf
+    return torch.cat(out).numpy()
