@@ -2,10 +2,11 @@
 """Benchmark of the batched octree hydro step on GB300.
 
 One step = one SSP-RK3 time step of the whole hot path over the workload:
-three RK stages (PPM reconstruction, central-upwind flux, maximum-speed
-reduction, flux-divergence update) with a ghost fill after each stage, the
-time step chosen on the device from the previous step's CFL speed, and the
-conservation totals.  The metric is interior cell-updates per second
+three RK stages (halo gather from the neighbours' interiors, PPM
+reconstruction, central-upwind flux, maximum-speed reduction, flux-divergence
+update), the time step chosen on the device from the previous step's CFL
+speed, and the conservation totals; the mixed path also writes the FP32 shadow
+of the state once per step (each stage then writes its output's shadow).  The metric is interior cell-updates per second
 (cells x 3 stages / step time).
 
 Workload (default): the largest configuration, a 65536-leaf octree of 8^3
@@ -39,6 +40,7 @@ METRIC = "hydro cell-updates/s (FP64 vs FP32/FP64-mixed batched) at stated error
 BYTES_PER_CELL_STAGE = 374.0     # read interior + 6 face slabs (1664 cells) + write interior (512), 88 B per cell
 FLOPS_PER_CELL_STAGE = 2200.0    # algorithmic operation count per cell-update of one stage
 GHOST_BYTES_PER_CELL = 396.0     # ghost fill: read + write 1152 face-slab cells per 512 interior cells
+SHADOW_BYTES_PER_CELL = 132.0    # FP32 shadow: read 88 B of FP64 interior, write 44 B
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 2 FP64 FMA/clk/SM at the 2070 MHz maximum clock
 # DRAM bytes (read + write) per cell-update of the mixed stage kernel from one ncu capture
 # (profiles/stage_mixed_binary4k.md), valid only for the kernel source it was taken on.
@@ -300,13 +302,23 @@ def main():
             torch.cuda.synchronize()
             return a.elapsed_time(b) / 1e3 / reps
 
-        t_stage = timed(lambda: g.step(U, 1e-9, U_out=s1, ids=ids, batch_offsets=offs, max_speed=s2[0, 0, 0, 0, :2]))
+        ms2 = torch.zeros(2, dtype=torch.float64, device=dev)
+        t_shadow = None
+        if prec == "mixed":
+            # the stage kernel alone, as the RK3 graph launches it (shadow in, shadow out)
+            S_in, S_out = g.shadow(U), g.empty_shadow()
+            t_stage = timed(lambda: g.step_shadowed(U, S_in, 1e-9, U_out=s1, S_out=S_out, ids=ids,
+                                                    batch_offsets=offs, max_speed=ms2))
+            t_shadow = timed(lambda: g.shadow(U, S_in))
+            del S_in, S_out
+        else:
+            t_stage = timed(lambda: g.step(U, 1e-9, U_out=s1, ids=ids, batch_offsets=offs, max_speed=ms2))
         t_ghost = timed(lambda: g.fill_ghosts(s1))
         t_tot = timed(lambda: g.totals(U, out=tot))
         g.sync()
         g.close()
         return dict(t_step=t_step, clocks=clocks, launches=launches, t_stage=t_stage, t_ghost=t_ghost, t_tot=t_tot,
-                    totals=tot.cpu().numpy(), tuned=tuned)
+                    t_shadow=t_shadow, totals=tot.cpu().numpy(), tuned=tuned)
 
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     smi_index = vis.split(",")[local] if vis and len(vis.split(",")) > local else str(local)
@@ -377,10 +389,11 @@ def main():
     traffic = stage_traffic_bytes(cells)
     roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": traffic,
             "traffic_source": STAGE_TRAFFIC["source"] if traffic else "kernel changed since the last capture",
-            "kernel": "stage_kernel<float> (mixed RK stage, beta = 1)", "peak_source": hbm_src,
+            "kernel": "stage_kernel<float> (mixed RK stage, beta = 1, shadow in and out)", "peak_source": hbm_src,
             "bytes_per_cell_update": BYTES_PER_CELL_STAGE, "launch_ms": t_st * 1e3}
     kernels = {
-        "stage_mixed_ms": t_st * 1e3, "ghost_fill_ms": r["t_ghost"] * 1e3, "totals_ms": r["t_tot"] * 1e3,
+        "stage_mixed_ms": t_st * 1e3, "shadow_ms": r["t_shadow"] * 1e3, "ghost_fill_ms": r["t_ghost"] * 1e3,
+        "totals_ms": r["t_tot"] * 1e3, "shadow_gbs": SHADOW_BYTES_PER_CELL * cells / r["t_shadow"] / 1e9,
         "ghost_fill_gbs": GHOST_BYTES_PER_CELL * cells / r["t_ghost"] / 1e9,
         "stage_share_of_step": 3 * t_st / r["t_step"], "totals_share_of_step": r["t_tot"] / r["t_step"],
         "note": "the stage kernel gathers halos from neighbour interiors; the ghost-fill kernel is not part of "
@@ -390,7 +403,7 @@ def main():
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": "%s (config %d): %s" % (w.name, w.index, w.description), "subgrids": w.grid.n,
                        "cells": cells, "batches": len(offs) - 1, "precision": "mixed",
-                       "step": "SSP-RK3 (3 stages with fused halo gather) + totals, device-side CFL dt",
+                       "step": "SSP-RK3 (FP32 shadow + 3 stages with fused halo gather) + totals, device-side CFL dt",
                        "l2": "inputs larger than L2 (%.1f GB state)" % (U.numel() * 8 / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "tuned": r["tuned"]},

@@ -124,9 +124,33 @@ int hydro_create(const hydro_grid_desc *desc, hydro_handle **out);
  *   d_max_speed  DEVICE double[2], overwritten with the maximum over the
  *          listed sub-grids and their faces of max(a+, -a-) (the CFL signal
  *          speed of the INPUT state) and of that speed divided by dx_s;
- *   stream cudaStream_t (NULL = legacy default stream). */
+ *   stream cudaStream_t (NULL = legacy default stream).
+ * A mixed-precision handle first writes the FP32 shadow of U_in (hydro_shadow,
+ * all sub-grids, into the handle's own buffer); hydro_step_shadowed skips that
+ * pass when the caller already holds the shadow. */
 int hydro_step(hydro_handle *h, const hydro_batch *batch, const double *U_in, const double *U0, double beta,
                double dt, double *U_out, double *d_max_speed, void *stream);
+
+/* FP32 shadow of the interiors of every sub-grid of U, the input the
+ * mixed-precision reconstruction reads (the paper has no counterpart; it is
+ * the GB300 layout of the float32 reconstruction inputs):
+ *   S[s][f][(k*8 + j)*8 + i] = U[s][f][k+3][j+3][i+3] rounded to the nearest
+ *   float32 (ties away from zero; magnitudes below the float32 normal range
+ *   become signed zero, finite values beyond it infinity).
+ *   U DEVICE padded state; S DEVICE float[n_subgrids][11][512], 16-byte
+ *   aligned.  Works with either precision of handle. */
+int hydro_shadow(hydro_handle *h, const double *U, float *S, void *stream);
+
+/* hydro_step for a mixed-precision handle whose caller keeps the shadows:
+ *   S_in   DEVICE shadow of U_in (as hydro_shadow writes it) for every
+ *          sub-grid; the reconstruction reads it in place of U_in's interiors
+ *          (finer neighbours' 2x2x2 means are still formed from U_in);
+ *   S_out  DEVICE shadow buffer or NULL; when given, the shadow of U_out is
+ *          written for the listed sub-grids; must not alias S_in.
+ * Other arguments as hydro_step.  A FP64 handle returns HYDRO_ERR_STATE. */
+int hydro_step_shadowed(hydro_handle *h, const hydro_batch *batch, const double *U_in, const float *S_in,
+                        const double *U0, double beta, double dt, double *U_out, float *S_out, double *d_max_speed,
+                        void *stream);
 
 /* Fill the six face ghost slabs (3 layers each) of every sub-grid of U from
  * the neighbours' interiors (Section VI: hydro boundary exchange): copy from a
@@ -139,7 +163,11 @@ int hydro_fill_ghosts(hydro_handle *h, double *U, void *stream);
 /* One SSP-RK3 step (three stages, Section I: three hydro iterations per
  * time-step), replayed from a CUDA graph that the handle captures on first use
  * for each (batch, U, scratch) combination.  The stages gather their halos
- * from the neighbours' interiors, so no ghost fill runs between stages.
+ * from the neighbours' interiors, so no ghost fill runs between stages.  The
+ * batch must list every sub-grid once (n_items == n_subgrids, any order and
+ * batch cut), since later stages read the neighbours' intermediate states;
+ * otherwise HYDRO_ERR_INVALID.  Mixed precision: the graph writes the shadow
+ * of U once and each stage then writes its output's shadow for the next.
  *   U        DEVICE padded state; its interior is overwritten by the new state
  *            (ghost cells are neither read nor updated: call hydro_fill_ghosts
  *            when they are wanted);

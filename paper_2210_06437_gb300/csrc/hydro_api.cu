@@ -5,6 +5,9 @@
 // counters, error word, totals partials, per-stage speed scratch), sizes the
 // persistent stage launch from the occupancy of the kernel, and replays a full
 // SSP-RK3 step from a CUDA graph captured once per (batch, buffers) set.
+// Mixed-precision handles also own two FP32 shadows of the interiors, which
+// the RK3 graph passes from stage to stage (each stage reads its input's shadow
+// and writes its output's).
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -53,6 +56,7 @@ struct hydro_handle {
   double* d_partial = nullptr;         // totals scratch (per-sub-grid and per-chunk partials)
   double* d_dt = nullptr;              // [1] time step read by graph replays
   unsigned long long* d_ms_tmp = nullptr;  // [2] speeds of RK stages 2 and 3
+  float* d_shadow[2] = {nullptr, nullptr};  // mixed precision: FP32 interior shadows [n][NF][512]
   cudaStream_t cap_stream = nullptr;
   cudaStream_t last_stream = nullptr;
   int64_t launches = 0;
@@ -97,6 +101,8 @@ void free_all(hydro_handle* h) {
   cudaFree(h->d_partial);
   cudaFree(h->d_dt);
   cudaFree(h->d_ms_tmp);
+  cudaFree(h->d_shadow[0]);
+  cudaFree(h->d_shadow[1]);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
 }
 
@@ -135,9 +141,9 @@ int stage_grid(hydro_handle* h, int n_items) {
 }
 
 // Enqueue one stage (no validation).  queue_slot selects the counter.
-int enqueue_stage(hydro_handle* h, const int32_t* ids, int n_items, const double* Uin, const double* U0,
-                  double beta, double dt, const double* dt_dev, double* Uout, unsigned long long* ms, int queue_slot,
-                  cudaStream_t st) {
+int enqueue_stage(hydro_handle* h, const int32_t* ids, int n_items, const double* Uin, const float* Sin,
+                  const double* U0, double beta, double dt, const double* dt_dev, double* Uout, float* Sout,
+                  unsigned long long* ms, int queue_slot, cudaStream_t st) {
   CUDA_TRY(h, cudaMemsetAsync(ms, 0, 2 * sizeof(unsigned long long), st));
   if (n_items == 0) return HYDRO_OK;
   CUDA_TRY(h, cudaMemsetAsync(h->d_queue + queue_slot, 0, sizeof(unsigned int), st));
@@ -145,6 +151,8 @@ int enqueue_stage(hydro_handle* h, const int32_t* ids, int n_items, const double
   a.Uin = Uin;
   a.U0 = U0;
   a.Uout = Uout;
+  a.Sin = Sin;
+  a.Sout = Sout;
   a.ids = ids;
   a.n_items = n_items;
   a.n_sub = h->n;
@@ -165,6 +173,13 @@ int enqueue_stage(hydro_handle* h, const int32_t* ids, int n_items, const double
   const int grid = stage_grid(h, n_items);
   cudaError_t e = h->precision == HYDRO_MIXED ? launch_stage_mixed(a, grid, st) : launch_stage_fp64(a, grid, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "stage kernel launch");
+  h->launches += 1;
+  return HYDRO_OK;
+}
+
+int enqueue_shadow(hydro_handle* h, const double* U, float* S, cudaStream_t st) {
+  cudaError_t e = launch_shadow(U, S, h->n, st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "shadow kernel launch");
   h->launches += 1;
   return HYDRO_OK;
 }
@@ -235,6 +250,9 @@ int hydro_create(const hydro_grid_desc* d, hydro_handle** out) {
   ok = ok && cudaMalloc(&h->d_partial, sizeof(double) * totals_scratch_doubles(n)) == cudaSuccess;
   ok = ok && cudaMalloc(&h->d_dt, sizeof(double)) == cudaSuccess;
   ok = ok && cudaMalloc(&h->d_ms_tmp, 2 * sizeof(unsigned long long)) == cudaSuccess;
+  if (d->precision == HYDRO_MIXED)
+    for (int b = 0; b < 2; ++b)
+      ok = ok && cudaMalloc(&h->d_shadow[b], sizeof(float) * (size_t)n * NF * SHADOW_FIELD) == cudaSuccess;
   if (!ok) {
     free_all(h);
     delete h;
@@ -262,9 +280,12 @@ int hydro_create(const hydro_grid_desc* d, hydro_handle** out) {
   return HYDRO_OK;
 }
 
-int hydro_step(hydro_handle* h, const hydro_batch* batch, const double* U_in, const double* U0, double beta,
-               double dt, double* U_out, double* d_max_speed, void* stream) {
-  if (!h) return HYDRO_ERR_INVALID;
+}  // extern "C"
+
+namespace {
+
+int check_step(hydro_handle* h, const hydro_batch* batch, const double* U_in, const double* U0, double beta,
+               double dt, const double* U_out, const double* d_max_speed) {
   int rc = check_batch(h, batch);
   if (rc) return rc;
   if (!U_in || !U_out || !d_max_speed) return fail(h, HYDRO_ERR_INVALID, "NULL state or speed pointer");
@@ -274,10 +295,52 @@ int hydro_step(hydro_handle* h, const hydro_batch* batch, const double* U_in, co
   if (!(beta > 0.0 && beta <= 1.0)) return fail(h, HYDRO_ERR_INVALID, "beta must be in (0, 1]");
   if (beta != 1.0 && !U0) return fail(h, HYDRO_ERR_INVALID, "U0 is required when beta != 1");
   if (!(dt >= 0.0) || !std::isfinite(dt)) return fail(h, HYDRO_ERR_INVALID, "dt must be finite and >= 0");
+  return HYDRO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hydro_step(hydro_handle* h, const hydro_batch* batch, const double* U_in, const double* U0, double beta,
+               double dt, double* U_out, double* d_max_speed, void* stream) {
+  if (!h) return HYDRO_ERR_INVALID;
+  int rc = check_step(h, batch, U_in, U0, beta, dt, U_out, d_max_speed);
+  if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   h->last_stream = st;
-  return enqueue_stage(h, batch->subgrid_ids, batch->n_items, U_in, beta == 1.0 ? nullptr : U0, beta, dt, nullptr,
-                       U_out, reinterpret_cast<unsigned long long*>(d_max_speed), 0, st);
+  const float* S = nullptr;
+  if (h->precision == HYDRO_MIXED && batch->n_items > 0) {
+    rc = enqueue_shadow(h, U_in, h->d_shadow[0], st);
+    if (rc) return rc;
+    S = h->d_shadow[0];
+  }
+  return enqueue_stage(h, batch->subgrid_ids, batch->n_items, U_in, S, beta == 1.0 ? nullptr : U0, beta, dt,
+                       nullptr, U_out, nullptr, reinterpret_cast<unsigned long long*>(d_max_speed), 0, st);
+}
+
+int hydro_shadow(hydro_handle* h, const double* U, float* S, void* stream) {
+  if (!h) return HYDRO_ERR_INVALID;
+  if (!U || !S || !aligned(U, 16) || !aligned(S, 16)) return fail(h, HYDRO_ERR_INVALID, "NULL or misaligned pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  return enqueue_shadow(h, U, S, st);
+}
+
+int hydro_step_shadowed(hydro_handle* h, const hydro_batch* batch, const double* U_in, const float* S_in,
+                        const double* U0, double beta, double dt, double* U_out, float* S_out, double* d_max_speed,
+                        void* stream) {
+  if (!h) return HYDRO_ERR_INVALID;
+  if (h->precision != HYDRO_MIXED) return fail(h, HYDRO_ERR_STATE, "hydro_step_shadowed needs a mixed-precision handle");
+  int rc = check_step(h, batch, U_in, U0, beta, dt, U_out, d_max_speed);
+  if (rc) return rc;
+  if (!S_in || !aligned(S_in, 16) || (S_out && !aligned(S_out, 16)))
+    return fail(h, HYDRO_ERR_INVALID, "NULL or misaligned shadow pointer");
+  if (S_out == S_in) return fail(h, HYDRO_ERR_INVALID, "S_out must not alias S_in");
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  return enqueue_stage(h, batch->subgrid_ids, batch->n_items, U_in, S_in, beta == 1.0 ? nullptr : U0, beta, dt,
+                       nullptr, U_out, S_out, reinterpret_cast<unsigned long long*>(d_max_speed), 0, st);
 }
 
 int hydro_fill_ghosts(hydro_handle* h, double* U, void* stream) {
@@ -303,6 +366,8 @@ int rk3_common(hydro_handle* h, const hydro_batch* batch, double* U, double* scr
   if (!aligned(U, 16) || !aligned(scratch1, 16) || !aligned(scratch2, 16) || !aligned(d_max_speed, 8) ||
       (d_dt_out && !aligned(d_dt_out, 8)))
     return fail(h, HYDRO_ERR_INVALID, "misaligned pointer");
+  if (batch->n_items != h->n)
+    return fail(h, HYDRO_ERR_INVALID, "an RK3 step advances every sub-grid: n_items must equal n_subgrids");
   if (cfl > 0.0) {
     if (!(cfl <= 1.0)) return fail(h, HYDRO_ERR_INVALID, "cfl must be in (0, 1]");
   } else if (!(dt >= 0.0) || !std::isfinite(dt)) {
@@ -324,10 +389,17 @@ int rk3_common(hydro_handle* h, const hydro_batch* batch, double* U, double* scr
     const int32_t* ids = batch->subgrid_ids;
     const int ni = batch->n_items;
     // the stage kernel gathers halos from the neighbours' interiors itself, so
-    // no ghost fill is needed between stages
-    rc = enqueue_stage(h, ids, ni, U, nullptr, 1.0, 0.0, h->d_dt, scratch1, ms, 0, cs);
-    if (!rc) rc = enqueue_stage(h, ids, ni, scratch1, U, 0.25, 0.0, h->d_dt, scratch2, h->d_ms_tmp, 1, cs);
-    if (!rc) rc = enqueue_stage(h, ids, ni, scratch2, U, 2.0 / 3.0, 0.0, h->d_dt, U, h->d_ms_tmp, 2, cs);
+    // no ghost fill is needed between stages; in mixed precision each stage
+    // reads the shadow of its input and writes the shadow of its output
+    float* Sa = h->d_shadow[0];
+    float* Sb = h->d_shadow[1];
+    const bool mixed = h->precision == HYDRO_MIXED;
+    rc = mixed ? enqueue_shadow(h, U, Sa, cs) : HYDRO_OK;
+    if (!rc) rc = enqueue_stage(h, ids, ni, U, Sa, nullptr, 1.0, 0.0, h->d_dt, scratch1, Sb, ms, 0, cs);
+    if (!rc)
+      rc = enqueue_stage(h, ids, ni, scratch1, Sb, U, 0.25, 0.0, h->d_dt, scratch2, Sa, h->d_ms_tmp, 1, cs);
+    if (!rc)
+      rc = enqueue_stage(h, ids, ni, scratch2, Sa, U, 2.0 / 3.0, 0.0, h->d_dt, U, nullptr, h->d_ms_tmp, 2, cs);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &graph);
     const int kernels = (int)(h->launches - before);

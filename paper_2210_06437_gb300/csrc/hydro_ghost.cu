@@ -95,3 +95,53 @@ cudaError_t launch_ghost_fill(const GhostArgs& a, int threads, cudaStream_t st) 
 }
 
 }  // namespace hydro
+
+// ---------------------------------------------------------------------------
+// FP32 shadow of the interior: S[s][f][(k*8 + j)*8 + i] = RN32(U[s][f][k+3][j+3][i+3]).
+// The mixed stage reads its reconstruction inputs (own interior and the
+// neighbours' boundary layers) from the shadow: half the bytes of the FP64
+// state, in 32-byte rows, and no conversion inside the stage.
+// ---------------------------------------------------------------------------
+
+namespace hydro {
+namespace {
+
+// FP64 -> FP32 with integer operations: round to nearest on the magnitude
+// (ties away from zero); values below the FP32 normal range become signed
+// zero, larger finite values infinity, NaN stays NaN.  (The same rounding as
+// the stage kernel's own conversion.)
+__device__ __forceinline__ float shadow_round(double x) {
+  const unsigned lo = (unsigned)__double2loint(x), hi = (unsigned)__double2hiint(x);
+  const unsigned mag = hi & 0x7fffffffu;
+  unsigned r = __funnelshift_l(lo, hi, 3) + ((lo >> 28) & 1u) - 0xC0000000u;
+  if (mag - 0x38100000u >= 0x0FE00000u) {
+    r = mag < 0x38100000u ? 0u : ((mag > 0x7ff00000u || (mag == 0x7ff00000u && lo)) ? 0x7fc00000u : 0x7f800000u);
+  }
+  return __uint_as_float(r | (hi & 0x80000000u));
+}
+
+__global__ void __launch_bounds__(256) shadow_kernel(const double* __restrict__ U, float* __restrict__ S, int n) {
+  const size_t total = (size_t)n * NF * CELLS;
+  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(g & (CELLS - 1));
+    const size_t sf = g >> 9;  // s * NF + f
+    const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
+    S[g] = shadow_round(U[sf * NP3 + (size_t)(k + NG) * NP2 + (j + NG) * NP + (i + NG)]);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_shadow(const double* U, float* S, int n, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t total = (size_t)n * NF * CELLS;
+  size_t blocks = (total + 255) / 256;
+  const size_t cap = (size_t)sms * 8 * 4;
+  if (blocks > cap) blocks = cap;
+  shadow_kernel<<<(unsigned)(blocks ? blocks : 1), 256, 0, st>>>(U, S, n);
+  return cudaGetLastError();
+}
+
+}  // namespace hydro

@@ -30,6 +30,8 @@ struct StageArgs {
   const double* Uin;
   const double* U0;     // nullptr when beta == 1
   double* Uout;
+  const float* Sin;     // mixed path: FP32 interior shadow of Uin, [n][11][512]
+  float* Sout;          // mixed path: shadow of Uout to write (may be null)
   const int32_t* ids;
   int32_t n_items;
   int32_t n_sub;
@@ -57,7 +59,10 @@ struct GhostArgs {
   const int8_t* oct;   // [n]
 };
 
+constexpr int SHADOW_FIELD = CELLS;       // floats per field of the shadow ([k][j][i], 8^3)
+
 // launchers (defined in the .cu files)
+cudaError_t launch_shadow(const double* U, float* S, int n, cudaStream_t st);
 cudaError_t launch_stage_fp64(const StageArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_stage_mixed(const StageArgs& a, int grid, cudaStream_t st);
 int stage_blocks_per_sm_fp64();

@@ -329,6 +329,14 @@ __device__ __forceinline__ void cp_async8(double* dst, const double* src) {  // 
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(a), "l"(src));
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::); }
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {  // 4-byte global -> shared copy
+  const unsigned a = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(a), "l"(src));
+}
+// Pull [src, src + bytes) into L2 (16-byte aligned address and size).
+__device__ __forceinline__ void prefetch_l2(const void* src, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src), "r"(bytes));
+}
 
 struct Nbr {
   int32_t id[6][4];
@@ -417,6 +425,81 @@ __device__ __forceinline__ void gather_halo(const double* __restrict__ U, int s,
   }
 }
 
+__device__ __forceinline__ int shadow_index(int i, int j, int k) { return (k * NX + j) * NX + i; }
+
+template <int D>
+__device__ __forceinline__ int shadow_dbb(int cd, int c1, int c2) {
+  return D == 0 ? shadow_index(cd, c1, c2) : (D == 1 ? shadow_index(c1, cd, c2) : shadow_index(c1, c2, cd));
+}
+
+// Mixed path: the same gather from the FP32 shadow S[s][f][(k*8 + j)*8 + i]
+// of the interiors (4-byte asynchronous copies, no conversion); the 2x2x2 means
+// of finer neighbours are formed from the FP64 state as above, then rounded.
+template <int D>
+__device__ __forceinline__ void gather_halo_shadow(const double* __restrict__ U, const float* __restrict__ S, int s,
+                                                   const Nbr& nb, float* halo) {
+  const int q = (int)threadIdx.x - (THREADS - HALO);
+  if (q < 0) return;
+  int l, p;
+  if (D == 0) {
+    p = q / 3;
+    l = q - 3 * p;
+  } else {
+    l = q >> 6;
+    p = q & 63;
+  }
+  const int t1 = p & 7, t2 = p >> 3;
+  const int b1 = D == 0 ? 1 : 0;
+  const int b2 = D == 2 ? 1 : 2;
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const int face = 2 * D + side;
+    const int ga = side ? NX + l : l - NG;
+    float* dst = halo + side * HALO + l * NPEN + p;
+    const int n0 = nb.id[face][0];
+    const int rel = nb.rel[face];
+    if (rel <= 0) {
+      int src_s, off;
+      if (n0 >= 0 && rel == 0) {
+        src_s = n0;
+        off = shadow_dbb<D>(side ? ga - NX : ga + NX, t1, t2);
+      } else if (n0 < 0) {
+        src_s = s;
+        off = shadow_dbb<D>(side ? NX - 1 : 0, t1, t2);
+      } else {
+        const int fa = ga >= 0 ? ga / 2 : -((1 - ga) / 2);
+        src_s = n0;
+        off = shadow_dbb<D>((side ? -4 : 8) + fa, 4 * ((nb.oct >> b1) & 1) + (t1 >> 1), 4 * ((nb.oct >> b2) & 1) + (t2 >> 1));
+      }
+      const float* src = S + (size_t)src_s * NF * SHADOW_FIELD + off;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) cp_async4(dst + f * 2 * HALO, src + f * SHADOW_FIELD);
+    } else {
+      const int q1 = t1 >> 2, q2 = t2 >> 2;
+      const int fs = nb.id[face][q1 + 2 * q2];
+      const int cd = 2 * (side ? ga - NX : ga + 4) + NG;
+      const int c1 = 2 * (t1 - 4 * q1) + NG, c2 = 2 * (t2 - 4 * q2) + NG;
+      int c[3];
+      c[D] = cd;
+      c[b1] = c1;
+      c[b2] = c2;
+      const double* src = U + field_offset(fs, 0) + pad_offset(c[0], c[1], c[2]);
+#pragma unroll 4
+      for (int f = 0; f < NF; ++f) {
+        const double* g = src + (size_t)f * NP3;
+        double sum = 0.0;
+#pragma unroll
+        for (int dk = 0; dk < 2; ++dk)
+#pragma unroll
+          for (int dj = 0; dj < 2; ++dj)
+#pragma unroll
+            for (int di = 0; di < 2; ++di) sum = __dadd_rn(sum, g[dk * NP2 + dj * NP + di]);
+        dst[f * 2 * HALO] = f64_to_f32(__dmul_rn(sum, 0.125));
+      }
+    }
+  }
+}
+
 // interior tile index of pencil position n (0..7) of pencil p in direction d
 __device__ __forceinline__ int tile_index(int d, int p, int n) {
   const int t1 = p & 7, t2 = p >> 3;
@@ -426,18 +509,40 @@ __device__ __forceinline__ int tile_index(int d, int p, int n) {
 template <typename T>
 struct StageSmem {
   static constexpr size_t interior = sizeof(T) * NF * ISZ;
-  static constexpr size_t halo = sizeof(double) * NF * 2 * HALO;
+  static constexpr size_t halo = sizeof(T) * NF * 2 * HALO;
   static constexpr size_t faces = sizeof(T) * 2 * NF * FACES_DIR;
   static constexpr size_t total = interior + halo + faces;
 };
 
 template <typename T>
 struct Shared {
-  T* tile;       // [NF][ISZ] interior, T
-  double* halo;  // [NF][2][HALO] current direction's halo slabs, FP64
+  T* tile;  // [NF][ISZ] interior
+  T* halo;  // [NF][2][HALO] current direction's halo slabs
   T* fsl;        // [NF][576] left face states, then fluxes
   T* fsr;        // [NF][576] right face states
 };
+
+template <typename T, int D>
+__device__ __forceinline__ void gather(const StageArgs& a, int s, const Nbr& nb, T* halo) {
+  if constexpr (sizeof(T) == 4)
+    gather_halo_shadow<D>(a.Uin, a.Sin, s, nb, halo);
+  else
+    gather_halo<D>(a.Uin, s, nb, halo);
+}
+
+// Mixed path: asynchronous copy of sub-grid s's interior (all fields) from the
+// shadow into the tile; consecutive threads take consecutive cells.
+__device__ __forceinline__ void stage_interior_async(const float* __restrict__ S, int s, float* tile) {
+  const float* src = S + (size_t)s * NF * SHADOW_FIELD;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int c = threadIdx.x + r * THREADS;
+    const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
+    const int t = k * SK + j * SJ + i;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) cp_async4(tile + f * ISZ + t, src + f * SHADOW_FIELD + c);
+  }
+}
 
 // Work item and what its processing needs: sub-grid id (-1: queue exhausted,
 // -2: bad id), neighbour table, dt/dx and 1/dx.
@@ -501,13 +606,13 @@ __device__ __forceinline__ void direction_pass(const Shared<T>& sh, const StageA
   for (int task = tid; task < NF * NPEN; task += THREADS) {
     const int f = task >> 6, p = task & 63;
     T q[NP];
-    const double* hl = sh.halo + (f * 2) * HALO + p;
+    const T* hl = sh.halo + (f * 2) * HALO + p;
 #pragma unroll
-    for (int m = 0; m < NG; ++m) q[m] = Arith<T>::from64(hl[m * NPEN]);
+    for (int m = 0; m < NG; ++m) q[m] = hl[m * NPEN];
 #pragma unroll
     for (int n = 0; n < NX; ++n) q[NG + n] = sh.tile[f * ISZ + tile_index(D, p, n)];
 #pragma unroll
-    for (int m = 0; m < NG; ++m) q[NG + NX + m] = Arith<T>::from64(hl[HALO + m * NPEN]);
+    for (int m = 0; m < NG; ++m) q[NG + NX + m] = hl[HALO + m * NPEN];
     T ul[NFACE], ur[NFACE];
     ppm_pencil(q, ul, ur);
 #pragma unroll
@@ -518,11 +623,14 @@ __device__ __forceinline__ void direction_pass(const Shared<T>& sh, const StageA
   }
   if (D == 2 && (tid >> 5) == THREADS / 32 - 1) prefetch_meta(a, dt, nxt);
   __syncthreads();
-  // the halo buffer is free: start gathering the next slabs
-  if (D < 2)
-    gather_halo<(D < 2 ? D + 1 : 2)>(a.Uin, cur.s, cur.nb, sh.halo);
-  else if (nxt.s >= 0)
-    gather_halo<0>(a.Uin, nxt.s, nxt.nb, sh.halo);
+  // the halo buffer is free: start gathering the next slabs; after z the tile
+  // is free too, and the mixed path starts copying the next interior
+  if (D < 2) {
+    gather<T, (D < 2 ? D + 1 : 2)>(a, cur.s, cur.nb, sh.halo);
+  } else if (nxt.s >= 0) {
+    if constexpr (sizeof(T) == 4) stage_interior_async(a.Sin, nxt.s, sh.tile);
+    gather<T, 0>(a, nxt.s, nxt.nb, sh.halo);
+  }
   // B: one face per iteration
 #pragma unroll 1
   for (int fc = tid; fc < FACES_DIR; fc += THREADS) {
@@ -563,7 +671,7 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Shared<T> sh;
   sh.tile = reinterpret_cast<T*>(smem_raw);
-  sh.halo = reinterpret_cast<double*>(smem_raw + StageSmem<T>::interior);
+  sh.halo = reinterpret_cast<T*>(smem_raw + StageSmem<T>::interior);
   sh.fsl = reinterpret_cast<T*>(smem_raw + StageSmem<T>::interior + StageSmem<T>::halo);
   sh.fsr = sh.fsl + NF * FACES_DIR;
   __shared__ Meta s_meta[2];
@@ -578,7 +686,10 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(
   // prologue: the first work item, its neighbour table and x halo
   if ((tid >> 5) == THREADS / 32 - 1) prefetch_meta(a, dt, s_meta[0]);
   __syncthreads();
-  if (s_meta[0].s >= 0) gather_halo<0>(a.Uin, s_meta[0].s, s_meta[0].nb, sh.halo);
+  if (s_meta[0].s >= 0) {
+    if constexpr (sizeof(T) == 4) stage_interior_async(a.Sin, s_meta[0].s, sh.tile);
+    gather<T, 0>(a, s_meta[0].s, s_meta[0].nb, sh.halo);
+  }
   int par = 0;
   for (;;) {
     const Meta& cur = s_meta[par];
@@ -590,20 +701,25 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(
       __syncthreads();
       if ((tid >> 5) == THREADS / 32 - 1) prefetch_meta(a, dt, nxt);
       __syncthreads();
-      if (nxt.s >= 0) gather_halo<0>(a.Uin, nxt.s, nxt.nb, sh.halo);
+      if (nxt.s >= 0) {
+        if constexpr (sizeof(T) == 4) stage_interior_async(a.Sin, nxt.s, sh.tile);
+        gather<T, 0>(a, nxt.s, nxt.nb, sh.halo);
+      }
       par ^= 1;
       continue;
     }
-    // interior of all fields, FP64 -> T
-    const double* Us = a.Uin + field_offset(s, 0);
+    if constexpr (sizeof(T) == 8) {
+      // FP64 path: interior of all fields, loaded synchronously
+      const double* Us = a.Uin + field_offset(s, 0);
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const int c = tid + r * THREADS;
-      const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
-      const int g = (k + NG) * NP2 + (j + NG) * NP + (i + NG);
-      const int t = k * SK + j * SJ + i;
+      for (int r = 0; r < 2; ++r) {
+        const int c = tid + r * THREADS;
+        const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
+        const int g = (k + NG) * NP2 + (j + NG) * NP + (i + NG);
+        const int t = k * SK + j * SJ + i;
 #pragma unroll
-      for (int f = 0; f < NF; ++f) sh.tile[f * ISZ + t] = Arith<T>::from64(Us[(size_t)f * NP3 + g]);
+        for (int f = 0; f < NF; ++f) sh.tile[f * ISZ + t] = Us[(size_t)f * NP3 + g];
+      }
     }
     cp_async_wait_all();
     __syncthreads();  // interior tile and x halo in place
@@ -629,6 +745,7 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(
         const double u0 = blend ? a.U0[o] : 0.0;
         const double v = acc[r][f].update(u, u0, lam, lh, ll, a.beta, blend);
         a.Uout[o] = v;
+        if (sizeof(T) == 4 && a.Sout) a.Sout[((size_t)s * NF + f) * SHADOW_FIELD + c] = f64_to_f32(v);
         bad |= bad64(v, f == F_RHO);
       }
     }

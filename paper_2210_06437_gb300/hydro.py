@@ -26,9 +26,10 @@ STATUS = {0: "HYDRO_OK", -1: "HYDRO_ERR_INVALID", -2: "HYDRO_ERR_CUDA", -3: "HYD
           -4: "HYDRO_ERR_NONFINITE", -5: "HYDRO_ERR_TIMEOUT", -6: "HYDRO_ERR_STATE"}
 
 # every symbol include/hydro.h declares
-EXPORTS = ("hydro_create", "hydro_step", "hydro_fill_ghosts", "hydro_rk3_step", "hydro_rk3_step_cfl", "hydro_totals",
-           "hydro_totals_noalloc", "hydro_sync", "hydro_last_error", "hydro_launch_count", "hydro_set_param",
-           "hydro_destroy")
+EXPORTS = ("hydro_create", "hydro_step", "hydro_shadow", "hydro_step_shadowed", "hydro_fill_ghosts", "hydro_rk3_step",
+           "hydro_rk3_step_cfl", "hydro_totals", "hydro_totals_noalloc", "hydro_sync", "hydro_last_error",
+           "hydro_launch_count", "hydro_set_param", "hydro_destroy")
+SHADOW_FIELD = NX * NX * NX
 TOTALS_NOALLOC_MAX_SUBGRIDS = 65536
 
 
@@ -64,6 +65,8 @@ def load_library(path: str = LIB_PATH):
     vp, i32, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
     L.hydro_create.argtypes = [ctypes.POINTER(GridDesc), ctypes.POINTER(vp)]
     L.hydro_step.argtypes = [vp, ctypes.POINTER(Batch), vp, vp, dbl, dbl, vp, vp, vp]
+    L.hydro_shadow.argtypes = [vp, vp, vp, vp]
+    L.hydro_step_shadowed.argtypes = [vp, ctypes.POINTER(Batch), vp, vp, vp, dbl, dbl, vp, vp, vp, vp]
     L.hydro_fill_ghosts.argtypes = [vp, vp, vp]
     L.hydro_rk3_step.argtypes = [vp, ctypes.POINTER(Batch), vp, vp, vp, dbl, vp, vp]
     L.hydro_rk3_step_cfl.argtypes = [vp, ctypes.POINTER(Batch), vp, vp, vp, dbl, vp, vp, vp]
@@ -168,6 +171,41 @@ class HydroGrid:
         b, keep = self._batch(ids, batch_offsets)
         self._check(self.lib.hydro_step(self.h, ctypes.byref(b), _ptr(U_in), _ptr(U0), float(beta), float(dt),
                                         _ptr(U_out), _ptr(ms), _stream_ptr(stream)))
+        return U_out, ms
+
+    def empty_shadow(self):
+        import torch
+        return torch.empty((self.n, NF, SHADOW_FIELD), dtype=torch.float32, device=self.device)
+
+    def _shadow_buf(self, S):
+        import torch
+        assert isinstance(S, torch.Tensor) and S.dtype == torch.float32 and S.is_cuda and S.is_contiguous()
+        assert S.numel() == self.n * NF * SHADOW_FIELD
+        return S
+
+    def shadow(self, U, S=None, stream=None):
+        """FP32 shadow of U's interiors (hydro_shadow).  Returns S [n, 11, 512]."""
+        self._state(U)
+        S = self.empty_shadow() if S is None else self._shadow_buf(S)
+        self._check(self.lib.hydro_shadow(self.h, _ptr(U), _ptr(S), _stream_ptr(stream)))
+        return S
+
+    def step_shadowed(self, U_in, S_in, dt, U0=None, beta=1.0, U_out=None, S_out=None, ids=None, batch_offsets=None,
+                      max_speed=None, stream=None):
+        """One RK stage from a caller-held shadow (hydro_step_shadowed, mixed
+        precision).  Returns (U_out, max_speed tensor[2])."""
+        self._state(U_in)
+        self._shadow_buf(S_in)
+        if S_out is not None:
+            self._shadow_buf(S_out)
+        if U_out is None:
+            U_out = U_in.clone()
+        self._state(U_out)
+        ms = self._ms if max_speed is None else max_speed
+        b, keep = self._batch(ids, batch_offsets)
+        self._check(self.lib.hydro_step_shadowed(self.h, ctypes.byref(b), _ptr(U_in), _ptr(S_in), _ptr(U0),
+                                                 float(beta), float(dt), _ptr(U_out), _ptr(S_out), _ptr(ms),
+                                                 _stream_ptr(stream)))
         return U_out, ms
 
     def fill_ghosts(self, U, stream=None):

@@ -338,3 +338,84 @@ def test_autotuned_launch_keeps_parity(hydro, oracle_mod, prec, tmp_path, monkey
     g.sync()
     ref, _, _ = oracle_mod.Oracle(w.grid).stage(U, dt)
     assert np.all(field_errors(_host(out), ref) <= TOL[prec])
+
+
+# ---------------------------------------------------------------------------
+# FP32 shadows of the interiors (mixed-precision inputs)
+# ---------------------------------------------------------------------------
+
+def _round32_away(x):
+    """float64 -> float32, nearest with ties away from zero, below the float32
+    normal range to signed zero (the rounding hydro_shadow documents)."""
+    with np.errstate(over="ignore"):
+        r = x.astype(np.float32)
+        up = np.nextafter(r, np.copysign(np.float32(np.inf), x).astype(np.float32))
+    d_r = np.abs(x - r.astype(np.float64))
+    d_up = np.abs(up.astype(np.float64) - x)
+    tie = (d_r == d_up) & (np.abs(up) > np.abs(r)) & np.isfinite(up)
+    r = np.where(tie, up, r)
+    return np.where(np.abs(x) < 2.0 ** -126, np.copysign(np.float32(0), x).astype(np.float32), r)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_shadow_is_rounded_interior(hydro, oracle_mod, prec):
+    w = W.config(3)
+    U = _filled(oracle_mod, w)
+    planted = {(0, 6, 3, 3, 3): 1.0 + 2.0 ** -24, (0, 6, 3, 3, 4): -(1.0 + 2.0 ** -24),
+               (0, 6, 3, 3, 5): 1e-40, (0, 6, 3, 3, 6): -1e-39, (0, 6, 3, 3, 7): 1e39,
+               (0, 6, 3, 3, 8): 1.0 + 2.0 ** -25, (0, 6, 3, 3, 9): 1.0 + 2.0 ** -24 + 2.0 ** -40}
+    for k, v in planted.items():
+        U[k] = v
+    g = hydro.HydroGrid(w.grid, precision=prec)
+    S = _host(g.shadow(_dev(U))).reshape(w.grid.n, 11, 8, 8, 8)
+    g.sync()
+    exp = _round32_away(U[IN])
+    assert np.array_equal(S.view(np.uint32), exp.view(np.uint32))
+    s0 = S[0, 6, 0, 0]
+    assert s0[0] == np.float32(1.0 + 2.0 ** -23) and s0[1] == -np.float32(1.0 + 2.0 ** -23)
+    assert s0[2] == 0.0 and s0[3] == 0.0 and np.signbit(s0[3]) and s0[4] == np.inf
+    assert s0[5] == 1.0 and s0[6] == np.float32(1.0 + 2.0 ** -23)
+
+
+def test_step_shadowed_matches_step(hydro, oracle_mod):
+    w = W.config(3)
+    U = _filled(oracle_mod, w)
+    dt, _ = _dt(oracle_mod, w, U)
+    g = hydro.HydroGrid(w.grid, precision="mixed")
+    Ud = _dev(U)
+    U0 = _dev(oracle_mod.Oracle(w.grid).stage(U, 0.5 * dt)[0])
+    S = g.shadow(Ud)
+    rng = np.random.default_rng(4)
+    sub = rng.permutation(w.grid.n)[:900].astype(np.int32)
+    for beta, u0 in ((1.0, None), (0.25, U0)):
+        a, ms_a = g.step(Ud, dt, U0=u0, beta=beta, U_out=torch.full_like(Ud, 2.0), ids=sub)
+        ms_a = ms_a.clone()
+        So = torch.full_like(S, -1.0)
+        b, ms_b = g.step_shadowed(Ud, S, dt, U0=u0, beta=beta, U_out=torch.full_like(Ud, 2.0), S_out=So, ids=sub,
+                                  batch_offsets=[0, 450, 900])
+        g.sync()
+        assert torch.equal(a, b)
+        assert torch.equal(ms_a, ms_b)
+        ref = g.shadow(b)
+        g.sync()
+        idx = torch.as_tensor(sub.astype(np.int64), device="cuda")
+        assert torch.equal(So[idx], ref[idx])            # shadow of the output, bit for bit
+        rest = torch.as_tensor(np.setdiff1d(np.arange(w.grid.n), sub), device="cuda")
+        assert torch.all(So[rest] == -1.0)               # untouched outside the batch
+
+
+def test_shadow_entry_errors(hydro):
+    w = W.config(1)
+    Ud = _dev(w.state())
+    g64 = hydro.HydroGrid(w.grid, precision="fp64")
+    S = g64.shadow(Ud)
+    with pytest.raises(hydro.HydroError) as e:
+        g64.step_shadowed(Ud, S, 1e-3, U_out=torch.empty_like(Ud))
+    assert e.value.code == -6
+    g = hydro.HydroGrid(w.grid, precision="mixed")
+    with pytest.raises(hydro.HydroError) as e:
+        g.step_shadowed(Ud, S, 1e-3, U_out=torch.empty_like(Ud), S_out=S)  # S_out aliases S_in
+    assert e.value.code == -1
+    with pytest.raises(hydro.HydroError) as e:  # an RK3 step must advance every sub-grid
+        g.rk3_step(Ud, 1e-3, torch.empty_like(Ud), torch.empty_like(Ud), ids=np.arange(w.grid.n - 1))
+    assert e.value.code == -1
