@@ -133,11 +133,16 @@ int hydro_step(hydro_handle *h, const hydro_batch *batch, const double *U_in, co
 
 /* FP32 shadow of the interiors of every sub-grid of U, the input the
  * mixed-precision reconstruction reads (the paper has no counterpart; it is
- * the GB300 layout of the float32 reconstruction inputs):
- *   S[s][f][(k*8 + j)*8 + i] = U[s][f][k+3][j+3][i+3] rounded to the nearest
- *   float32 (ties away from zero; magnitudes below the float32 normal range
- *   become signed zero, finite values beyond it infinity).
- *   U DEVICE padded state; S DEVICE float[n_subgrids][11][512], 16-byte
+ * the GB300 layout of the float32 reconstruction inputs).  Per sub-grid s and
+ * field f, 576 floats:
+ *   S[s][f][(k*8 + j)*8 + i] = r(U[s][f][k+3][j+3][i+3]), k, j, i < 8, with r
+ *     the rounding to the nearest float32 (ties away from zero; magnitudes
+ *     below the float32 normal range become signed zero, finite values beyond
+ *     it infinity);
+ *   S[s][f][512 + (K*4 + J)*4 + I] = the float32 sum of the eight rounded cells
+ *     (2K+dk, 2J+dj, 2I+di), added in (dk, dj, di) order, times 1/8: the
+ *     restriction a coarser neighbour reads as its halo.
+ *   U DEVICE padded state; S DEVICE float[n_subgrids][11][576], 16-byte
  *   aligned.  Works with either precision of handle. */
 int hydro_shadow(hydro_handle *h, const double *U, float *S, void *stream);
 

@@ -97,10 +97,13 @@ cudaError_t launch_ghost_fill(const GhostArgs& a, int threads, cudaStream_t st) 
 }  // namespace hydro
 
 // ---------------------------------------------------------------------------
-// FP32 shadow of the interior: S[s][f][(k*8 + j)*8 + i] = RN32(U[s][f][k+3][j+3][i+3]).
-// The mixed stage reads its reconstruction inputs (own interior and the
-// neighbours' boundary layers) from the shadow: half the bytes of the FP64
-// state, in 32-byte rows, and no conversion inside the stage.
+// FP32 shadow of the interior: per sub-grid field, the 512 interior cells
+// RN32(U[s][f][k+3][j+3][i+3]) at (k*8 + j)*8 + i, then the 64 cells of its
+// 2x2x2 restriction at 512 + (K*4 + J)*4 + I: the FP32 sum of the 8 rounded
+// cells in (k, j, i) order, times 1/8.  The mixed stage reads its
+// reconstruction inputs (own interior, the neighbours' boundary layers and the
+// finer neighbours' restrictions) from the shadow: half the bytes of the FP64
+// state, in 32-byte rows, every halo cell a plain copy.
 // ---------------------------------------------------------------------------
 
 namespace hydro {
@@ -121,12 +124,26 @@ __device__ __forceinline__ float shadow_round(double x) {
 }
 
 __global__ void __launch_bounds__(256) shadow_kernel(const double* __restrict__ U, float* __restrict__ S, int n) {
-  const size_t total = (size_t)n * NF * CELLS;
+  const size_t total = (size_t)n * NF * SHADOW_FIELD;
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
-    const int c = (int)(g & (CELLS - 1));
-    const size_t sf = g >> 9;  // s * NF + f
-    const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
-    S[g] = shadow_round(U[sf * NP3 + (size_t)(k + NG) * NP2 + (j + NG) * NP + (i + NG)]);
+    const size_t sf = g / SHADOW_FIELD;  // s * NF + f
+    const int c = (int)(g - sf * SHADOW_FIELD);
+    const double* u = U + sf * NP3;
+    if (c < SHADOW_COARSE) {
+      const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
+      S[g] = shadow_round(u[(size_t)(k + NG) * NP2 + (j + NG) * NP + (i + NG)]);
+    } else {
+      const int cc = c - SHADOW_COARSE;
+      const int I = cc & 3, J = (cc >> 2) & 3, K = cc >> 4;
+      const double* b = u + (size_t)(2 * K + NG) * NP2 + (2 * J + NG) * NP + (2 * I + NG);
+      float sum = shadow_round(b[0]);
+#pragma unroll
+      for (int m = 1; m < 8; ++m) {  // m = dk*4 + dj*2 + di
+        const int dk = m >> 2, dj = (m >> 1) & 1, di = m & 1;
+        sum = __fadd_rn(sum, shadow_round(b[dk * NP2 + dj * NP + di]));
+      }
+      S[g] = __fmul_rn(sum, 0.125f);
+    }
   }
 }
 
@@ -136,7 +153,7 @@ cudaError_t launch_shadow(const double* U, float* S, int n, cudaStream_t st) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const size_t total = (size_t)n * NF * CELLS;
+  const size_t total = (size_t)n * NF * SHADOW_FIELD;
   size_t blocks = (total + 255) / 256;
   const size_t cap = (size_t)sms * 8 * 4;
   if (blocks > cap) blocks = cap;

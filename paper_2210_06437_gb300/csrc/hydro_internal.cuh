@@ -59,7 +59,11 @@ struct GhostArgs {
   const int8_t* oct;   // [n]
 };
 
-constexpr int SHADOW_FIELD = CELLS;       // floats per field of the shadow ([k][j][i], 8^3)
+// FP32 shadow of a sub-grid field: the 8^3 interior [k][j][i], then its 4^3
+// restriction [K][J][I] (FP32 mean of the 2x2x2 rounded cells, summed in
+// (k, j, i) order), which a coarser neighbour reads as its halo.
+constexpr int SHADOW_COARSE = CELLS;            // offset of the restriction
+constexpr int SHADOW_FIELD = CELLS + CELLS / 8;  // 576 floats per field
 
 // launchers (defined in the .cu files)
 cudaError_t launch_shadow(const double* U, float* S, int n, cudaStream_t st);

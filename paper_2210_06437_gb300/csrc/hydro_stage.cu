@@ -432,12 +432,11 @@ __device__ __forceinline__ int shadow_dbb(int cd, int c1, int c2) {
   return D == 0 ? shadow_index(cd, c1, c2) : (D == 1 ? shadow_index(c1, cd, c2) : shadow_index(c1, c2, cd));
 }
 
-// Mixed path: the same gather from the FP32 shadow S[s][f][(k*8 + j)*8 + i]
-// of the interiors (4-byte asynchronous copies, no conversion); the 2x2x2 means
-// of finer neighbours are formed from the FP64 state as above, then rounded.
+// Mixed path: the same gather from the FP32 shadow (interior at
+// (k*8 + j)*8 + i, 4^3 restriction after it): every ghost cell is one 4-byte
+// asynchronous copy, a finer neighbour's from its restriction.
 template <int D>
-__device__ __forceinline__ void gather_halo_shadow(const double* __restrict__ U, const float* __restrict__ S, int s,
-                                                   const Nbr& nb, float* halo) {
+__device__ __forceinline__ void gather_halo_shadow(const float* __restrict__ S, int s, const Nbr& nb, float* halo) {
   const int q = (int)threadIdx.x - (THREADS - HALO);
   if (q < 0) return;
   int l, p;
@@ -458,46 +457,38 @@ __device__ __forceinline__ void gather_halo_shadow(const double* __restrict__ U,
     float* dst = halo + side * HALO + l * NPEN + p;
     const int n0 = nb.id[face][0];
     const int rel = nb.rel[face];
-    if (rel <= 0) {
-      int src_s, off;
-      if (n0 >= 0 && rel == 0) {
-        src_s = n0;
-        off = shadow_dbb<D>(side ? ga - NX : ga + NX, t1, t2);
-      } else if (n0 < 0) {
-        src_s = s;
-        off = shadow_dbb<D>(side ? NX - 1 : 0, t1, t2);
-      } else {
-        const int fa = ga >= 0 ? ga / 2 : -((1 - ga) / 2);
-        src_s = n0;
-        off = shadow_dbb<D>((side ? -4 : 8) + fa, 4 * ((nb.oct >> b1) & 1) + (t1 >> 1), 4 * ((nb.oct >> b2) & 1) + (t2 >> 1));
-      }
-      const float* src = S + (size_t)src_s * NF * SHADOW_FIELD + off;
-#pragma unroll
-      for (int f = 0; f < NF; ++f) cp_async4(dst + f * 2 * HALO, src + f * SHADOW_FIELD);
-    } else {
+    int src_s, off;
+    if (n0 >= 0 && rel == 0) {  // same level
+      src_s = n0;
+      off = shadow_dbb<D>(side ? ga - NX : ga + NX, t1, t2);
+    } else if (n0 < 0) {  // domain boundary: outflow
+      src_s = s;
+      off = shadow_dbb<D>(side ? NX - 1 : 0, t1, t2);
+    } else if (rel < 0) {  // coarser: the coarse cell containing the ghost-cell centre
+      const int fa = ga >= 0 ? ga / 2 : -((1 - ga) / 2);
+      src_s = n0;
+      off = shadow_dbb<D>((side ? -4 : 8) + fa, 4 * ((nb.oct >> b1) & 1) + (t1 >> 1), 4 * ((nb.oct >> b2) & 1) + (t2 >> 1));
+    } else {  // finer: the restricted cell of the quadrant's neighbour
       const int q1 = t1 >> 2, q2 = t2 >> 2;
-      const int fs = nb.id[face][q1 + 2 * q2];
-      const int cd = 2 * (side ? ga - NX : ga + 4) + NG;
-      const int c1 = 2 * (t1 - 4 * q1) + NG, c2 = 2 * (t2 - 4 * q2) + NG;
+      src_s = nb.id[face][q1 + 2 * q2];
       int c[3];
-      c[D] = cd;
-      c[b1] = c1;
-      c[b2] = c2;
-      const double* src = U + field_offset(fs, 0) + pad_offset(c[0], c[1], c[2]);
-#pragma unroll 4
-      for (int f = 0; f < NF; ++f) {
-        const double* g = src + (size_t)f * NP3;
-        double sum = 0.0;
-#pragma unroll
-        for (int dk = 0; dk < 2; ++dk)
-#pragma unroll
-          for (int dj = 0; dj < 2; ++dj)
-#pragma unroll
-            for (int di = 0; di < 2; ++di) sum = __dadd_rn(sum, g[dk * NP2 + dj * NP + di]);
-        dst[f * 2 * HALO] = f64_to_f32(__dmul_rn(sum, 0.125));
-      }
+      c[D] = side ? ga - NX : ga + 4;
+      c[b1] = t1 - 4 * q1;
+      c[b2] = t2 - 4 * q2;
+      off = SHADOW_COARSE + (c[2] * 4 + c[1]) * 4 + c[0];
     }
+    const float* src = S + (size_t)src_s * NF * SHADOW_FIELD + off;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) cp_async4(dst + f * 2 * HALO, src + f * SHADOW_FIELD);
   }
+}
+
+// Cell r (0, 1) owned by this thread in the flux accumulation and the update:
+// the k-pair (2*(tid/64) + r) at (i, j) = (tid % 8, tid / 8 % 8), so that a
+// 2x2x2 block lies in one thread pair in k and lanes ^1, ^8, ^9 of one warp.
+__device__ __forceinline__ int owned_cell(int r) {
+  const int tid = threadIdx.x;
+  return ((tid >> 6) * 2 + r) * 64 + (tid & 63);
 }
 
 // interior tile index of pencil position n (0..7) of pencil p in direction d
@@ -525,7 +516,7 @@ struct Shared {
 template <typename T, int D>
 __device__ __forceinline__ void gather(const StageArgs& a, int s, const Nbr& nb, T* halo) {
   if constexpr (sizeof(T) == 4)
-    gather_halo_shadow<D>(a.Uin, a.Sin, s, nb, halo);
+    gather_halo_shadow<D>(a.Sin, s, nb, halo);
   else
     gather_halo<D>(a.Uin, s, nb, halo);
 }
@@ -649,7 +640,7 @@ __device__ __forceinline__ void direction_pass(const Shared<T>& sh, const StageA
   // C: flux differences of direction D for the two owned cells
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
-    const int c = tid + r * THREADS;
+    const int c = owned_cell(r);
     const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
     const int p = D == 0 ? (k * 8 + j) : (D == 1 ? (k * 8 + i) : (j * 8 + i));
     const int id = D == 0 ? i : (D == 1 ? j : k);
@@ -730,23 +721,39 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(
     direction_pass<T, 1>(sh, a, cur, nxt, dt, acc, amax, gamma, eta);
     direction_pass<T, 2>(sh, a, cur, nxt, dt, acc, amax, gamma, eta);
 
-    // update of the owned cells
+    // update of the owned cells; mixed precision also writes the output's
+    // shadow: the rounded cells and their 2x2x2 restriction (FP32 sum in
+    // (k, j, i) order, the partners' cells by warp shuffles)
     const double lam = cur.lam;
     const float lh = cur.lh, ll = cur.ll;
+    const int c0 = owned_cell(0);
+    const size_t cell0 = (size_t)((c0 >> 6) + NG) * NP2 + (((c0 >> 3) & 7) + NG) * NP + ((c0 & 7) + NG);
+    const bool shadow_out = sizeof(T) == 4 && a.Sout != nullptr;
+    const bool restrict_lane = (tid & 9) == 0;  // i and j even
+    const int cc = (tid >> 6) * 16 + ((tid >> 4) & 3) * 4 + ((tid >> 1) & 3);
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const int c = tid + r * THREADS;
-      const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
-      const size_t cell = (size_t)(k + NG) * NP2 + (j + NG) * NP + (i + NG);
+    for (int f = 0; f < NF; ++f) {
+      double v[2];
 #pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        const size_t o = field_offset(s, f) + cell;
+      for (int r = 0; r < 2; ++r) {
+        const size_t o = field_offset(s, f) + cell0 + (size_t)r * NP2;
         const double u = a.Uin[o];
         const double u0 = blend ? a.U0[o] : 0.0;
-        const double v = acc[r][f].update(u, u0, lam, lh, ll, a.beta, blend);
-        a.Uout[o] = v;
-        if (sizeof(T) == 4 && a.Sout) a.Sout[((size_t)s * NF + f) * SHADOW_FIELD + c] = f64_to_f32(v);
-        bad |= bad64(v, f == F_RHO);
+        v[r] = acc[r][f].update(u, u0, lam, lh, ll, a.beta, blend);
+        a.Uout[o] = v[r];
+        bad |= bad64(v[r], f == F_RHO);
+      }
+      if (shadow_out) {
+        float* So = a.Sout + ((size_t)s * NF + f) * SHADOW_FIELD;
+        const float x0 = f64_to_f32(v[0]), x1 = f64_to_f32(v[1]);
+        So[c0] = x0;
+        So[c0 + 64] = x1;
+        const float b0 = __shfl_xor_sync(0xffffffffu, x0, 1), b1 = __shfl_xor_sync(0xffffffffu, x1, 1);
+        const float e0 = __shfl_xor_sync(0xffffffffu, x0, 8), e1 = __shfl_xor_sync(0xffffffffu, x1, 8);
+        const float d0 = __shfl_xor_sync(0xffffffffu, x0, 9), d1 = __shfl_xor_sync(0xffffffffu, x1, 9);
+        float m = __fadd_rn(__fadd_rn(__fadd_rn(x0, b0), e0), d0);
+        m = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(m, x1), b1), e1), d1);
+        if (restrict_lane) So[SHADOW_COARSE + cc] = __fmul_rn(m, 0.125f);
       }
     }
 

@@ -29,7 +29,7 @@ STATUS = {0: "HYDRO_OK", -1: "HYDRO_ERR_INVALID", -2: "HYDRO_ERR_CUDA", -3: "HYD
 EXPORTS = ("hydro_create", "hydro_step", "hydro_shadow", "hydro_step_shadowed", "hydro_fill_ghosts", "hydro_rk3_step",
            "hydro_rk3_step_cfl", "hydro_totals", "hydro_totals_noalloc", "hydro_sync", "hydro_last_error",
            "hydro_launch_count", "hydro_set_param", "hydro_destroy")
-SHADOW_FIELD = NX * NX * NX
+SHADOW_FIELD = NX * NX * NX + (NX // 2) ** 3   # interior, then its 4^3 restriction
 TOTALS_NOALLOC_MAX_SUBGRIDS = 65536
 
 

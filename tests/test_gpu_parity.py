@@ -367,10 +367,21 @@ def test_shadow_is_rounded_interior(hydro, oracle_mod, prec):
     for k, v in planted.items():
         U[k] = v
     g = hydro.HydroGrid(w.grid, precision=prec)
-    S = _host(g.shadow(_dev(U))).reshape(w.grid.n, 11, 8, 8, 8)
+    S = _host(g.shadow(_dev(U)))
     g.sync()
+    n = w.grid.n
     exp = _round32_away(U[IN])
-    assert np.array_equal(S.view(np.uint32), exp.view(np.uint32))
+    assert np.array_equal(S[:, :, :512].view(np.uint32), exp.reshape(n, 11, 512).view(np.uint32))
+    # restriction: float32 sum of the 8 rounded cells in (dk, dj, di) order, times 1/8
+    e = exp.reshape(n, 11, 4, 2, 4, 2, 4, 2)
+    acc = e[:, :, :, 0, :, 0, :, 0].copy()
+    for m in range(1, 8):
+        dk, dj, di = m >> 2, (m >> 1) & 1, m & 1
+        acc = acc + e[:, :, :, dk, :, dj, :, di]
+    acc = acc * np.float32(0.125)
+    assert acc.dtype == np.float32
+    assert np.array_equal(S[:, :, 512:].view(np.uint32), acc.reshape(n, 11, 64).view(np.uint32))
+    S = S[:, :, :512].reshape(n, 11, 8, 8, 8)
     s0 = S[0, 6, 0, 0]
     assert s0[0] == np.float32(1.0 + 2.0 ** -23) and s0[1] == -np.float32(1.0 + 2.0 ** -23)
     assert s0[2] == 0.0 and s0[3] == 0.0 and np.signbit(s0[3]) and s0[4] == np.inf
