@@ -40,7 +40,7 @@ METRIC = "hydro cell-updates/s (FP64 vs FP32/FP64-mixed batched) at stated error
 BYTES_PER_CELL_STAGE = 374.0     # read interior + 6 face slabs (1664 cells) + write interior (512), 88 B per cell
 FLOPS_PER_CELL_STAGE = 2200.0    # algorithmic operation count per cell-update of one stage
 GHOST_BYTES_PER_CELL = 396.0     # ghost fill: read + write 1152 face-slab cells per 512 interior cells
-SHADOW_BYTES_PER_CELL = 132.0    # FP32 shadow: read 88 B of FP64 interior, write 44 B
+SHADOW_BYTES_PER_CELL = 137.5    # FP32 shadow: read 88 B of FP64 interior, write 44 B + 5.5 B of restriction
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 2 FP64 FMA/clk/SM at the 2070 MHz maximum clock
 # DRAM bytes (read + write) per cell-update of the mixed stage kernel from one ncu capture
 # (profiles/stage_mixed_binary4k.md), valid only for the kernel source it was taken on.

@@ -209,9 +209,9 @@ int hydro_totals(hydro_handle *h, const double *U, double *d_totals, void *strea
  *   n_subgrids in [1, HYDRO_TOTALS_NOALLOC_MAX_SUBGRIDS]; a larger value is
  *             rejected with HYDRO_ERR_INVALID before anything is launched.
  * Needs no handle and allocates nothing: the partial sums live in one fixed
- * device array inside the library (HYDRO_TOTALS_NOALLOC_MAX_SUBGRIDS * 11 * 2
- * doubles, 11.5 MB, held on every GPU that loads the library until the process
- * exits).  The first call on a device looks up that array's device address
+ * device array inside the library (HYDRO_TOTALS_NOALLOC_MAX_SUBGRIDS * 11 * 3
+ * words of 8 bytes, 17.3 MB, held on every GPU that loads the library until
+ * the process exits).  The first call on a device looks up that array's device address
  * with the device current; make that first call before any stream capture.
  * All calls share the array: calls whose work overlaps on the GPU (different
  * streams, or the same stream from several threads without ordering) race and

@@ -535,6 +535,20 @@ __device__ __forceinline__ void stage_interior_async(const float* __restrict__ S
   }
 }
 
+// Pull the interior rows of sub-grid s that the update will read (U_in, and U0
+// when blending) into L2 ahead of time: per field and k-plane one bulk prefetch
+// of the 864 bytes from the 16-byte boundary before cell (3, 3, k+3) through
+// cell (10, 10, k+3).
+__device__ __forceinline__ void prefetch_update_rows(const StageArgs& a, int s) {
+  const int t = threadIdx.x;
+  const bool blend = a.beta != 1.0;
+  if (t >= (blend ? 2 : 1) * NF * NX) return;
+  const double* base = (t < NF * NX) ? a.Uin : a.U0;
+  const int q = t < NF * NX ? t : t - NF * NX;
+  const int f = q >> 3, k = q & 7;
+  prefetch_l2(base + field_offset(s, f) + (size_t)(k + NG) * NP2 + NG * NP + NG - 1, 864);
+}
+
 // Work item and what its processing needs: sub-grid id (-1: queue exhausted,
 // -2: bad id), neighbour table, dt/dx and 1/dx.
 struct Meta {
@@ -588,10 +602,7 @@ __device__ __forceinline__ void direction_pass(const Shared<T>& sh, const StageA
                                                Meta& nxt, double dt, Acc<T> (&acc)[2][NF], T& amax, T gamma,
                                                T eta) {
   const int tid = threadIdx.x;
-  if (D > 0) {
-    cp_async_wait_all();
-    __syncthreads();  // this direction's halo is in place
-  }
+  if (D == 1) prefetch_update_rows(a, cur.s);
   // A: PPM, one (field, pencil) task per iteration
 #pragma unroll 1
   for (int task = tid; task < NF * NPEN; task += THREADS) {
@@ -654,7 +665,12 @@ __device__ __forceinline__ void direction_pass(const Shared<T>& sh, const StageA
         acc[r][f].add_diff(lo, hi);
     }
   }
-  __syncthreads();
+  // the next direction's halo is in place and the face buffers are free (after
+  // z, the loop head's barrier does both for the next sub-grid)
+  if (D < 2) {
+    cp_async_wait_all();
+    __syncthreads();
+  }
 }
 
 template <typename T>

@@ -9,10 +9,11 @@
 //           as signed 128-bit fixed-point numbers with 63 guard bits below the
 //           last bit of a value of exponent E (values more than 63 binades
 //           below E keep their leading bits only).  The integer sum is exact
-//           and independent of order; it becomes a double-double once, scaled
-//           by dx^3, and is stored as the sub-grid's partial (hi, lo);
-//   pass 2: per field and chunk of sub-grids, a Neumaier-compensated sum of
-//           the partials in a fixed order;
+//           and independent of order; it is stored with E (integer work only);
+//   pass 2: per field and chunk of sub-grids, one thread per sub-grid turns
+//           the integer sum into a double-double scaled by dx^3 (the FP64
+//           work, every lane busy), then a Neumaier-compensated sum of these
+//           partials in a fixed order;
 //   pass 3: per field, the chunk sums combined in a fixed order.
 // No atomics anywhere, so the result is bit-reproducible.
 #include "hydro_internal.cuh"
@@ -82,8 +83,12 @@ __device__ __forceinline__ void i128_to_dd(__int128 v, int e2, double& hi, doubl
   }
 }
 
-__global__ void __launch_bounds__(TT) totals_subgrid(const double* __restrict__ U, const double* __restrict__ dx,
-                                                     int n, double* __restrict__ partial) {
+// pass 1 output per (sub-grid, field): the 128-bit sum (low, high word) and E
+// (0x7ff: a value is not finite).
+constexpr int PARTIAL_WORDS = 3;
+
+__global__ void __launch_bounds__(TT) totals_subgrid(const double* __restrict__ U, int n,
+                                                     unsigned long long* __restrict__ partial) {
   const int gw = blockIdx.x * (TT / 32) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (gw >= n * NF) return;
@@ -123,31 +128,42 @@ __global__ void __launch_bounds__(TT) totals_subgrid(const double* __restrict__ 
     acc += (__int128)(((unsigned __int128)hi << 64) | lo);
   }
   if (lane == 0) {
-    double hi, lo;
-    if (emax == 0x7ffu) {  // a non-finite value: make the total non-finite
-      hi = __longlong_as_double(0x7ff8000000000000ll);
-      lo = 0.0;
-    } else {
-      i128_to_dd(acc, (int)emax - 1075 - 63, hi, lo);
-    }
-    const double v = dx[s] * dx[s] * dx[s];
-    const double p = hi * v;
-    const double e = fma(hi, v, -p) + lo * v;
-    partial[((size_t)s * NF + f) * 2 + 0] = p;
-    partial[((size_t)s * NF + f) * 2 + 1] = e;
+    unsigned long long* o = partial + ((size_t)s * NF + f) * PARTIAL_WORDS;
+    o[0] = (unsigned long long)acc;
+    o[1] = (unsigned long long)((unsigned __int128)acc >> 64);
+    o[2] = emax;
   }
 }
 
+// Sub-grid partial dx^3 * sum as a double pair (p, e), p + e the exact value
+// rounded to about 2^-106.
+__device__ __forceinline__ void subgrid_partial(const unsigned long long* w, double dx, double& p, double& e) {
+  const unsigned emax = (unsigned)w[2];
+  if (emax == 0x7ffu) {  // a non-finite value: make the total non-finite
+    p = __longlong_as_double(0x7ff8000000000000ll);
+    e = 0.0;
+    return;
+  }
+  const __int128 acc = (__int128)(((unsigned __int128)w[1] << 64) | w[0]);
+  double hi, lo;
+  i128_to_dd(acc, (int)emax - 1075 - 63, hi, lo);
+  const double v = dx * dx * dx;
+  p = hi * v;
+  e = fma(hi, v, -p) + lo * v;
+}
+
 // pass 2: block (f, chunk) sums the partials of its contiguous range of sub-grids
-__global__ void __launch_bounds__(TT) totals_chunks(const double* __restrict__ partial, int n,
-                                                    double* __restrict__ chunk) {
+__global__ void __launch_bounds__(TT) totals_chunks(const unsigned long long* __restrict__ partial,
+                                                    const double* __restrict__ dx, int n, double* __restrict__ chunk) {
   __shared__ Pair sh[TT / 32];
   const int f = blockIdx.x, ch = blockIdx.y;
   const int a = (int)((long long)n * ch / CHUNKS), b = (int)((long long)n * (ch + 1) / CHUNKS);
   Pair p{0.0, 0.0};
   for (int s = a + (int)threadIdx.x; s < b; s += TT) {
-    neumaier(p, partial[((size_t)s * NF + f) * 2 + 0]);
-    neumaier(p, partial[((size_t)s * NF + f) * 2 + 1]);
+    double ps, pe;
+    subgrid_partial(partial + ((size_t)s * NF + f) * PARTIAL_WORDS, dx[s], ps, pe);
+    neumaier(p, ps);
+    neumaier(p, pe);
   }
   p = warp_merge(p);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = p;
@@ -174,15 +190,15 @@ __global__ void totals_final(const double* __restrict__ chunk, double* __restric
 
 }  // namespace
 
-size_t totals_scratch_doubles(int n) { return (size_t)n * NF * 2 + (size_t)NF * CHUNKS * 2; }
+size_t totals_scratch_doubles(int n) { return (size_t)n * NF * PARTIAL_WORDS + (size_t)NF * CHUNKS * 2; }
 
 cudaError_t launch_totals(const double* U, int n, const double* dx, double* scratch, double* totals,
                           cudaStream_t st) {
-  double* partial = scratch;
-  double* chunk = scratch + (size_t)n * NF * 2;
+  unsigned long long* partial = reinterpret_cast<unsigned long long*>(scratch);
+  double* chunk = scratch + (size_t)n * NF * PARTIAL_WORDS;
   const int warps = n * NF;
-  totals_subgrid<<<(warps + TT / 32 - 1) / (TT / 32), TT, 0, st>>>(U, dx, n, partial);
-  totals_chunks<<<dim3(NF, CHUNKS), TT, 0, st>>>(partial, n, chunk);
+  totals_subgrid<<<(warps + TT / 32 - 1) / (TT / 32), TT, 0, st>>>(U, n, partial);
+  totals_chunks<<<dim3(NF, CHUNKS), TT, 0, st>>>(partial, dx, n, chunk);
   totals_final<<<NF, 32, 0, st>>>(chunk, totals);
   return cudaGetLastError();
 }
@@ -198,7 +214,7 @@ cudaError_t launch_totals(const double* U, int n, const double* dx, double* scra
 // fully reserved up front.  hydro_totals_noalloc serves them: the caller passes
 // the state, the cell widths and the output, and the per-sub-grid partial sums
 // live in the fixed array below, which is part of the loaded module (every
-// GPU that loads the library holds its 11.5 MB until the process exits).
+// GPU that loads the library holds its 17.3 MB until the process exits).
 // ---------------------------------------------------------------------------
 
 #include <mutex>
@@ -207,7 +223,7 @@ cudaError_t launch_totals(const double* U, int n, const double* dx, double* scra
 
 namespace {
 
-static __device__ __align__(256) double g_noalloc_partial[(size_t)HYDRO_TOTALS_NOALLOC_MAX_SUBGRIDS * hydro::NF * 2 +
+static __device__ __align__(256) double g_noalloc_partial[(size_t)HYDRO_TOTALS_NOALLOC_MAX_SUBGRIDS * hydro::NF * 3 +
                                                           (size_t)hydro::NF * 128 * 2];
 
 std::mutex g_noalloc_mu;
