@@ -27,7 +27,7 @@
 // conversions at about 2 per clock per SM, the FP32/INT pipes at 128), the
 // reconstruction and flux run in FP32, the six flux terms of every cell are
 // summed error-free as a float pair (TwoSum cascade), and the conserved update
-// is done in FP64 (2 FP64 operations per value in stage 1, 4 with the blend).
+// is done in FP64 (2 FP64 operations per value in stage 1, 3 with the blend).
 #include <cmath>
 
 #include "hydro_internal.cuh"
@@ -106,20 +106,29 @@ struct Arith<float> {
 // PPM
 // ---------------------------------------------------------------------------
 
-// Monotonized-central slope: (qp - qm)/2 limited by twice the one-sided
-// differences, zero at a local extremum (CW84 eq. 1.8).
+// Twice the monotonized-central slope: (qp - qm) limited by four times the
+// one-sided differences, zero at a local extremum (CW84 eq. 1.8, scaled by 2,
+// which is exact in binary floating point).
 template <typename T>
-__device__ __forceinline__ T limited_slope(T qm, T q0, T qp) {
+__device__ __forceinline__ T limited_slope2(T qm, T q0, T qp) {
   T dl = q0 - qm;
   T dr = qp - q0;
-  T delta = T(0.5) * (qp - qm);
+  T delta = qp - qm;
   T m = fabs(delta);
-  T l = T(2) * fabs(dl);
-  T r = T(2) * fabs(dr);
+  T l = T(4) * fabs(dl);
+  T r = T(4) * fabs(dr);
   m = (l < m) ? l : m;
   m = (r < m) ? r : m;
-  T res = (delta > T(0)) ? m : -m;
-  return (dl * dr <= T(0)) ? T(0) : res;
+  if constexpr (sizeof(T) == 4) {
+    // same sign for dl and dr (else 0); then delta has it too (a zero dl or
+    // dr already made m zero)
+    const unsigned sl = __float_as_uint(dl), sr = __float_as_uint(dr);
+    const unsigned keep = ~(unsigned)((int)(sl ^ sr) >> 31);
+    return __uint_as_float((__float_as_uint(m) | (sl & 0x80000000u)) & keep);
+  } else {
+    T res = (delta > T(0)) ? m : -m;
+    return (dl * dr <= T(0)) ? T(0) : res;
+  }
 }
 
 // CW84 eq. 1.10: flatten at an extremum, else move the far face so that the
@@ -144,10 +153,10 @@ template <typename T>
 __device__ __forceinline__ void ppm_pencil(const T (&q)[NP], T (&ul)[NFACE], T (&ur)[NFACE]) {
   T dm[NP];
 #pragma unroll
-  for (int m = 1; m <= 12; ++m) dm[m] = limited_slope(q[m - 1], q[m], q[m + 1]);
+  for (int m = 1; m <= 12; ++m) dm[m] = limited_slope2(q[m - 1], q[m], q[m + 1]);  // 2 x slope
   T face[NP];
 #pragma unroll
-  for (int m = 1; m <= 11; ++m) face[m] = T(0.5) * (q[m] + q[m + 1]) - (dm[m + 1] - dm[m]) * T(1.0 / 6.0);
+  for (int m = 1; m <= 11; ++m) face[m] = T(0.5) * (q[m] + q[m + 1]) - (dm[m + 1] - dm[m]) * T(1.0 / 12.0);
 #pragma unroll
   for (int m = 2; m <= 11; ++m) {
     T l = face[m - 1], r = face[m];
@@ -219,28 +228,32 @@ __device__ __forceinline__ T face_flux(const T (&UL)[NF], const T (&UR)[NF], int
 // accumulators and update
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  float bp = __fadd_rn(s, -a);
-  float ap = __fadd_rn(s, -bp);
-  e = __fadd_rn(__fadd_rn(a, -ap), __fadd_rn(b, -bp));
+// Packed FP32 pairs: lane x is the thread's first owned cell, lane y its second.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  unsigned long long ra, rb, rd;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+  float2 d;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
+  return d;
 }
 
-template <typename T>
-struct Acc;
-
-template <>
-struct Acc<double> {
-  double v;
-  __device__ __forceinline__ void set_diff(double lo, double hi) { v = lo - hi; }
-  __device__ __forceinline__ void add_diff(double lo, double hi) { v = v + (lo - hi); }
-  // U* = u + lam dU;  out = u0 + beta (U* - u0)
-  __device__ __forceinline__ double update(double u, double u0, double lam, float, float, double beta,
-                                           bool blend) const {
-    double us = fma(lam, v, u);
-    return blend ? fma(beta, us - u0, u0) : us;
-  }
-};
+// Error-free sums (Knuth's TwoSum) on both lanes: s + e == a + b exactly.
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
+  s = add2(a, b);
+  const float2 bp = sub2(s, a);
+  const float2 ap = sub2(s, bp);
+  e = add2(sub2(a, ap), sub2(b, bp));
+}
+// the same for a - b (bit-identical to two_sum2(a, -b))
+__device__ __forceinline__ void two_diff2(float2 a, float2 b, float2& s, float2& e) {
+  s = sub2(a, b);
+  const float2 bp = sub2(s, a);
+  const float2 ap = sub2(s, bp);
+  e = sub2(sub2(a, ap), add2(b, bp));
+}
 
 // RN64(s + c) for a float pair with |c| <= ulp(s)/2, by integer operations.
 // The exact sum has the bits of s followed, after a gap, by those of c; it is
@@ -287,29 +300,57 @@ __device__ __forceinline__ double pair_to_f64(float s, float c) {
   return __longlong_as_double((long long)bits);
 }
 
-// Float pair (s + c) holding the running flux-difference sum: the difference
-// of a direction's two face fluxes is formed exactly first (so a mirrored cell,
-// which sees the two terms swapped and negated, gets the same pair), then added
-// through an error-free TwoSum; the six-term sum is exact to about 2^-48.
+// Flux-difference accumulator of one field for the thread's two owned cells.
+template <typename T>
+struct Acc;
+
+template <>
+struct Acc<double> {
+  double v0, v1;
+  __device__ __forceinline__ void set_diff(double lo0, double hi0, double lo1, double hi1) {
+    v0 = lo0 - hi0;
+    v1 = lo1 - hi1;
+  }
+  __device__ __forceinline__ void add_diff(double lo0, double hi0, double lo1, double hi1) {
+    v0 = v0 + (lo0 - hi0);
+    v1 = v1 + (lo1 - hi1);
+  }
+  // U* = u + lam dU of cell r
+  __device__ __forceinline__ double advance(int r, double u, double lam) const { return fma(lam, r ? v1 : v0, u); }
+};
+
+// Float pair (s + c) per cell holding the running flux-difference sum: the
+// difference of a direction's two face fluxes is formed exactly first (so a
+// mirrored cell, which sees the two terms swapped and negated, gets the same
+// pair), then added through an error-free TwoSum; the six-term sum is exact to
+// about 2^-48.  Both cells advance together in packed FP32x2 operations.
 template <>
 struct Acc<float> {
-  float s, c;
-  __device__ __forceinline__ void set_diff(float a, float b) { two_sum(a, -b, s, c); }
-  __device__ __forceinline__ void add_diff(float a, float b) {
-    float d, e, t, e2;
-    two_sum(a, -b, d, e);
-    two_sum(s, d, t, e2);
-    s = t;
-    c = __fadd_rn(c, __fadd_rn(e, e2));
+  float2 s, c;
+  __device__ __forceinline__ void set_diff(float lo0, float hi0, float lo1, float hi1) {
+    two_diff2(make_float2(lo0, lo1), make_float2(hi0, hi1), s, c);
   }
-  // dU = RN64(s + c) (integer assembly), then U* = fma(lam, dU, u): one FP64
-  // operation in stage 1, three with the blend.
-  __device__ __forceinline__ double update(double u, double u0, double lam, float, float, double beta,
-                                           bool blend) const {
-    float hi = __fadd_rn(s, c);                 // renormalize: |lo| <= ulp(hi)/2
-    float lo = __fadd_rn(c, -__fadd_rn(hi, -s));
-    double us = fma(lam, pair_to_f64(hi, lo), u);
-    return blend ? fma(beta, us - u0, u0) : us;
+  __device__ __forceinline__ void add_diff(float lo0, float hi0, float lo1, float hi1) {
+    float2 d, e, t, e2;
+    two_diff2(make_float2(lo0, lo1), make_float2(hi0, hi1), d, e);
+    two_sum2(s, d, t, e2);
+    s = t;
+    c = add2(c, add2(e, e2));
+  }
+  // U* = u + lam (s + c): both terms widen exactly to FP64 (integer
+  // operations), the small one is added first; two FP64 operations.
+  __device__ __forceinline__ double advance(int r, double u, double lam) const {
+    const double sd = f32_to_f64(r ? s.y : s.x), cd = f32_to_f64(r ? c.y : c.x);
+    return fma(lam, sd, fma(lam, cd, u));
+  }
+  // The same with one FP64 operation: dU = RN64(s + c) assembled by integer
+  // operations after renormalizing the pair (for the blended stages, whose two
+  // further FP64 operations keep the FP64 pipe busier than the integer pipes).
+  __device__ __forceinline__ double advance_one_fma(int r, double u, double lam) const {
+    const float sv = r ? s.y : s.x, cv = r ? c.y : c.x;
+    const float hi = __fadd_rn(sv, cv);  // renormalize: |lo| <= ulp(hi)/2
+    const float lo = __fadd_rn(cv, -__fadd_rn(hi, -sv));
+    return fma(lam, pair_to_f64(hi, lo), u);
   }
 };
 
@@ -318,6 +359,12 @@ __device__ __forceinline__ bool bad64(double v, bool density) {
   const bool nonfinite = (hi & 0x7ff00000u) == 0x7ff00000u;
   const bool nonpos = density && (((int)hi < 0) || ((hi | (unsigned)__double2loint(v)) == 0u));
   return nonfinite || nonpos;
+}
+
+// Bit 31 of the result is set iff v is not finite: the exponent field plus one
+// overflows into it only for the all-ones exponent.  OR-ed over many values.
+__device__ __forceinline__ unsigned nonfinite_bit(double v) {
+  return ((unsigned)__double2hiint(v) & 0x7ff00000u) + 0x00100000u;
 }
 
 // ---------------------------------------------------------------------------
@@ -556,7 +603,6 @@ struct Meta {
   int item;
   int s;
   double lam, idx;
-  float lh, ll;
 };
 
 // Warp 7 (threads 224..255, one PPM task fewer than threads 0..191) takes the
@@ -583,8 +629,6 @@ __device__ __forceinline__ void prefetch_meta(const StageArgs& a, double dt, Met
       const double lam = dt * idx;
       m.lam = lam;
       m.idx = idx;
-      m.lh = (float)lam;
-      m.ll = (float)(lam - (double)(float)lam);
     }
   }
   if (lane == 0) {
@@ -599,7 +643,7 @@ __device__ __forceinline__ void prefetch_meta(const StageArgs& a, double dt, Met
 // owned cells.  During z, warp 7 also prefetches the next work item.
 template <typename T, int D>
 __device__ __forceinline__ void direction_pass(const Shared<T>& sh, const StageArgs& a, const Meta& cur,
-                                               Meta& nxt, double dt, Acc<T> (&acc)[2][NF], T& amax, T gamma,
+                                               Meta& nxt, double dt, Acc<T> (&acc)[NF], T& amax, T gamma,
                                                T eta) {
   const int tid = threadIdx.x;
   if (D == 1) prefetch_update_rows(a, cur.s);
@@ -648,21 +692,24 @@ __device__ __forceinline__ void direction_pass(const Shared<T>& sh, const StageA
     for (int f = 0; f < NF; ++f) sh.fsl[f * FACES_DIR + fc] = F[f];
   }
   __syncthreads();
-  // C: flux differences of direction D for the two owned cells
-#pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    const int c = owned_cell(r);
+  // C: flux differences of direction D for the two owned cells (k and k+1:
+  // same pencil for x and y, adjacent faces of one pencil for z)
+  {
+    const int c = owned_cell(0);
     const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
-    const int p = D == 0 ? (k * 8 + j) : (D == 1 ? (k * 8 + i) : (j * 8 + i));
-    const int id = D == 0 ? i : (D == 1 ? j : k);
-    const int base = p * NFACE + id;
+    const int p0 = D == 0 ? (k * 8 + j) : (D == 1 ? (k * 8 + i) : (j * 8 + i));
+    const int p1 = D == 2 ? p0 : p0 + 8;
+    const int id0 = D == 0 ? i : (D == 1 ? j : k);
+    const int id1 = D == 2 ? k + 1 : id0;
+    const int b0 = p0 * NFACE + id0, b1 = p1 * NFACE + id1;
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-      T lo = sh.fsl[f * FACES_DIR + base], hi = sh.fsl[f * FACES_DIR + base + 1];
+      const T* F = sh.fsl + f * FACES_DIR;
+      const T lo0 = F[b0], hi0 = F[b0 + 1], lo1 = F[b1], hi1 = F[b1 + 1];
       if (D == 0)
-        acc[r][f].set_diff(lo, hi);
+        acc[f].set_diff(lo0, hi0, lo1, hi1);
       else
-        acc[r][f].add_diff(lo, hi);
+        acc[f].add_diff(lo0, hi0, lo1, hi1);
     }
   }
   // the next direction's halo is in place and the face buffers are free (after
@@ -671,6 +718,54 @@ __device__ __forceinline__ void direction_pass(const Shared<T>& sh, const StageA
     cp_async_wait_all();
     __syncthreads();
   }
+}
+
+// U_out = U* (or U0 + beta (U* - U0) when BLEND) for the two owned cells of
+// sub-grid s; SHADOW (mixed only) also writes the rounded cells and their
+// 2x2x2 restriction (FP32 sum in (k, j, i) order, the partner cells by warp
+// shuffles).  Returns non-zero if a value is not finite or a density <= 0.
+template <typename T, bool BLEND, bool SHADOW>
+__device__ __forceinline__ unsigned update_cells(const StageArgs& a, int s, const Acc<T> (&acc)[NF], double lam) {
+  const int tid = threadIdx.x;
+  const int c0 = owned_cell(0);
+  const size_t cell0 = (size_t)((c0 >> 6) + NG) * NP2 + (((c0 >> 3) & 7) + NG) * NP + ((c0 & 7) + NG);
+  unsigned nf = 0, bad = 0;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    double v[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const size_t o = field_offset(s, f) + cell0 + (size_t)r * NP2;
+      if constexpr (BLEND) {
+        double us;
+        if constexpr (sizeof(T) == 4)
+          us = acc[f].advance_one_fma(r, a.Uin[o], lam);
+        else
+          us = acc[f].advance(r, a.Uin[o], lam);
+        const double u0 = a.U0[o];
+        v[r] = fma(a.beta, us - u0, u0);
+      } else {
+        v[r] = acc[f].advance(r, a.Uin[o], lam);
+      }
+      a.Uout[o] = v[r];
+      nf |= nonfinite_bit(v[r]);
+      if (f == F_RHO) bad |= bad64(v[r], true);
+    }
+    if constexpr (SHADOW && sizeof(T) == 4) {
+      float* So = a.Sout + ((size_t)s * NF + f) * SHADOW_FIELD;
+      const float x0 = f64_to_f32(v[0]), x1 = f64_to_f32(v[1]);
+      So[c0] = x0;
+      So[c0 + 64] = x1;
+      const float b0 = __shfl_xor_sync(0xffffffffu, x0, 1), b1 = __shfl_xor_sync(0xffffffffu, x1, 1);
+      const float e0 = __shfl_xor_sync(0xffffffffu, x0, 8), e1 = __shfl_xor_sync(0xffffffffu, x1, 8);
+      const float d0 = __shfl_xor_sync(0xffffffffu, x0, 9), d1 = __shfl_xor_sync(0xffffffffu, x1, 9);
+      float m = __fadd_rn(__fadd_rn(__fadd_rn(x0, b0), e0), d0);
+      m = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(m, x1), b1), e1), d1);
+      const int cc = (tid >> 6) * 16 + ((tid >> 4) & 3) * 4 + ((tid >> 1) & 3);
+      if ((tid & 9) == 0) So[SHADOW_COARSE + cc] = __fmul_rn(m, 0.125f);  // i and j even
+    }
+  }
+  return bad | (nf >> 31);
 }
 
 template <typename T>
@@ -688,7 +783,8 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(
   const T gamma = T(a.gamma), eta = T(a.eta);
   const double dt = a.dt_dev ? *a.dt_dev : a.dt;
   const bool blend = a.beta != 1.0;
-  int bad = 0;
+  const bool shadow_out = sizeof(T) == 4 && a.Sout != nullptr;
+  unsigned bad = 0;
 
   // prologue: the first work item, its neighbour table and x halo
   if ((tid >> 5) == THREADS / 32 - 1) prefetch_meta(a, dt, s_meta[0]);
@@ -731,46 +827,23 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(
     cp_async_wait_all();
     __syncthreads();  // interior tile and x halo in place
 
-    Acc<T> acc[2][NF];
+    Acc<T> acc[NF];
     T amax = T(0);
     direction_pass<T, 0>(sh, a, cur, nxt, dt, acc, amax, gamma, eta);
     direction_pass<T, 1>(sh, a, cur, nxt, dt, acc, amax, gamma, eta);
     direction_pass<T, 2>(sh, a, cur, nxt, dt, acc, amax, gamma, eta);
 
-    // update of the owned cells; mixed precision also writes the output's
-    // shadow: the rounded cells and their 2x2x2 restriction (FP32 sum in
-    // (k, j, i) order, the partners' cells by warp shuffles)
-    const double lam = cur.lam;
-    const float lh = cur.lh, ll = cur.ll;
-    const int c0 = owned_cell(0);
-    const size_t cell0 = (size_t)((c0 >> 6) + NG) * NP2 + (((c0 >> 3) & 7) + NG) * NP + ((c0 & 7) + NG);
-    const bool shadow_out = sizeof(T) == 4 && a.Sout != nullptr;
-    const bool restrict_lane = (tid & 9) == 0;  // i and j even
-    const int cc = (tid >> 6) * 16 + ((tid >> 4) & 3) * 4 + ((tid >> 1) & 3);
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      double v[2];
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        const size_t o = field_offset(s, f) + cell0 + (size_t)r * NP2;
-        const double u = a.Uin[o];
-        const double u0 = blend ? a.U0[o] : 0.0;
-        v[r] = acc[r][f].update(u, u0, lam, lh, ll, a.beta, blend);
-        a.Uout[o] = v[r];
-        bad |= bad64(v[r], f == F_RHO);
-      }
-      if (shadow_out) {
-        float* So = a.Sout + ((size_t)s * NF + f) * SHADOW_FIELD;
-        const float x0 = f64_to_f32(v[0]), x1 = f64_to_f32(v[1]);
-        So[c0] = x0;
-        So[c0 + 64] = x1;
-        const float b0 = __shfl_xor_sync(0xffffffffu, x0, 1), b1 = __shfl_xor_sync(0xffffffffu, x1, 1);
-        const float e0 = __shfl_xor_sync(0xffffffffu, x0, 8), e1 = __shfl_xor_sync(0xffffffffu, x1, 8);
-        const float d0 = __shfl_xor_sync(0xffffffffu, x0, 9), d1 = __shfl_xor_sync(0xffffffffu, x1, 9);
-        float m = __fadd_rn(__fadd_rn(__fadd_rn(x0, b0), e0), d0);
-        m = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(m, x1), b1), e1), d1);
-        if (restrict_lane) So[SHADOW_COARSE + cc] = __fmul_rn(m, 0.125f);
-      }
+    // update of the owned cells (and, mixed, the output's shadow)
+    if (blend) {
+      if (shadow_out)
+        bad |= update_cells<T, true, true>(a, s, acc, cur.lam);
+      else
+        bad |= update_cells<T, true, false>(a, s, acc, cur.lam);
+    } else {
+      if (shadow_out)
+        bad |= update_cells<T, false, true>(a, s, acc, cur.lam);
+      else
+        bad |= update_cells<T, false, false>(a, s, acc, cur.lam);
     }
 
     // largest face speed of this sub-grid (non-negative values order as their bits)
