@@ -140,8 +140,9 @@ int hydro_step(hydro_handle *h, const hydro_batch *batch, const double *U_in, co
  *     below the float32 normal range become signed zero, finite values beyond
  *     it infinity);
  *   S[s][f][512 + (K*4 + J)*4 + I] = the float32 sum of the eight rounded cells
- *     (2K+dk, 2J+dj, 2I+di), added in (dk, dj, di) order, times 1/8: the
- *     restriction a coarser neighbour reads as its halo.
+ *     c(dk,dj,di) = (2K+dk, 2J+dj, 2I+di), added pairwise as
+ *     ((c000 + c001) + (c010 + c011)) + ((c100 + c101) + (c110 + c111)),
+ *     times 1/8: the restriction a coarser neighbour reads as its halo.
  *   U DEVICE padded state; S DEVICE float[n_subgrids][11][576], 16-byte
  *   aligned.  Works with either precision of handle. */
 int hydro_shadow(hydro_handle *h, const double *U, float *S, void *stream);

@@ -99,8 +99,8 @@ cudaError_t launch_ghost_fill(const GhostArgs& a, int threads, cudaStream_t st) 
 // ---------------------------------------------------------------------------
 // FP32 shadow of the interior: per sub-grid field, the 512 interior cells
 // RN32(U[s][f][k+3][j+3][i+3]) at (k*8 + j)*8 + i, then the 64 cells of its
-// 2x2x2 restriction at 512 + (K*4 + J)*4 + I: the FP32 sum of the 8 rounded
-// cells in (k, j, i) order, times 1/8.  The mixed stage reads its
+// 2x2x2 restriction at 512 + (K*4 + J)*4 + I: the FP32 pairwise sum of the 8
+// rounded cells (pairs in i, then in j, then in k), times 1/8.  The mixed stage reads its
 // reconstruction inputs (own interior, the neighbours' boundary layers and the
 // finer neighbours' restrictions) from the shadow: half the bytes of the FP64
 // state, in 32-byte rows, every halo cell a plain copy.
@@ -136,13 +136,14 @@ __global__ void __launch_bounds__(256) shadow_kernel(const double* __restrict__ 
       const int cc = c - SHADOW_COARSE;
       const int I = cc & 3, J = (cc >> 2) & 3, K = cc >> 4;
       const double* b = u + (size_t)(2 * K + NG) * NP2 + (2 * J + NG) * NP + (2 * I + NG);
-      float sum = shadow_round(b[0]);
+      float h[2];  // pairwise: ((c000 + c001) + (c010 + c011)) + ((c100 + c101) + (c110 + c111)), c_{dk dj di}
 #pragma unroll
-      for (int m = 1; m < 8; ++m) {  // m = dk*4 + dj*2 + di
-        const int dk = m >> 2, dj = (m >> 1) & 1, di = m & 1;
-        sum = __fadd_rn(sum, shadow_round(b[dk * NP2 + dj * NP + di]));
+      for (int dk = 0; dk < 2; ++dk) {
+        const double* bk = b + dk * NP2;
+        h[dk] = __fadd_rn(__fadd_rn(shadow_round(bk[0]), shadow_round(bk[1])),
+                          __fadd_rn(shadow_round(bk[NP]), shadow_round(bk[NP + 1])));
       }
-      S[g] = __fmul_rn(sum, 0.125f);
+      S[g] = __fmul_rn(__fadd_rn(h[0], h[1]), 0.125f);
     }
   }
 }

@@ -60,8 +60,8 @@ struct GhostArgs {
 };
 
 // FP32 shadow of a sub-grid field: the 8^3 interior [k][j][i], then its 4^3
-// restriction [K][J][I] (FP32 mean of the 2x2x2 rounded cells, summed in
-// (k, j, i) order), which a coarser neighbour reads as its halo.
+// restriction [K][J][I] (FP32 mean of the 2x2x2 rounded cells, summed
+// pairwise: in i, then j, then k), which a coarser neighbour reads as its halo.
 constexpr int SHADOW_COARSE = CELLS;            // offset of the restriction
 constexpr int SHADOW_FIELD = CELLS + CELLS / 8;  // 576 floats per field
 

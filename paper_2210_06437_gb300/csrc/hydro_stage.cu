@@ -722,16 +722,24 @@ __device__ __forceinline__ void direction_pass(const Shared<T>& sh, const StageA
 
 // U_out = U* (or U0 + beta (U* - U0) when BLEND) for the two owned cells of
 // sub-grid s; SHADOW (mixed only) also writes the rounded cells and their
-// 2x2x2 restriction (FP32 sum in (k, j, i) order, the partner cells by warp
-// shuffles).  Returns non-zero if a value is not finite or a density <= 0.
-template <typename T, bool BLEND, bool SHADOW>
-__device__ __forceinline__ unsigned update_cells(const StageArgs& a, int s, const Acc<T> (&acc)[NF], double lam) {
+// 2x2x2 restriction (FP32 pairwise sum, the partner cells by warp shuffles).  Returns non-zero if a value is not finite or a density <= 0.
+template <typename T, bool BLEND, bool SHADOW, int F0, int F1>
+__device__ __forceinline__ unsigned update_fields(const StageArgs& a, int s, const Acc<T> (&acc)[NF], double lam,
+                                                  size_t cell0, int c0, unsigned& nf) {
   const int tid = threadIdx.x;
-  const int c0 = owned_cell(0);
-  const size_t cell0 = (size_t)((c0 >> 6) + NG) * NP2 + (((c0 >> 3) & 7) + NG) * NP + ((c0 & 7) + NG);
-  unsigned nf = 0, bad = 0;
+  unsigned bad = 0;
+  // every load of the group first: one memory latency per group, not per field
+  double uin[F1 - F0][2], u0v[BLEND ? F1 - F0 : 1][2];
 #pragma unroll
-  for (int f = 0; f < NF; ++f) {
+  for (int f = F0; f < F1; ++f)
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const size_t o = field_offset(s, f) + cell0 + (size_t)r * NP2;
+      uin[f - F0][r] = a.Uin[o];
+      if constexpr (BLEND) u0v[f - F0][r] = a.U0[o];
+    }
+#pragma unroll
+  for (int f = F0; f < F1; ++f) {
     double v[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -739,13 +747,13 @@ __device__ __forceinline__ unsigned update_cells(const StageArgs& a, int s, cons
       if constexpr (BLEND) {
         double us;
         if constexpr (sizeof(T) == 4)
-          us = acc[f].advance_one_fma(r, a.Uin[o], lam);
+          us = acc[f].advance_one_fma(r, uin[f - F0][r], lam);
         else
-          us = acc[f].advance(r, a.Uin[o], lam);
-        const double u0 = a.U0[o];
+          us = acc[f].advance(r, uin[f - F0][r], lam);
+        const double u0 = u0v[f - F0][r];
         v[r] = fma(a.beta, us - u0, u0);
       } else {
-        v[r] = acc[f].advance(r, a.Uin[o], lam);
+        v[r] = acc[f].advance(r, uin[f - F0][r], lam);
       }
       a.Uout[o] = v[r];
       nf |= nonfinite_bit(v[r]);
@@ -756,14 +764,32 @@ __device__ __forceinline__ unsigned update_cells(const StageArgs& a, int s, cons
       const float x0 = f64_to_f32(v[0]), x1 = f64_to_f32(v[1]);
       So[c0] = x0;
       So[c0 + 64] = x1;
-      const float b0 = __shfl_xor_sync(0xffffffffu, x0, 1), b1 = __shfl_xor_sync(0xffffffffu, x1, 1);
-      const float e0 = __shfl_xor_sync(0xffffffffu, x0, 8), e1 = __shfl_xor_sync(0xffffffffu, x1, 8);
-      const float d0 = __shfl_xor_sync(0xffffffffu, x0, 9), d1 = __shfl_xor_sync(0xffffffffu, x1, 9);
-      float m = __fadd_rn(__fadd_rn(__fadd_rn(x0, b0), e0), d0);
-      m = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(m, x1), b1), e1), d1);
+      // pairs in i (lane ^ 1), then in j (lane ^ 8), both cells of the k-pair at once
+      const float2 xi = make_float2(x0, x1);
+      const float2 p = add2(xi, make_float2(__shfl_xor_sync(0xffffffffu, x0, 1), __shfl_xor_sync(0xffffffffu, x1, 1)));
+      const float2 t = add2(p, make_float2(__shfl_xor_sync(0xffffffffu, p.x, 8), __shfl_xor_sync(0xffffffffu, p.y, 8)));
       const int cc = (tid >> 6) * 16 + ((tid >> 4) & 3) * 4 + ((tid >> 1) & 3);
-      if ((tid & 9) == 0) So[SHADOW_COARSE + cc] = __fmul_rn(m, 0.125f);  // i and j even
+      if ((tid & 9) == 0) So[SHADOW_COARSE + cc] = __fmul_rn(__fadd_rn(t.x, t.y), 0.125f);  // i and j even
     }
+  }
+  return bad;
+}
+
+// U_out = U* (or U0 + beta (U* - U0) when BLEND) for the two owned cells of
+// sub-grid s; SHADOW (mixed only) also writes the rounded cells and their
+// 2x2x2 restriction (FP32 pairwise sum, the partner cells by warp shuffles).  The loads are issued in one group (two with the blend, which
+// reads twice as many) so that their latencies overlap.  Returns non-zero if
+// a value is not finite or a density <= 0.
+template <typename T, bool BLEND, bool SHADOW>
+__device__ __forceinline__ unsigned update_cells(const StageArgs& a, int s, const Acc<T> (&acc)[NF], double lam) {
+  const int c0 = owned_cell(0);
+  const size_t cell0 = (size_t)((c0 >> 6) + NG) * NP2 + (((c0 >> 3) & 7) + NG) * NP + ((c0 & 7) + NG);
+  unsigned nf = 0, bad = 0;
+  if constexpr (BLEND) {
+    bad |= update_fields<T, BLEND, SHADOW, 0, 6>(a, s, acc, lam, cell0, c0, nf);
+    bad |= update_fields<T, BLEND, SHADOW, 6, NF>(a, s, acc, lam, cell0, c0, nf);
+  } else {
+    bad |= update_fields<T, BLEND, SHADOW, 0, NF>(a, s, acc, lam, cell0, c0, nf);
   }
   return bad | (nf >> 31);
 }

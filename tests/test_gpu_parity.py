@@ -372,13 +372,11 @@ def test_shadow_is_rounded_interior(hydro, oracle_mod, prec):
     n = w.grid.n
     exp = _round32_away(U[IN])
     assert np.array_equal(S[:, :, :512].view(np.uint32), exp.reshape(n, 11, 512).view(np.uint32))
-    # restriction: float32 sum of the 8 rounded cells in (dk, dj, di) order, times 1/8
-    e = exp.reshape(n, 11, 4, 2, 4, 2, 4, 2)
-    acc = e[:, :, :, 0, :, 0, :, 0].copy()
-    for m in range(1, 8):
-        dk, dj, di = m >> 2, (m >> 1) & 1, m & 1
-        acc = acc + e[:, :, :, dk, :, dj, :, di]
-    acc = acc * np.float32(0.125)
+    # restriction: float32 pairwise sum of the 8 rounded cells (in i, then j, then k), times 1/8
+    e = exp.reshape(n, 11, 4, 2, 4, 2, 4, 2)     # [s, f, K, dk, J, dj, I, di]
+    c = lambda dk, dj, di: e[:, :, :, dk, :, dj, :, di]
+    h = [(c(dk, 0, 0) + c(dk, 0, 1)) + (c(dk, 1, 0) + c(dk, 1, 1)) for dk in (0, 1)]
+    acc = (h[0] + h[1]) * np.float32(0.125)
     assert acc.dtype == np.float32
     assert np.array_equal(S[:, :, 512:].view(np.uint32), acc.reshape(n, 11, 64).view(np.uint32))
     S = S[:, :, :512].reshape(n, 11, 8, 8, 8)
