@@ -605,16 +605,31 @@ struct Meta {
   double lam, idx;
 };
 
-// Warp 7 (threads 224..255, one PPM task fewer than threads 0..191) takes the
-// next work item from the queue and reads its neighbour table into m.
-__device__ __forceinline__ void prefetch_meta(const StageArgs& a, double dt, Meta& m) {
+// The next work item as warp 7 (threads 224..255, one PPM task fewer than
+// threads 0..191) fetches it while the current one is processed: the queue
+// ticket during x, the sub-grid id during y, the neighbour table during z, so
+// that each dependent load has a whole direction pass to arrive.
+struct Pf {
+  int item;  // queue ticket (lane 0 until shuffled)
+  int s;     // its sub-grid id, -1 past the end of the queue
+};
+
+__device__ __forceinline__ void pf_ticket(const StageArgs& a, Pf& pf) {
+  if ((threadIdx.x & 31) == 0) pf.item = (int)atomicAdd(a.queue, 1u);
+}
+
+__device__ __forceinline__ void pf_id(const StageArgs& a, Pf& pf) {
+  pf.item = __shfl_sync(0xffffffffu, pf.item, 0);
+  pf.s = pf.item < a.n_items ? a.ids[pf.item] : -1;
+}
+
+// Check the fetched id and read its neighbour table into m.
+__device__ __forceinline__ void pf_finish(const StageArgs& a, double dt, const Pf& pf, Meta& m) {
   const int lane = threadIdx.x & 31;
-  int item = 0;
-  if (lane == 0) item = (int)atomicAdd(a.queue, 1u);
-  item = __shfl_sync(0xffffffffu, item, 0);
+  const int item = pf.item;
   int s = -1;
   if (item < a.n_items) {
-    s = a.ids[item];
+    s = pf.s;
     if (s < 0 || s >= a.n_sub) {
       if (lane == 0) atomicOr(a.err, ERRBIT_BAD_ID);
       s = -2;
@@ -637,13 +652,21 @@ __device__ __forceinline__ void prefetch_meta(const StageArgs& a, double dt, Met
   }
 }
 
+// All three steps at once (loop prologue and after a bad id).
+__device__ __forceinline__ void prefetch_meta(const StageArgs& a, double dt, Meta& m) {
+  Pf pf;
+  pf_ticket(a, pf);
+  pf_id(a, pf);
+  pf_finish(a, dt, pf, m);
+}
+
 // One direction of the stage: PPM of every (field, pencil), the next
 // direction's halo gather (issued once the halo buffer is free; after z, the
 // next sub-grid's x halo), the face fluxes and the flux differences of the two
-// owned cells.  During z, warp 7 also prefetches the next work item.
+// owned cells.  Warp 7 also fetches the next work item, one step per pass.
 template <typename T, int D>
 __device__ __forceinline__ void direction_pass(const Shared<T>& sh, const StageArgs& a, const Meta& cur,
-                                               Meta& nxt, double dt, Acc<T> (&acc)[NF], T& amax, T gamma,
+                                               Meta& nxt, Pf& pf, double dt, Acc<T> (&acc)[NF], T& amax, T gamma,
                                                T eta) {
   const int tid = threadIdx.x;
   if (D == 1) prefetch_update_rows(a, cur.s);
@@ -667,7 +690,11 @@ __device__ __forceinline__ void direction_pass(const Shared<T>& sh, const StageA
       sh.fsr[f * FACES_DIR + p * NFACE + m] = ur[m];
     }
   }
-  if (D == 2 && (tid >> 5) == THREADS / 32 - 1) prefetch_meta(a, dt, nxt);
+  if ((tid >> 5) == THREADS / 32 - 1) {
+    if (D == 0) pf_ticket(a, pf);
+    if (D == 1) pf_id(a, pf);
+    if (D == 2) pf_finish(a, dt, pf, nxt);
+  }
   __syncthreads();
   // the halo buffer is free: start gathering the next slabs; after z the tile
   // is free too, and the mixed path starts copying the next interior
@@ -854,10 +881,11 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(
     __syncthreads();  // interior tile and x halo in place
 
     Acc<T> acc[NF];
+    Pf pf;
     T amax = T(0);
-    direction_pass<T, 0>(sh, a, cur, nxt, dt, acc, amax, gamma, eta);
-    direction_pass<T, 1>(sh, a, cur, nxt, dt, acc, amax, gamma, eta);
-    direction_pass<T, 2>(sh, a, cur, nxt, dt, acc, amax, gamma, eta);
+    direction_pass<T, 0>(sh, a, cur, nxt, pf, dt, acc, amax, gamma, eta);
+    direction_pass<T, 1>(sh, a, cur, nxt, pf, dt, acc, amax, gamma, eta);
+    direction_pass<T, 2>(sh, a, cur, nxt, pf, dt, acc, amax, gamma, eta);
 
     // update of the owned cells (and, mixed, the output's shadow)
     if (blend) {
