@@ -428,3 +428,54 @@ def test_shadow_entry_errors(hydro):
     with pytest.raises(hydro.HydroError) as e:  # an RK3 step must advance every sub-grid
         g.rk3_step(Ud, 1e-3, torch.empty_like(Ud), torch.empty_like(Ud), ids=np.arange(w.grid.n - 1))
     assert e.value.code == -1
+
+
+# ---------------------------------------------------------------------------
+# flux form and dual-energy variants
+# ---------------------------------------------------------------------------
+
+def _fast_flow(U, mach_scale, gamma=5.0 / 3.0):
+    """Copy of U with the momenta scaled by mach_scale and the total energy
+    raised by the added kinetic energy (internal energy and tau unchanged)."""
+    V = U.copy()
+    rho, s = V[:, 0], V[:, 1:4]
+    ek = 0.5 * (s ** 2).sum(axis=1) / rho
+    V[:, 1:4] *= mach_scale
+    V[:, 4] += (mach_scale ** 2 - 1.0) * ek
+    return V
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("form,de_switch,mach", [(1, 1e-3, 1.0), (0, 0.0, 1.0), (0, 1e-3, 100.0), (1, 1e-3, 100.0)])
+def test_flux_form_and_dual_energy(hydro, oracle_mod, prec, form, de_switch, mach):
+    """KT flux form, the dual-energy switch disabled, and a fast flow in which
+    the switch selects e_int = tau^gamma in many cells: one blended stage
+    against the oracle with the same options."""
+    w = W.config(2)
+    U = _fast_flow(w.state(), mach)
+    o = oracle_mod.Oracle(w.grid, flux_form=form, de_switch=de_switch)
+    o.fill_ghosts(U)
+    ui = U[IN]
+    ek = 0.5 * (ui[:, 1] ** 2 + ui[:, 2] ** 2 + ui[:, 3] ** 2) / ui[:, 0]
+    switched = np.mean(ui[:, 4] - ek < 1e-3 * ui[:, 4])
+    if mach > 1.0:
+        assert switched > 0.05      # the dual-energy branch is exercised
+    else:
+        assert switched == 0.0
+    _, ms, st = o.stage(U, 0.0)
+    assert st == 0
+    dt = 0.4 / ms[1]
+    U0 = U.copy()
+    U0[IN] *= 1.0 + 1e-3 * np.cos(np.arange(U0[IN].size).reshape(U0[IN].shape))
+    ref, ms_o, st = o.stage(U, dt, U0=U0, beta=2.0 / 3.0)
+    assert st == 0
+    g = hydro.HydroGrid(w.grid, precision=prec, flux_form=form, de_switch=de_switch)
+    Ud = _dev(U)
+    out, msd = g.step(Ud, dt, U0=_dev(U0), beta=2.0 / 3.0, U_out=Ud.clone())
+    g.sync()
+    got = _host(out)
+    err = field_errors(got, ref)
+    assert np.all(err <= TOL[prec]), (err, field_errors(got, ref, plain=True))
+    if prec == "fp64":
+        assert np.all(field_errors(got, ref, plain=True) <= TOL[prec])
+    np.testing.assert_allclose(msd.cpu().numpy(), ms_o, rtol=1e-14 if prec == "fp64" else 1e-6)
