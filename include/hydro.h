@@ -195,6 +195,29 @@ int hydro_rk3_step(hydro_handle *h, const hydro_batch *batch, double *U, double 
 int hydro_rk3_step_cfl(hydro_handle *h, const hydro_batch *batch, double *U, double *scratch1, double *scratch2,
                        double cfl, double *d_max_speed, double *d_dt_out, void *stream);
 
+/* n_steps successive SSP-RK3 steps in one call, each exactly as
+ * hydro_rk3_step_cfl followed by hydro_totals, replayed from one CUDA graph:
+ * step k takes dt = cfl / d_max_speed[1] from the speeds left by step k-1 (or
+ * by the caller on entry), writes it to d_dt_out[k] if d_dt_out is not NULL,
+ * and writes the totals of its new state to d_totals[11*k .. 11*k+10] if
+ * d_totals is not NULL (DEVICE double[n_steps][11]).  The results are
+ * bit-identical to n_steps separate calls; a mixed-precision handle writes
+ * the FP32 shadow of U once per call instead of once per step (the last
+ * stage of each step writes the next step's shadow).
+ *   n_steps in [1, HYDRO_RK3_RUN_MAX_STEPS]; other arguments as
+ *   hydro_rk3_step_cfl.  One graph is kept per (batch, buffers, n_steps,
+ *   cfl, output pointers) combination. */
+#define HYDRO_RK3_RUN_MAX_STEPS 1024
+int hydro_rk3_run_cfl(hydro_handle *h, const hydro_batch *batch, double *U, double *scratch1, double *scratch2,
+                      double cfl, int32_t n_steps, double *d_max_speed, double *d_dt_out, double *d_totals,
+                      void *stream);
+
+/* Capture (and cache) the graph hydro_rk3_run_cfl would replay for these
+ * arguments without launching anything, so that a later call starts at once.
+ * Same validation and return codes as hydro_rk3_run_cfl. */
+int hydro_rk3_run_prepare(hydro_handle *h, const hydro_batch *batch, double *U, double *scratch1, double *scratch2,
+                          double cfl, int32_t n_steps, double *d_max_speed, double *d_dt_out, double *d_totals);
+
 /* Grid totals (diagnostics): d_totals[f] = sum_s dx_s^3 * sum_interior U_f,
  * compensated and in a fixed order, so the result is deterministic.
  *   U DEVICE padded state; d_totals DEVICE double[11]. */

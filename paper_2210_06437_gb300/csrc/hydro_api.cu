@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "hydro.h"
@@ -22,13 +23,28 @@ using namespace hydro;
 
 namespace {
 
-struct GraphEntry {
+// What a captured RK3 graph depends on: the batch ids and buffers it was
+// captured with, and, for a multi-step run, the step count and the per-step
+// outputs (0 steps: the single-step graph, whose dt is set before each launch).
+struct GraphKey {
   const int32_t* ids;
   int32_t n_items;
   double* U;
   double* s1;
   double* s2;
   double* dms;
+  int32_t n_steps;
+  double cfl;
+  double* dt_out;
+  double* totals;
+  bool operator==(const GraphKey& o) const {
+    return ids == o.ids && n_items == o.n_items && U == o.U && s1 == o.s1 && s2 == o.s2 && dms == o.dms &&
+           n_steps == o.n_steps && cfl == o.cfl && dt_out == o.dt_out && totals == o.totals;
+  }
+};
+
+struct GraphEntry {
+  GraphKey key;
   cudaGraphExec_t exec;
   int kernels;
 };
@@ -355,9 +371,8 @@ int hydro_fill_ghosts(hydro_handle* h, double* U, void* stream) {
 
 namespace {
 
-int rk3_common(hydro_handle* h, const hydro_batch* batch, double* U, double* scratch1, double* scratch2,
-               double dt, double cfl, double* d_max_speed, double* d_dt_out, void* stream) {
-  if (!h) return HYDRO_ERR_INVALID;
+int check_rk3(hydro_handle* h, const hydro_batch* batch, double* U, double* scratch1, double* scratch2,
+              double* d_max_speed, double* d_dt_out) {
   int rc = check_batch(h, batch);
   if (rc) return rc;
   if (!U || !scratch1 || !scratch2 || !d_max_speed) return fail(h, HYDRO_ERR_INVALID, "NULL pointer");
@@ -368,6 +383,96 @@ int rk3_common(hydro_handle* h, const hydro_batch* batch, double* U, double* scr
     return fail(h, HYDRO_ERR_INVALID, "misaligned pointer");
   if (batch->n_items != h->n)
     return fail(h, HYDRO_ERR_INVALID, "an RK3 step advances every sub-grid: n_items must equal n_subgrids");
+  return HYDRO_OK;
+}
+
+// Enqueue the three stages of one RK3 step on cs.  Mixed precision: Sin is the
+// shadow of U, Smid the other shadow buffer; Sout_last, if not NULL, receives
+// the shadow of the new U (it must be Smid: free again after stage 2).
+int enqueue_rk3_stages(hydro_handle* h, const int32_t* ids, int ni, double* U, double* s1, double* s2,
+                       unsigned long long* ms, float* Sin, float* Smid, float* Sout_last, cudaStream_t cs) {
+  int rc = enqueue_stage(h, ids, ni, U, Sin, nullptr, 1.0, 0.0, h->d_dt, s1, Smid, ms, 0, cs);
+  if (!rc) rc = enqueue_stage(h, ids, ni, s1, Smid, U, 0.25, 0.0, h->d_dt, s2, Sin, h->d_ms_tmp, 1, cs);
+  if (!rc)
+    rc = enqueue_stage(h, ids, ni, s2, Sin, U, 2.0 / 3.0, 0.0, h->d_dt, U, Sout_last, h->d_ms_tmp, 2, cs);
+  return rc;
+}
+
+// Find or capture the graph of key k.  n_steps == 0: one RK3 step whose dt the
+// caller sets in h->d_dt before each launch.  n_steps >= 1: that many steps,
+// each with dt = cfl / d_max_speed[1] chosen on the device and the totals of
+// the new state, the shadow written once and then chained from step to step.
+int get_graph(hydro_handle* h, const GraphKey& k, GraphEntry** out) {
+  for (auto& e : h->graphs)
+    if (e.key == k) {
+      *out = &e;
+      return HYDRO_OK;
+    }
+  const int64_t before = h->launches;
+  CUDA_TRY(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaStream_t cs = h->cap_stream;
+  unsigned long long* ms = reinterpret_cast<unsigned long long*>(k.dms);
+  // the stage kernel gathers halos from the neighbours' interiors itself, so
+  // no ghost fill is needed between stages; in mixed precision each stage
+  // reads the shadow of its input and writes the shadow of its output
+  const bool mixed = h->precision == HYDRO_MIXED;
+  float* Sa = h->d_shadow[0];
+  float* Sb = h->d_shadow[1];
+  int rc = mixed ? enqueue_shadow(h, k.U, Sa, cs) : HYDRO_OK;
+  if (k.n_steps == 0) {
+    if (!rc) rc = enqueue_rk3_stages(h, k.ids, k.n_items, k.U, k.s1, k.s2, ms, Sa, Sb, nullptr, cs);
+  } else {
+    for (int step = 0; step < k.n_steps && !rc; ++step) {
+      cfl_dt<<<1, 1, 0, cs>>>(h->d_dt, k.dms, k.cfl, k.dt_out ? k.dt_out + step : nullptr);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) {
+        rc = cuda_fail(h, e, "cfl_dt launch");
+        break;
+      }
+      h->launches += 1;
+      const bool last = step + 1 == k.n_steps;
+      // step's input shadow in Sa; stage 3 leaves the new state's shadow in Sb
+      rc = enqueue_rk3_stages(h, k.ids, k.n_items, k.U, k.s1, k.s2, ms, mixed ? Sa : nullptr,
+                              mixed ? Sb : nullptr, (mixed && !last) ? Sb : nullptr, cs);
+      std::swap(Sa, Sb);
+      if (!rc && k.totals) {
+        e = launch_totals(k.U, h->n, h->d_dx, h->d_partial, k.totals + (size_t)step * NF, cs);
+        if (e != cudaSuccess)
+          rc = cuda_fail(h, e, "totals kernel launch");
+        else
+          h->launches += 3;
+      }
+    }
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &graph);
+  const int kernels = (int)(h->launches - before);
+  h->launches = before;
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+  GraphEntry ne;
+  ne.key = k;
+  ne.kernels = kernels;
+  e = cudaGraphInstantiate(&ne.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+  if (h->graphs.size() >= 16) {
+    cudaGraphExecDestroy(h->graphs.front().exec);
+    h->graphs.erase(h->graphs.begin());
+  }
+  h->graphs.push_back(ne);
+  *out = &h->graphs.back();
+  return HYDRO_OK;
+}
+
+int rk3_common(hydro_handle* h, const hydro_batch* batch, double* U, double* scratch1, double* scratch2,
+               double dt, double cfl, double* d_max_speed, double* d_dt_out, void* stream) {
+  if (!h) return HYDRO_ERR_INVALID;
+  int rc = check_rk3(h, batch, U, scratch1, scratch2, d_max_speed, d_dt_out);
+  if (rc) return rc;
   if (cfl > 0.0) {
     if (!(cfl <= 1.0)) return fail(h, HYDRO_ERR_INVALID, "cfl must be in (0, 1]");
   } else if (!(dt >= 0.0) || !std::isfinite(dt)) {
@@ -375,58 +480,10 @@ int rk3_common(hydro_handle* h, const hydro_batch* batch, double* U, double* scr
   }
   cudaStream_t st = (cudaStream_t)stream;
   h->last_stream = st;
+  GraphKey k{batch->subgrid_ids, batch->n_items, U, scratch1, scratch2, d_max_speed, 0, 0.0, nullptr, nullptr};
   GraphEntry* g = nullptr;
-  for (auto& e : h->graphs)
-    if (e.ids == batch->subgrid_ids && e.n_items == batch->n_items && e.U == U && e.s1 == scratch1 &&
-        e.s2 == scratch2 && e.dms == d_max_speed)
-      g = &e;
-  if (!g) {
-    // capture the three stages and the ghost fills on the handle's private stream
-    const int64_t before = h->launches;
-    CUDA_TRY(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-    cudaStream_t cs = h->cap_stream;
-    unsigned long long* ms = reinterpret_cast<unsigned long long*>(d_max_speed);
-    const int32_t* ids = batch->subgrid_ids;
-    const int ni = batch->n_items;
-    // the stage kernel gathers halos from the neighbours' interiors itself, so
-    // no ghost fill is needed between stages; in mixed precision each stage
-    // reads the shadow of its input and writes the shadow of its output
-    float* Sa = h->d_shadow[0];
-    float* Sb = h->d_shadow[1];
-    const bool mixed = h->precision == HYDRO_MIXED;
-    rc = mixed ? enqueue_shadow(h, U, Sa, cs) : HYDRO_OK;
-    if (!rc) rc = enqueue_stage(h, ids, ni, U, Sa, nullptr, 1.0, 0.0, h->d_dt, scratch1, Sb, ms, 0, cs);
-    if (!rc)
-      rc = enqueue_stage(h, ids, ni, scratch1, Sb, U, 0.25, 0.0, h->d_dt, scratch2, Sa, h->d_ms_tmp, 1, cs);
-    if (!rc)
-      rc = enqueue_stage(h, ids, ni, scratch2, Sa, U, 2.0 / 3.0, 0.0, h->d_dt, U, nullptr, h->d_ms_tmp, 2, cs);
-    cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamEndCapture(cs, &graph);
-    const int kernels = (int)(h->launches - before);
-    h->launches = before;
-    if (rc) {
-      if (graph) cudaGraphDestroy(graph);
-      return rc;
-    }
-    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
-    GraphEntry ne;
-    ne.ids = batch->subgrid_ids;
-    ne.n_items = batch->n_items;
-    ne.U = U;
-    ne.s1 = scratch1;
-    ne.s2 = scratch2;
-    ne.dms = d_max_speed;
-    ne.kernels = kernels;
-    e = cudaGraphInstantiate(&ne.exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
-    if (h->graphs.size() >= 16) {
-      cudaGraphExecDestroy(h->graphs.front().exec);
-      h->graphs.erase(h->graphs.begin());
-    }
-    h->graphs.push_back(ne);
-    g = &h->graphs.back();
-  }
+  rc = get_graph(h, k, &g);
+  if (rc) return rc;
   if (cfl > 0.0)
     cfl_dt<<<1, 1, 0, st>>>(h->d_dt, d_max_speed, cfl, d_dt_out);
   else
@@ -450,6 +507,48 @@ int hydro_rk3_step_cfl(hydro_handle* h, const hydro_batch* batch, double* U, dou
                        double cfl, double* d_max_speed, double* d_dt_out, void* stream) {
   if (!(cfl > 0.0)) return h ? fail(h, HYDRO_ERR_INVALID, "cfl must be in (0, 1]") : HYDRO_ERR_INVALID;
   return rk3_common(h, batch, U, scratch1, scratch2, 0.0, cfl, d_max_speed, d_dt_out, stream);
+}
+
+}  // extern "C"
+
+namespace {
+
+int run_graph(hydro_handle* h, const hydro_batch* batch, double* U, double* scratch1, double* scratch2, double cfl,
+              int32_t n_steps, double* d_max_speed, double* d_dt_out, double* d_totals, GraphEntry** g) {
+  int rc = check_rk3(h, batch, U, scratch1, scratch2, d_max_speed, d_dt_out);
+  if (rc) return rc;
+  if (!(cfl > 0.0 && cfl <= 1.0)) return fail(h, HYDRO_ERR_INVALID, "cfl must be in (0, 1]");
+  if (n_steps < 1 || n_steps > HYDRO_RK3_RUN_MAX_STEPS)
+    return fail(h, HYDRO_ERR_INVALID, "n_steps must be in [1, %d]", HYDRO_RK3_RUN_MAX_STEPS);
+  if (d_totals && !aligned(d_totals, 8)) return fail(h, HYDRO_ERR_INVALID, "misaligned pointer");
+  GraphKey k{batch->subgrid_ids, batch->n_items, U, scratch1, scratch2, d_max_speed, n_steps, cfl, d_dt_out,
+             d_totals};
+  return get_graph(h, k, g);
+}
+
+}  // namespace
+
+extern "C" {
+
+int hydro_rk3_run_cfl(hydro_handle* h, const hydro_batch* batch, double* U, double* scratch1, double* scratch2,
+                      double cfl, int32_t n_steps, double* d_max_speed, double* d_dt_out, double* d_totals,
+                      void* stream) {
+  if (!h) return HYDRO_ERR_INVALID;
+  GraphEntry* g = nullptr;
+  int rc = run_graph(h, batch, U, scratch1, scratch2, cfl, n_steps, d_max_speed, d_dt_out, d_totals, &g);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  CUDA_TRY(h, cudaGraphLaunch(g->exec, st));
+  h->launches += g->kernels;
+  return HYDRO_OK;
+}
+
+int hydro_rk3_run_prepare(hydro_handle* h, const hydro_batch* batch, double* U, double* scratch1, double* scratch2,
+                          double cfl, int32_t n_steps, double* d_max_speed, double* d_dt_out, double* d_totals) {
+  if (!h) return HYDRO_ERR_INVALID;
+  GraphEntry* g = nullptr;
+  return run_graph(h, batch, U, scratch1, scratch2, cfl, n_steps, d_max_speed, d_dt_out, d_totals, &g);
 }
 
 int hydro_totals(hydro_handle* h, const double* U, double* d_totals, void* stream) {

@@ -27,10 +27,12 @@ STATUS = {0: "HYDRO_OK", -1: "HYDRO_ERR_INVALID", -2: "HYDRO_ERR_CUDA", -3: "HYD
 
 # every symbol include/hydro.h declares
 EXPORTS = ("hydro_create", "hydro_step", "hydro_shadow", "hydro_step_shadowed", "hydro_fill_ghosts", "hydro_rk3_step",
-           "hydro_rk3_step_cfl", "hydro_totals", "hydro_totals_noalloc", "hydro_sync", "hydro_last_error",
-           "hydro_launch_count", "hydro_set_param", "hydro_destroy")
+           "hydro_rk3_step_cfl", "hydro_rk3_run_cfl", "hydro_rk3_run_prepare", "hydro_totals",
+           "hydro_totals_noalloc", "hydro_sync", "hydro_last_error", "hydro_launch_count", "hydro_set_param",
+           "hydro_destroy")
 SHADOW_FIELD = NX * NX * NX + (NX // 2) ** 3   # interior, then its 4^3 restriction
 TOTALS_NOALLOC_MAX_SUBGRIDS = 65536
+RK3_RUN_MAX_STEPS = 1024
 
 
 class HydroError(RuntimeError):
@@ -70,6 +72,8 @@ def load_library(path: str = LIB_PATH):
     L.hydro_fill_ghosts.argtypes = [vp, vp, vp]
     L.hydro_rk3_step.argtypes = [vp, ctypes.POINTER(Batch), vp, vp, vp, dbl, vp, vp]
     L.hydro_rk3_step_cfl.argtypes = [vp, ctypes.POINTER(Batch), vp, vp, vp, dbl, vp, vp, vp]
+    L.hydro_rk3_run_cfl.argtypes = [vp, ctypes.POINTER(Batch), vp, vp, vp, dbl, i32, vp, vp, vp, vp]
+    L.hydro_rk3_run_prepare.argtypes = [vp, ctypes.POINTER(Batch), vp, vp, vp, dbl, i32, vp, vp, vp]
     L.hydro_totals.argtypes = [vp, vp, vp, vp]
     L.hydro_totals_noalloc.argtypes = [vp, vp, i32, vp, vp]
     L.hydro_sync.argtypes = [vp]
@@ -236,6 +240,31 @@ class HydroGrid:
         self._check(self.lib.hydro_rk3_step_cfl(self.h, ctypes.byref(b), _ptr(U), _ptr(scratch1), _ptr(scratch2),
                                                 float(cfl), _ptr(max_speed), _ptr(dt_out), _stream_ptr(stream)))
         return max_speed
+
+    def rk3_run_cfl(self, U, cfl, scratch1, scratch2, max_speed, n_steps, ids=None, batch_offsets=None,
+                    dt_out=None, totals=None, stream=None):
+        """n_steps SSP-RK3 steps with device-chosen dt in one graph launch
+        (hydro_rk3_run_cfl); dt_out [n_steps] and totals [n_steps, 11] are
+        optional device outputs.  Returns max_speed."""
+        for t in (U, scratch1, scratch2):
+            self._state(t)
+        b, keep = self._batch(ids, batch_offsets)
+        self._keep = keep
+        self._check(self.lib.hydro_rk3_run_cfl(self.h, ctypes.byref(b), _ptr(U), _ptr(scratch1), _ptr(scratch2),
+                                               float(cfl), int(n_steps), _ptr(max_speed), _ptr(dt_out),
+                                               _ptr(totals), _stream_ptr(stream)))
+        return max_speed
+
+    def rk3_run_prepare(self, U, cfl, scratch1, scratch2, max_speed, n_steps, ids=None, batch_offsets=None,
+                        dt_out=None, totals=None):
+        """Capture the graph of the matching rk3_run_cfl call without running it."""
+        for t in (U, scratch1, scratch2):
+            self._state(t)
+        b, keep = self._batch(ids, batch_offsets)
+        self._keep = keep
+        self._check(self.lib.hydro_rk3_run_prepare(self.h, ctypes.byref(b), _ptr(U), _ptr(scratch1),
+                                                   _ptr(scratch2), float(cfl), int(n_steps), _ptr(max_speed),
+                                                   _ptr(dt_out), _ptr(totals)))
 
     def totals(self, U, out=None, stream=None):
         import torch

@@ -479,3 +479,39 @@ def test_flux_form_and_dual_energy(hydro, oracle_mod, prec, form, de_switch, mac
     if prec == "fp64":
         assert np.all(field_errors(got, ref, plain=True) <= TOL[prec])
     np.testing.assert_allclose(msd.cpu().numpy(), ms_o, rtol=1e-14 if prec == "fp64" else 1e-6)
+
+
+# ---------------------------------------------------------------------------
+# several RK3 steps in one graph
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_rk3_run_matches_separate_steps(hydro, oracle_mod, prec):
+    """hydro_rk3_run_cfl over 3 steps is bit-identical to 3 hydro_rk3_step_cfl
+    calls each followed by hydro_totals (same dt sequence, same totals)."""
+    w = W.config(3)
+    U = _filled(oracle_mod, w)
+    ids = torch.as_tensor(w.batches.ids, device="cuda")
+    g = hydro.HydroGrid(w.grid, precision=prec)
+    res = []
+    for mode in ("separate", "run"):
+        Ud = _dev(U)
+        s1, s2 = torch.empty_like(Ud), torch.empty_like(Ud)
+        ms = torch.zeros(2, dtype=torch.float64, device="cuda")
+        g.step(Ud, 0.0, U_out=s1, ids=ids, max_speed=ms)      # first CFL speed
+        dts = torch.zeros(3, dtype=torch.float64, device="cuda")
+        tots = torch.zeros((3, 11), dtype=torch.float64, device="cuda")
+        if mode == "separate":
+            for k in range(3):
+                g.rk3_step_cfl(Ud, 0.4, s1, s2, ms, ids=ids, batch_offsets=w.batches.offsets, dt_out=dts[k:k + 1])
+                g.totals(Ud, out=tots[k])
+        else:
+            g.rk3_run_cfl(Ud, 0.4, s1, s2, ms, 3, ids=ids, batch_offsets=w.batches.offsets, dt_out=dts,
+                          totals=tots)
+        g.sync()
+        res.append((_host(Ud)[IN], dts.cpu().numpy(), tots.cpu().numpy(), ms.cpu().numpy()))
+    for a, b in zip(*res):
+        assert np.array_equal(a, b)
+    assert np.all(res[0][1] > 0)
+    with pytest.raises(hydro.HydroError):
+        g.rk3_run_cfl(_dev(U), 0.4, s1, s2, ms, 0, ids=ids)
