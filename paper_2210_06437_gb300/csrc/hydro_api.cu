@@ -164,6 +164,8 @@ int enqueue_stage(hydro_handle* h, const int32_t* ids, int n_items, const double
   if (n_items == 0) return HYDRO_OK;
   CUDA_TRY(h, cudaMemsetAsync(h->d_queue + queue_slot, 0, sizeof(unsigned int), st));
   StageArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.has_tm = encode_state_map(&a.tm_in, Uin, h->n) && (!U0 || encode_state_map(&a.tm_u0, U0, h->n));
   a.Uin = Uin;
   a.U0 = U0;
   a.Uout = Uout;

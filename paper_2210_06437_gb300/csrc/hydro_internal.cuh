@@ -4,6 +4,7 @@
 // per field, interior 3..10, 11 fields (rho, sx, sy, sz, egas, tau, rhoX1..5).
 #pragma once
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace hydro {
@@ -27,6 +28,12 @@ constexpr int ERRBIT_BAD_ID = 2;
 __host__ __device__ inline size_t field_offset(int s, int f) { return ((size_t)s * NF + f) * NP3; }
 
 struct StageArgs {
+  // TMA descriptors of Uin and U0 viewed as [n*11][14][14][14] doubles with a
+  // box of 10 x 8 x 8 x 11 (i = 2..11, j, k = 3..10, all fields of one
+  // sub-grid); the kernel prefetches each sub-grid's box into L2 ahead of its
+  // update.  Zero-filled when not used.
+  CUtensorMap tm_in;  // 128-byte aligned by its type
+  CUtensorMap tm_u0;
   const double* Uin;
   const double* U0;     // nullptr when beta == 1
   double* Uout;
@@ -49,7 +56,12 @@ struct StageArgs {
   unsigned int* queue;   // work-queue counter, zero at launch
   int* err;
   unsigned long long* max_speed;  // [2] ordered bits of non-negative doubles
+  int32_t has_tm;        // tm_in (and tm_u0 when U0 is set) are valid
 };
+
+// Encode the TMA descriptor of a padded state (n sub-grids) used by
+// StageArgs::tm_in / tm_u0; returns false if the driver refuses it.
+bool encode_state_map(CUtensorMap* tm, const double* U, int n);
 
 struct GhostArgs {
   double* U;

@@ -380,10 +380,6 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src) {  // 4-
   const unsigned a = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(a), "l"(src));
 }
-// Pull [src, src + bytes) into L2 (16-byte aligned address and size).
-__device__ __forceinline__ void prefetch_l2(const void* src, unsigned bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src), "r"(bytes));
-}
 
 struct Nbr {
   int32_t id[6][4];
@@ -582,18 +578,18 @@ __device__ __forceinline__ void stage_interior_async(const float* __restrict__ S
   }
 }
 
-// Pull the interior rows of sub-grid s that the update will read (U_in, and U0
-// when blending) into L2 ahead of time: per field and k-plane one bulk prefetch
-// of the 864 bytes from the 16-byte boundary before cell (3, 3, k+3) through
-// cell (10, 10, k+3).
+// Pull the 10 x 8 x 8 x 11 box around the interior rows of sub-grid s that
+// the update will read (U_in, and U0 when blending) into L2 ahead of time: one
+// TMA tensor prefetch per array (the box starts at i = 2, a 16-byte boundary).
 __device__ __forceinline__ void prefetch_update_rows(const StageArgs& a, int s) {
-  const int t = threadIdx.x;
-  const bool blend = a.beta != 1.0;
-  if (t >= (blend ? 2 : 1) * NF * NX) return;
-  const double* base = (t < NF * NX) ? a.Uin : a.U0;
-  const int q = t < NF * NX ? t : t - NF * NX;
-  const int f = q >> 3, k = q & 7;
-  prefetch_l2(base + field_offset(s, f) + (size_t)(k + NG) * NP2 + NG * NP + NG - 1, 864);
+  if (threadIdx.x != 0 || !a.has_tm) return;
+  asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"(&a.tm_in), "r"(NG - 1),
+               "r"(NG), "r"(NG), "r"(s * NF)
+               : "memory");
+  if (a.beta != 1.0)
+    asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"(&a.tm_u0),
+                 "r"(NG - 1), "r"(NG), "r"(NG), "r"(s * NF)
+                 : "memory");
 }
 
 // Work item and what its processing needs: sub-grid id (-1: queue exhausted,
@@ -822,7 +818,7 @@ __device__ __forceinline__ unsigned update_cells(const StageArgs& a, int s, cons
 }
 
 template <typename T>
-__global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(const StageArgs a) {
+__global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(const __grid_constant__ StageArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Shared<T> sh;
   sh.tile = reinterpret_cast<T*>(smem_raw);
@@ -959,6 +955,38 @@ int blocks_per_sm() {
 }
 
 }  // namespace
+
+namespace {
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder() {
+  static EncodeTiled fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<EncodeTiled>(p);
+  }();
+  return fn;
+}
+
+}  // namespace
+
+bool encode_state_map(CUtensorMap* tm, const double* U, int n) {
+  EncodeTiled fn = encoder();
+  if (!fn || !U || n < 1) return false;
+  const cuuint64_t dims[4] = {NP, NP, NP, (cuuint64_t)n * NF};
+  const cuuint64_t strides[3] = {NP * sizeof(double), NP2 * sizeof(double), NP3 * sizeof(double)};
+  const cuuint32_t box[4] = {NX + 2, NX, NX, NF};  // i = 2..11 keeps the box start on a 16-byte boundary
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return fn(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, const_cast<double*>(U), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 cudaError_t launch_stage_fp64(const StageArgs& a, int grid, cudaStream_t st) { return launch<double>(a, grid, st); }
 cudaError_t launch_stage_mixed(const StageArgs& a, int grid, cudaStream_t st) { return launch<float>(a, grid, st); }
