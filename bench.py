@@ -324,26 +324,27 @@ def main():
     if not args.skip_fp64:
         results["fp64"] = run_precision("fp64", None)
 
-    # end-to-end through the public API with host buffers (mixed path)
+    # end-to-end through the public API with host buffers (mixed path): the
+    # state lives on the host as packed interiors (pinned) and every step
+    # uploads it, advances it one RK3 step with its totals, and downloads it
     e2e = None
     if not args.skip_e2e:
         g = HY.HydroGrid(w.grid, precision="mixed")
-        Uh = torch.empty(U.shape, dtype=torch.float64, pin_memory=True)
-        Uh.copy_(torch.from_numpy(U_host))
-        g.fill_ghosts(U)
+        n = w.grid.n
+        Ph = g.empty_interiors(pin_memory=True)
+        Ph.copy_(torch.from_numpy(np.ascontiguousarray(U_host[:, :, 3:11, 3:11, 3:11]).reshape(n, 11, 512)))
+        Pd = g.empty_interiors()
         ms = torch.zeros(2, dtype=torch.float64, device=dev)
         tot = torch.empty(11, dtype=torch.float64, device=dev)
         toth = torch.empty(11, dtype=torch.float64, pin_memory=True)
-        U.copy_(Uh)
-        g.fill_ghosts(U)
-        Uh.copy_(U)
-        g.step(U, 0.0, U_out=s1, ids=ids, batch_offsets=offs, max_speed=ms)
+        g.upload(Ph, U, Pd)
+        g.step(U, 0.0, U_out=s1, ids=ids, batch_offsets=offs, max_speed=ms)   # first CFL speed
 
         def e2e_step():
-            U.copy_(Uh, non_blocking=True)
+            g.upload(Ph, U, Pd)
             g.rk3_step_cfl(U, 0.4, s1, s2, ms, ids=ids, batch_offsets=offs)
             g.totals(U, out=tot)
-            Uh.copy_(U, non_blocking=True)
+            g.download(U, Pd, Ph)
             toth.copy_(tot, non_blocking=True)
 
         for _ in range(max(1, min(args.warmup, 2))):
@@ -357,12 +358,13 @@ def main():
         barrier()
         g.sync()
         t_e2e = ranks_max(e0.elapsed_time(e1) / 1e3 / args.steps)
-        nbytes = U.numel() * 8
+        nbytes = Pd.numel() * 8
         e2e = {"value": aggregate_rate(cells, 3, world, t_e2e), "unit": "cell-updates/s", "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes + 88, "ms_per_step": t_e2e * 1e3,
-               "api": "HydroGrid.rk3_step_cfl + totals on a pinned host state copied in and out every step"}
+               "api": "HydroGrid.upload (pinned host packed interiors -> device) + rk3_step_cfl + totals + download "
+                      "(device -> pinned host packed interiors) every step"}
         g.close()
-        del Uh
+        del Ph, Pd
 
     # CPU oracle baseline on a bounded sample (rank 0, N = 1 only)
     cpu = None

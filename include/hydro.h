@@ -158,6 +158,16 @@ int hydro_step_shadowed(hydro_handle *h, const hydro_batch *batch, const double 
                         const double *U0, double beta, double dt, double *U_out, float *S_out, double *d_max_speed,
                         void *stream);
 
+/* Packed interiors, for moving states between host and device without their
+ * ghost cells (5.36x fewer bytes than the padded layout; the paper has no
+ * counterpart):
+ *   P[s][f][(k*8 + j)*8 + i] = U[s][f][k+3][j+3][i+3],  P DEVICE double[n][11][512].
+ * hydro_pack_interiors writes P from U; hydro_unpack_interiors writes the
+ * interiors of U from P and leaves its ghost cells untouched.  Both pointers
+ * 16-byte aligned. */
+int hydro_pack_interiors(hydro_handle *h, const double *U, double *P, void *stream);
+int hydro_unpack_interiors(hydro_handle *h, const double *P, double *U, void *stream);
+
 /* Fill the six face ghost slabs (3 layers each) of every sub-grid of U from
  * the neighbours' interiors (Section VI: hydro boundary exchange): copy from a
  * same-level neighbour; coarse neighbour: value of the coarse cell containing

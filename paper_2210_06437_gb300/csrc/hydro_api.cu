@@ -345,6 +345,28 @@ int hydro_shadow(hydro_handle* h, const double* U, float* S, void* stream) {
   return enqueue_shadow(h, U, S, st);
 }
 
+int hydro_pack_interiors(hydro_handle* h, const double* U, double* P, void* stream) {
+  if (!h) return HYDRO_ERR_INVALID;
+  if (!U || !P || !aligned(U, 16) || !aligned(P, 16)) return fail(h, HYDRO_ERR_INVALID, "NULL or misaligned pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  cudaError_t e = launch_pack(U, P, h->n, st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "pack kernel launch");
+  h->launches += 1;
+  return HYDRO_OK;
+}
+
+int hydro_unpack_interiors(hydro_handle* h, const double* P, double* U, void* stream) {
+  if (!h) return HYDRO_ERR_INVALID;
+  if (!U || !P || !aligned(U, 16) || !aligned(P, 16)) return fail(h, HYDRO_ERR_INVALID, "NULL or misaligned pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  cudaError_t e = launch_unpack(P, U, h->n, st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "unpack kernel launch");
+  h->launches += 1;
+  return HYDRO_OK;
+}
+
 int hydro_step_shadowed(hydro_handle* h, const hydro_batch* batch, const double* U_in, const float* S_in,
                         const double* U0, double beta, double dt, double* U_out, float* S_out, double* d_max_speed,
                         void* stream) {

@@ -163,3 +163,54 @@ cudaError_t launch_shadow(const double* U, float* S, int n, cudaStream_t st) {
 }
 
 }  // namespace hydro
+
+// ---------------------------------------------------------------------------
+// Packed interiors: P[s][f][(k*8 + j)*8 + i] = U[s][f][k+3][j+3][i+3], the
+// state without its ghost cells (5.36x fewer bytes than the padded layout), for
+// moving states between host and device.
+// ---------------------------------------------------------------------------
+
+namespace hydro {
+namespace {
+
+__global__ void __launch_bounds__(256) pack_kernel(const double* __restrict__ U, double* __restrict__ P, int n) {
+  const size_t total = (size_t)n * NF * CELLS;
+  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(g & (CELLS - 1));
+    const size_t sf = g >> 9;
+    P[g] = U[sf * NP3 + (size_t)((c >> 6) + NG) * NP2 + (((c >> 3) & 7) + NG) * NP + ((c & 7) + NG)];
+  }
+}
+
+__global__ void __launch_bounds__(256) unpack_kernel(const double* __restrict__ P, double* __restrict__ U, int n) {
+  const size_t total = (size_t)n * NF * CELLS;
+  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(g & (CELLS - 1));
+    const size_t sf = g >> 9;
+    U[sf * NP3 + (size_t)((c >> 6) + NG) * NP2 + (((c >> 3) & 7) + NG) * NP + ((c & 7) + NG)] = P[g];
+  }
+}
+
+size_t layout_blocks(int n) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t total = (size_t)n * NF * CELLS;
+  size_t blocks = (total + 255) / 256;
+  const size_t cap = (size_t)sms * 8 * 4;
+  return blocks > cap ? cap : (blocks ? blocks : 1);
+}
+
+}  // namespace
+
+cudaError_t launch_pack(const double* U, double* P, int n, cudaStream_t st) {
+  pack_kernel<<<(unsigned)layout_blocks(n), 256, 0, st>>>(U, P, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const double* P, double* U, int n, cudaStream_t st) {
+  unpack_kernel<<<(unsigned)layout_blocks(n), 256, 0, st>>>(P, U, n);
+  return cudaGetLastError();
+}
+
+}  // namespace hydro

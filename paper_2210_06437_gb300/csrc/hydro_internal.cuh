@@ -79,6 +79,8 @@ constexpr int SHADOW_FIELD = CELLS + CELLS / 8;  // 576 floats per field
 
 // launchers (defined in the .cu files)
 cudaError_t launch_shadow(const double* U, float* S, int n, cudaStream_t st);
+cudaError_t launch_pack(const double* U, double* P, int n, cudaStream_t st);
+cudaError_t launch_unpack(const double* P, double* U, int n, cudaStream_t st);
 cudaError_t launch_stage_fp64(const StageArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_stage_mixed(const StageArgs& a, int grid, cudaStream_t st);
 int stage_blocks_per_sm_fp64();

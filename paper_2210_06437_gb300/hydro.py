@@ -28,8 +28,8 @@ STATUS = {0: "HYDRO_OK", -1: "HYDRO_ERR_INVALID", -2: "HYDRO_ERR_CUDA", -3: "HYD
 # every symbol include/hydro.h declares
 EXPORTS = ("hydro_create", "hydro_step", "hydro_shadow", "hydro_step_shadowed", "hydro_fill_ghosts", "hydro_rk3_step",
            "hydro_rk3_step_cfl", "hydro_rk3_run_cfl", "hydro_rk3_run_prepare", "hydro_totals",
-           "hydro_totals_noalloc", "hydro_sync", "hydro_last_error", "hydro_launch_count", "hydro_set_param",
-           "hydro_destroy")
+           "hydro_totals_noalloc", "hydro_pack_interiors", "hydro_unpack_interiors", "hydro_sync",
+           "hydro_last_error", "hydro_launch_count", "hydro_set_param", "hydro_destroy")
 SHADOW_FIELD = NX * NX * NX + (NX // 2) ** 3   # interior, then its 4^3 restriction
 TOTALS_NOALLOC_MAX_SUBGRIDS = 65536
 RK3_RUN_MAX_STEPS = 1024
@@ -70,6 +70,8 @@ def load_library(path: str = LIB_PATH):
     L.hydro_shadow.argtypes = [vp, vp, vp, vp]
     L.hydro_step_shadowed.argtypes = [vp, ctypes.POINTER(Batch), vp, vp, vp, dbl, dbl, vp, vp, vp, vp]
     L.hydro_fill_ghosts.argtypes = [vp, vp, vp]
+    L.hydro_pack_interiors.argtypes = [vp, vp, vp, vp]
+    L.hydro_unpack_interiors.argtypes = [vp, vp, vp, vp]
     L.hydro_rk3_step.argtypes = [vp, ctypes.POINTER(Batch), vp, vp, vp, dbl, vp, vp]
     L.hydro_rk3_step_cfl.argtypes = [vp, ctypes.POINTER(Batch), vp, vp, vp, dbl, vp, vp, vp]
     L.hydro_rk3_run_cfl.argtypes = [vp, ctypes.POINTER(Batch), vp, vp, vp, dbl, i32, vp, vp, vp, vp]
@@ -211,6 +213,44 @@ class HydroGrid:
                                                  float(beta), float(dt), _ptr(U_out), _ptr(S_out), _ptr(ms),
                                                  _stream_ptr(stream)))
         return U_out, ms
+
+    def empty_interiors(self, pin_memory=False, device=None):
+        """A packed-interior array [n, 11, 512] float64 (device, or pinned host)."""
+        import torch
+        if device == "cpu" or pin_memory:
+            return torch.empty((self.n, NF, NX ** 3), dtype=torch.float64, pin_memory=pin_memory)
+        return torch.empty((self.n, NF, NX ** 3), dtype=torch.float64, device=self.device)
+
+    def _packed(self, P):
+        import torch
+        assert isinstance(P, torch.Tensor) and P.dtype == torch.float64 and P.is_cuda and P.is_contiguous()
+        assert P.numel() == self.n * NF * NX ** 3
+        return P
+
+    def pack(self, U, P=None, stream=None):
+        """Interiors of U into the packed array P (hydro_pack_interiors)."""
+        self._state(U)
+        P = self.empty_interiors() if P is None else self._packed(P)
+        self._check(self.lib.hydro_pack_interiors(self.h, _ptr(U), _ptr(P), _stream_ptr(stream)))
+        return P
+
+    def unpack(self, P, U, stream=None):
+        """Interiors of U from the packed array P (hydro_unpack_interiors)."""
+        self._state(U)
+        self._packed(P)
+        self._check(self.lib.hydro_unpack_interiors(self.h, _ptr(P), _ptr(U), _stream_ptr(stream)))
+        return U
+
+    def upload(self, P_host, U, P_dev, stream=None):
+        """Host packed interiors (pinned) -> device state U: copy into P_dev, unpack."""
+        P_dev.copy_(P_host, non_blocking=True)
+        return self.unpack(P_dev, U, stream)
+
+    def download(self, U, P_dev, P_host, stream=None):
+        """Device state U -> host packed interiors (pinned): pack into P_dev, copy."""
+        self.pack(U, P_dev, stream)
+        P_host.copy_(P_dev, non_blocking=True)
+        return P_host
 
     def fill_ghosts(self, U, stream=None):
         self._state(U)

@@ -515,3 +515,29 @@ def test_rk3_run_matches_separate_steps(hydro, oracle_mod, prec):
     assert np.all(res[0][1] > 0)
     with pytest.raises(hydro.HydroError):
         g.rk3_run_cfl(_dev(U), 0.4, s1, s2, ms, 0, ids=ids)
+
+
+# ---------------------------------------------------------------------------
+# packed interiors
+# ---------------------------------------------------------------------------
+
+def test_pack_unpack_interiors(hydro):
+    w = W.config(3)
+    U = w.state()
+    g = hydro.HydroGrid(w.grid, precision="mixed")
+    Ud = _dev(U)
+    P = g.pack(Ud)
+    g.sync()
+    n = w.grid.n
+    assert np.array_equal(_host(P), U[IN].reshape(n, 11, 512))
+    V = torch.full_like(Ud, -5.0)
+    g.unpack(P * 2.0, V)
+    g.sync()
+    v = _host(V)
+    assert np.array_equal(v[IN], 2.0 * U[IN])
+    v[IN] = -5.0
+    assert np.all(v == -5.0)          # ghost cells untouched
+    Ph = g.empty_interiors(pin_memory=True)
+    g.download(Ud, P, Ph)
+    torch.cuda.synchronize()
+    assert np.array_equal(Ph.numpy(), U[IN].reshape(n, 11, 512))
