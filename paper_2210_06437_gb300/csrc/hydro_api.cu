@@ -157,15 +157,25 @@ int stage_grid(hydro_handle* h, int n_items) {
 }
 
 // Enqueue one stage (no validation).  queue_slot selects the counter.
+// mode 0: Shu-Osher stage; 1..3: mixed RK3 in increment form (Din / Dout the
+// increment pairs, see StageArgs)
 int enqueue_stage(hydro_handle* h, const int32_t* ids, int n_items, const double* Uin, const float* Sin,
                   const double* U0, double beta, double dt, const double* dt_dev, double* Uout, float* Sout,
-                  unsigned long long* ms, int queue_slot, cudaStream_t st) {
+                  unsigned long long* ms, int queue_slot, cudaStream_t st, int mode = 0, const double* Din = nullptr,
+                  double* Dout = nullptr) {
   CUDA_TRY(h, cudaMemsetAsync(ms, 0, 2 * sizeof(unsigned long long), st));
   if (n_items == 0) return HYDRO_OK;
   CUDA_TRY(h, cudaMemsetAsync(h->d_queue + queue_slot, 0, sizeof(unsigned int), st));
   StageArgs a;
   std::memset(&a, 0, sizeof(a));
-  a.has_tm = encode_state_map(&a.tm_in, Uin, h->n) && (!U0 || encode_state_map(&a.tm_u0, U0, h->n));
+  const double* second = mode >= 2 ? Din : U0;  // the other FP64-layout array the update reads
+  if (encode_state_map(&a.tm_in, Uin, h->n)) {
+    a.has_tm = 1;
+    if (second && encode_state_map(&a.tm_u0, second, h->n)) a.has_tm |= 2;
+  }
+  a.mode = mode;
+  a.Din = Din;
+  a.Dout = Dout;
   a.Uin = Uin;
   a.U0 = U0;
   a.Uout = Uout;
@@ -412,10 +422,25 @@ int check_rk3(hydro_handle* h, const hydro_batch* batch, double* U, double* scra
 
 // Enqueue the three stages of one RK3 step on cs.  Mixed precision: Sin is the
 // shadow of U, Smid the other shadow buffer; Sout_last, if not NULL, receives
-// the shadow of the new U (it must be Smid: free again after stage 2).
+// the shadow of the new U (it must be Smid: free again after stage 2).  FP64:
+// the Shu-Osher stages U1 = U*(U), U2 = U + 1/4 (U*(U1) - U),
+// U3 = U + 2/3 (U*(U2) - U) through scratch1 and scratch2.  Mixed: the same
+// step in increment form (modes 1..3), scratch1 and scratch2 holding the
+// increment pairs, U changed once at the end.
 int enqueue_rk3_stages(hydro_handle* h, const int32_t* ids, int ni, double* U, double* s1, double* s2,
                        unsigned long long* ms, float* Sin, float* Smid, float* Sout_last, cudaStream_t cs) {
-  int rc = enqueue_stage(h, ids, ni, U, Sin, nullptr, 1.0, 0.0, h->d_dt, s1, Smid, ms, 0, cs);
+  int rc;
+  if (h->precision == HYDRO_MIXED) {
+    rc = enqueue_stage(h, ids, ni, U, Sin, nullptr, 1.0, 0.0, h->d_dt, nullptr, Smid, ms, 0, cs, 1, nullptr, s1);
+    if (!rc)
+      rc = enqueue_stage(h, ids, ni, U, Smid, nullptr, 1.0, 0.0, h->d_dt, nullptr, Sin, h->d_ms_tmp, 1, cs, 2, s1,
+                         s2);
+    if (!rc)
+      rc = enqueue_stage(h, ids, ni, U, Sin, nullptr, 1.0, 0.0, h->d_dt, U, Sout_last, h->d_ms_tmp, 2, cs, 3, s2,
+                         nullptr);
+    return rc;
+  }
+  rc = enqueue_stage(h, ids, ni, U, Sin, nullptr, 1.0, 0.0, h->d_dt, s1, Smid, ms, 0, cs);
   if (!rc) rc = enqueue_stage(h, ids, ni, s1, Smid, U, 0.25, 0.0, h->d_dt, s2, Sin, h->d_ms_tmp, 1, cs);
   if (!rc)
     rc = enqueue_stage(h, ids, ni, s2, Sin, U, 2.0 / 3.0, 0.0, h->d_dt, U, Sout_last, h->d_ms_tmp, 2, cs);

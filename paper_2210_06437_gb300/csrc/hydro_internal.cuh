@@ -56,7 +56,17 @@ struct StageArgs {
   unsigned int* queue;   // work-queue counter, zero at launch
   int* err;
   unsigned long long* max_speed;  // [2] ordered bits of non-negative doubles
-  int32_t has_tm;        // tm_in (and tm_u0 when U0 is set) are valid
+  int32_t has_tm;        // bit 0: tm_in valid; bit 1: tm_u0 valid and read by the update
+  // Mixed-precision RK3 in increment form (mode 1..3; 0 = the Shu-Osher stage
+  // U_out = U0 + beta (U* - U0) above).  Stage k's increment L_k = lam * dU_k
+  // is kept as a float pair (hi word, lo word of an 8-byte slot of the padded
+  // layout); Uin is always the state U at the start of the step:
+  //   mode 1: Dout = L0,                     Sout ~ shadow of U + L0;
+  //   mode 2: Dout = (Din + L1) / 4,         Sout ~ shadow of U + Dout;
+  //   mode 3: Uout = U + 2/3 (Din + L2) (FP64), Sout (optional) = its shadow.
+  int32_t mode;
+  const double* Din;
+  double* Dout;
 };
 
 // Encode the TMA descriptor of a padded state (n sub-grids) used by

@@ -579,14 +579,15 @@ __device__ __forceinline__ void stage_interior_async(const float* __restrict__ S
 }
 
 // Pull the 10 x 8 x 8 x 11 box around the interior rows of sub-grid s that
-// the update will read (U_in, and U0 when blending) into L2 ahead of time: one
-// TMA tensor prefetch per array (the box starts at i = 2, a 16-byte boundary).
+// the update will read (U_in, and U0 or the previous increment when that is
+// read too) into L2 ahead of time: one TMA tensor prefetch per array (the box
+// starts at i = 2, a 16-byte boundary).
 __device__ __forceinline__ void prefetch_update_rows(const StageArgs& a, int s) {
-  if (threadIdx.x != 0 || !a.has_tm) return;
+  if (threadIdx.x != 0 || !(a.has_tm & 1)) return;
   asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"(&a.tm_in), "r"(NG - 1),
                "r"(NG), "r"(NG), "r"(s * NF)
                : "memory");
-  if (a.beta != 1.0)
+  if (a.has_tm & 2)
     asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"(&a.tm_u0),
                  "r"(NG - 1), "r"(NG), "r"(NG), "r"(s * NF)
                  : "memory");
@@ -599,6 +600,7 @@ struct Meta {
   int item;
   int s;
   double lam, idx;
+  float lh, ll;  // lam split into two floats (lh + ll = lam to about 2^-48)
 };
 
 // The next work item as warp 7 (threads 224..255, one PPM task fewer than
@@ -640,6 +642,8 @@ __device__ __forceinline__ void pf_finish(const StageArgs& a, double dt, const P
       const double lam = dt * idx;
       m.lam = lam;
       m.idx = idx;
+      m.lh = (float)lam;
+      m.ll = (float)(lam - (double)m.lh);
     }
   }
   if (lane == 0) {
@@ -743,13 +747,132 @@ __device__ __forceinline__ void direction_pass(const Shared<T>& sh, const StageA
   }
 }
 
-// U_out = U* (or U0 + beta (U* - U0) when BLEND) for the two owned cells of
-// sub-grid s; SHADOW (mixed only) also writes the rounded cells and their
-// 2x2x2 restriction (FP32 pairwise sum, the partner cells by warp shuffles).  Returns non-zero if a value is not finite or a density <= 0.
+// ---------------------------------------------------------------------------
+// Mixed-precision SSP-RK3 in increment form.  With L_k = lam * dU(U_k) the
+// stages are U1 = U + L0, U2 = U + (L0 + L1)/4, U3 = U + 2/3 ((L0 + L1)/4 + L2),
+// algebraically the Shu-Osher stages.  The increments stay float pairs (about
+// 48 bits; error-free TwoSums and products); the FP64 state is read by every
+// stage but changed only once, by two FP64 additions in stage 3.  Stages 1
+// and 2 write the shadow of their state as RN32(RN32(U) + D_hi), within one
+// FP32 ulp of the rounded state.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// (h, l) = (ah + al) * (bh + bl) to about 2^-46, both cells packed
+__device__ __forceinline__ void pair_mul(float2 ah, float2 al, float2 bh, float2 bl, float2& h, float2& l) {
+  h = mul2(ah, bh);
+  const float2 e = fma2(ah, bh, neg2(h));
+  l = fma2(ah, bl, fma2(al, bh, e));
+}
+
+// (h, l) = (ah + al) + (bh + bl)
+__device__ __forceinline__ void pair_add(float2 ah, float2 al, float2 bh, float2 bl, float2& h, float2& l) {
+  float2 e;
+  two_sum2(ah, bh, h, e);
+  l = add2(e, add2(al, bl));
+}
+
+__device__ __forceinline__ double pack_pair(float h, float l) {
+  return __hiloint2double(__float_as_int(h), __float_as_int(l));
+}
+__device__ __forceinline__ float pair_hi(double d) { return __int_as_float(__double2hiint(d)); }
+__device__ __forceinline__ float pair_lo(double d) { return __int_as_float(__double2loint(d)); }
+
+// Shadow output of one field (the two owned cells x0, x1) and its restriction.
+__device__ __forceinline__ void write_shadow(float* So, int c0, float x0, float x1) {
+  const int tid = threadIdx.x;
+  So[c0] = x0;
+  So[c0 + 64] = x1;
+  // pairs in i (lane ^ 1), then in j (lane ^ 8), both cells of the k-pair at once
+  const float2 xi = make_float2(x0, x1);
+  const float2 p = add2(xi, make_float2(__shfl_xor_sync(0xffffffffu, x0, 1), __shfl_xor_sync(0xffffffffu, x1, 1)));
+  const float2 t = add2(p, make_float2(__shfl_xor_sync(0xffffffffu, p.x, 8), __shfl_xor_sync(0xffffffffu, p.y, 8)));
+  const int cc = (tid >> 6) * 16 + ((tid >> 4) & 3) * 4 + ((tid >> 1) & 3);
+  if ((tid & 9) == 0) So[SHADOW_COARSE + cc] = __fmul_rn(__fadd_rn(t.x, t.y), 0.125f);  // i and j even
+}
+
+// Fields [F0, F1) of update_inc below.
+template <int MODE, bool SHADOW, int F0, int F1>
+__device__ __forceinline__ unsigned update_inc_fields(const StageArgs& a, int s, const Acc<float> (&acc)[NF],
+                                                      float lh, float ll, size_t cell0, int c0, unsigned& nf) {
+  constexpr bool READ_D = MODE >= 2;
+  unsigned bad = 0;
+  double u0v[F1 - F0][2], dv[READ_D ? F1 - F0 : 1][2];
+#pragma unroll
+  for (int f = F0; f < F1; ++f)
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const size_t o = field_offset(s, f) + cell0 + (size_t)r * NP2;
+      u0v[f - F0][r] = a.Uin[o];
+      if constexpr (READ_D) dv[f - F0][r] = a.Din[o];
+    }
+  const float2 lh2 = make_float2(lh, lh), ll2 = make_float2(ll, ll);
+#pragma unroll
+  for (int f = F0; f < F1; ++f) {
+    float2 Lh, Ll;  // L = lam * (s + c) for both cells
+    pair_mul(acc[f].s, acc[f].c, lh2, ll2, Lh, Ll);
+    float2 Dh, Dl;  // the new increment
+    if constexpr (MODE == 1) {
+      Dh = Lh, Dl = Ll;
+    } else {
+      const float2 ph = make_float2(pair_hi(dv[f - F0][0]), pair_hi(dv[f - F0][1]));
+      const float2 pl = make_float2(pair_lo(dv[f - F0][0]), pair_lo(dv[f - F0][1]));
+      pair_add(ph, pl, Lh, Ll, Dh, Dl);
+      if constexpr (MODE == 2) {
+        Dh = mul2(Dh, make_float2(0.25f, 0.25f));
+        Dl = mul2(Dl, make_float2(0.25f, 0.25f));
+      } else {
+        constexpr float ch = (float)(2.0 / 3.0), cl = (float)(2.0 / 3.0 - (double)(float)(2.0 / 3.0));
+        pair_mul(Dh, Dl, make_float2(ch, ch), make_float2(cl, cl), Dh, Dl);
+      }
+    }
+    float x[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const size_t o = field_offset(s, f) + cell0 + (size_t)r * NP2;
+      const float dh = r ? Dh.y : Dh.x, dl = r ? Dl.y : Dl.x;
+      if constexpr (MODE == 3) {
+        const double v = __dadd_rn(__dadd_rn(u0v[f - F0][r], f32_to_f64(dh)), f32_to_f64(dl));
+        a.Uout[o] = v;
+        nf |= nonfinite_bit(v);
+        if (f == F_RHO) bad |= bad64(v, true);
+        x[r] = f64_to_f32(v);
+      } else {
+        a.Dout[o] = pack_pair(dh, dl);
+        x[r] = __fadd_rn(f64_to_f32(u0v[f - F0][r]), dh);
+        nf |= (__float_as_uint(x[r]) & 0x7f800000u) == 0x7f800000u ? 0x80000000u : 0u;
+        if (f == F_RHO) bad |= !(x[r] > 0.0f);
+      }
+    }
+    if constexpr (SHADOW) write_shadow(a.Sout + ((size_t)s * NF + f) * SHADOW_FIELD, c0, x[0], x[1]);
+  }
+  return bad;
+}
+
+// The update of mode 1..3 for the two owned cells of sub-grid s (loads in one
+// group in mode 1, two when the previous increment is read as well).
+template <int MODE, bool SHADOW>
+__device__ __forceinline__ unsigned update_inc(const StageArgs& a, int s, const Acc<float> (&acc)[NF], float lh,
+                                               float ll) {
+  const int c0 = owned_cell(0);
+  const size_t cell0 = (size_t)((c0 >> 6) + NG) * NP2 + (((c0 >> 3) & 7) + NG) * NP + ((c0 & 7) + NG);
+  unsigned nf = 0, bad = 0;
+  if constexpr (MODE >= 2) {
+    bad |= update_inc_fields<MODE, SHADOW, 0, 6>(a, s, acc, lh, ll, cell0, c0, nf);
+    bad |= update_inc_fields<MODE, SHADOW, 6, NF>(a, s, acc, lh, ll, cell0, c0, nf);
+  } else {
+    bad |= update_inc_fields<MODE, SHADOW, 0, NF>(a, s, acc, lh, ll, cell0, c0, nf);
+  }
+  return bad | (nf >> 31);
+}
+
+// Fields [F0, F1) of update_cells below.
 template <typename T, bool BLEND, bool SHADOW, int F0, int F1>
 __device__ __forceinline__ unsigned update_fields(const StageArgs& a, int s, const Acc<T> (&acc)[NF], double lam,
                                                   size_t cell0, int c0, unsigned& nf) {
-  const int tid = threadIdx.x;
   unsigned bad = 0;
   // every load of the group first: one memory latency per group, not per field
   double uin[F1 - F0][2], u0v[BLEND ? F1 - F0 : 1][2];
@@ -782,27 +905,18 @@ __device__ __forceinline__ unsigned update_fields(const StageArgs& a, int s, con
       nf |= nonfinite_bit(v[r]);
       if (f == F_RHO) bad |= bad64(v[r], true);
     }
-    if constexpr (SHADOW && sizeof(T) == 4) {
-      float* So = a.Sout + ((size_t)s * NF + f) * SHADOW_FIELD;
-      const float x0 = f64_to_f32(v[0]), x1 = f64_to_f32(v[1]);
-      So[c0] = x0;
-      So[c0 + 64] = x1;
-      // pairs in i (lane ^ 1), then in j (lane ^ 8), both cells of the k-pair at once
-      const float2 xi = make_float2(x0, x1);
-      const float2 p = add2(xi, make_float2(__shfl_xor_sync(0xffffffffu, x0, 1), __shfl_xor_sync(0xffffffffu, x1, 1)));
-      const float2 t = add2(p, make_float2(__shfl_xor_sync(0xffffffffu, p.x, 8), __shfl_xor_sync(0xffffffffu, p.y, 8)));
-      const int cc = (tid >> 6) * 16 + ((tid >> 4) & 3) * 4 + ((tid >> 1) & 3);
-      if ((tid & 9) == 0) So[SHADOW_COARSE + cc] = __fmul_rn(__fadd_rn(t.x, t.y), 0.125f);  // i and j even
-    }
+    if constexpr (SHADOW && sizeof(T) == 4)
+      write_shadow(a.Sout + ((size_t)s * NF + f) * SHADOW_FIELD, c0, f64_to_f32(v[0]), f64_to_f32(v[1]));
   }
   return bad;
 }
 
 // U_out = U* (or U0 + beta (U* - U0) when BLEND) for the two owned cells of
 // sub-grid s; SHADOW (mixed only) also writes the rounded cells and their
-// 2x2x2 restriction (FP32 pairwise sum, the partner cells by warp shuffles).  The loads are issued in one group (two with the blend, which
-// reads twice as many) so that their latencies overlap.  Returns non-zero if
-// a value is not finite or a density <= 0.
+// 2x2x2 restriction (FP32 pairwise sum, the partner cells by warp shuffles).
+// The loads are issued in one group (two with the blend, which reads twice as
+// many) so that their latencies overlap.  Returns non-zero if a value is not
+// finite or a density <= 0.
 template <typename T, bool BLEND, bool SHADOW>
 __device__ __forceinline__ unsigned update_cells(const StageArgs& a, int s, const Acc<T> (&acc)[NF], double lam) {
   const int c0 = owned_cell(0);
@@ -884,7 +998,19 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(
     direction_pass<T, 2>(sh, a, cur, nxt, pf, dt, acc, amax, gamma, eta);
 
     // update of the owned cells (and, mixed, the output's shadow)
-    if (blend) {
+    if (sizeof(T) == 4 && a.mode != 0) {
+      if constexpr (sizeof(T) == 4) {
+        const float lh = cur.lh, ll = cur.ll;
+        if (a.mode == 1)
+          bad |= update_inc<1, true>(a, s, acc, lh, ll);
+        else if (a.mode == 2)
+          bad |= update_inc<2, true>(a, s, acc, lh, ll);
+        else if (shadow_out)
+          bad |= update_inc<3, true>(a, s, acc, lh, ll);
+        else
+          bad |= update_inc<3, false>(a, s, acc, lh, ll);
+      }
+    } else if (blend) {
       if (shadow_out)
         bad |= update_cells<T, true, true>(a, s, acc, cur.lam);
       else
