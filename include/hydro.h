@@ -182,13 +182,20 @@ int hydro_fill_ghosts(hydro_handle *h, double *U, void *stream);
  * from the neighbours' interiors, so no ghost fill runs between stages.  The
  * batch must list every sub-grid once (n_items == n_subgrids, any order and
  * batch cut), since later stages read the neighbours' intermediate states;
- * otherwise HYDRO_ERR_INVALID.  Mixed precision: the graph writes the shadow
- * of U once and each stage then writes its output's shadow for the next.
+ * otherwise HYDRO_ERR_INVALID.  FP64: the Shu-Osher stages of hydro_step
+ * (beta = 1, 1/4, 2/3), scratch1 and scratch2 holding U1 and U2.  Mixed
+ * precision evaluates the same step in increment form, with L_k = dt/dx *
+ * dU(U_k): U1 = U + L0, U2 = U + (L0 + L1)/4, U_new = U + 2/3 ((L0 + L1)/4 + L2);
+ * the increments are kept as float pairs (about 48 bits) in scratch1 and
+ * scratch2, and U is changed once, by two FP64 additions per value.  The
+ * graph writes the FP32 shadow of U once; each stage writes the shadow of its
+ * state for the next (stages 1 and 2 as RN32(RN32(U) + increment), within one
+ * float32 ulp of the rounded state).
  *   U        DEVICE padded state; its interior is overwritten by the new state
  *            (ghost cells are neither read nor updated: call hydro_fill_ghosts
  *            when they are wanted);
- *   scratch1, scratch2  DEVICE padded states of the same size (contents
- *            destroyed);
+ *   scratch1, scratch2  DEVICE arrays of the size of a padded state
+ *            (contents destroyed);
  *   d_max_speed DEVICE double[2]: the max speeds of the first stage, i.e. of
  *            the state at the start of the step. */
 int hydro_rk3_step(hydro_handle *h, const hydro_batch *batch, double *U, double *scratch1, double *scratch2,

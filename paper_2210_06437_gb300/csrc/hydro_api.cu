@@ -72,7 +72,7 @@ struct hydro_handle {
   double* d_partial = nullptr;         // totals scratch (per-sub-grid and per-chunk partials)
   double* d_dt = nullptr;              // [1] time step read by graph replays
   unsigned long long* d_ms_tmp = nullptr;  // [2] speeds of RK stages 2 and 3
-  float* d_shadow[2] = {nullptr, nullptr};  // mixed precision: FP32 interior shadows [n][NF][512]
+  float* d_shadow[3] = {nullptr, nullptr, nullptr};  // mixed precision: FP32 shadows [n][NF][576]
   cudaStream_t cap_stream = nullptr;
   cudaStream_t last_stream = nullptr;
   int64_t launches = 0;
@@ -117,8 +117,7 @@ void free_all(hydro_handle* h) {
   cudaFree(h->d_partial);
   cudaFree(h->d_dt);
   cudaFree(h->d_ms_tmp);
-  cudaFree(h->d_shadow[0]);
-  cudaFree(h->d_shadow[1]);
+  for (float* p : h->d_shadow) cudaFree(p);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
 }
 
@@ -162,20 +161,24 @@ int stage_grid(hydro_handle* h, int n_items) {
 int enqueue_stage(hydro_handle* h, const int32_t* ids, int n_items, const double* Uin, const float* Sin,
                   const double* U0, double beta, double dt, const double* dt_dev, double* Uout, float* Sout,
                   unsigned long long* ms, int queue_slot, cudaStream_t st, int mode = 0, const double* Din = nullptr,
-                  double* Dout = nullptr) {
+                  double* Dout = nullptr, const float* S0 = nullptr) {
   CUDA_TRY(h, cudaMemsetAsync(ms, 0, 2 * sizeof(unsigned long long), st));
   if (n_items == 0) return HYDRO_OK;
   CUDA_TRY(h, cudaMemsetAsync(h->d_queue + queue_slot, 0, sizeof(unsigned int), st));
   StageArgs a;
   std::memset(&a, 0, sizeof(a));
-  const double* second = mode >= 2 ? Din : U0;  // the other FP64-layout array the update reads
-  if (encode_state_map(&a.tm_in, Uin, h->n)) {
+  // the FP64-layout arrays the update reads: Uin (and U0) in mode 0, nothing in
+  // mode 1, the increment in mode 2, U and the increment in mode 3
+  const double* first = mode == 0 || mode == 3 ? Uin : (mode == 2 ? Din : nullptr);
+  const double* second = mode == 3 ? Din : (mode == 0 ? U0 : nullptr);
+  if (first && encode_state_map(&a.tm_in, first, h->n)) {
     a.has_tm = 1;
     if (second && encode_state_map(&a.tm_u0, second, h->n)) a.has_tm |= 2;
   }
   a.mode = mode;
   a.Din = Din;
   a.Dout = Dout;
+  a.S0 = S0;
   a.Uin = Uin;
   a.U0 = U0;
   a.Uout = Uout;
@@ -279,7 +282,7 @@ int hydro_create(const hydro_grid_desc* d, hydro_handle** out) {
   ok = ok && cudaMalloc(&h->d_dt, sizeof(double)) == cudaSuccess;
   ok = ok && cudaMalloc(&h->d_ms_tmp, 2 * sizeof(unsigned long long)) == cudaSuccess;
   if (d->precision == HYDRO_MIXED)
-    for (int b = 0; b < 2; ++b)
+    for (int b = 0; b < 3; ++b)
       ok = ok && cudaMalloc(&h->d_shadow[b], sizeof(float) * (size_t)n * NF * SHADOW_FIELD) == cudaSuccess;
   if (!ok) {
     free_all(h);
@@ -420,30 +423,29 @@ int check_rk3(hydro_handle* h, const hydro_batch* batch, double* U, double* scra
   return HYDRO_OK;
 }
 
-// Enqueue the three stages of one RK3 step on cs.  Mixed precision: Sin is the
-// shadow of U, Smid the other shadow buffer; Sout_last, if not NULL, receives
-// the shadow of the new U (it must be Smid: free again after stage 2).  FP64:
-// the Shu-Osher stages U1 = U*(U), U2 = U + 1/4 (U*(U1) - U),
-// U3 = U + 2/3 (U*(U2) - U) through scratch1 and scratch2.  Mixed: the same
-// step in increment form (modes 1..3), scratch1 and scratch2 holding the
-// increment pairs, U changed once at the end.
+// Enqueue the three stages of one RK3 step on cs.  FP64: the Shu-Osher stages
+// U1 = U*(U), U2 = U + 1/4 (U*(U1) - U), U3 = U + 2/3 (U*(U2) - U) through
+// scratch1 and scratch2.  Mixed: the same step in increment form (modes 1..3),
+// scratch1 and scratch2 holding the increment pairs, U changed once at the
+// end; shadow buffers A = shadow of U (kept for the whole step), B = stage 1's
+// state, C = stage 2's; with write_next, stage 3 writes the new U's shadow into A.
 int enqueue_rk3_stages(hydro_handle* h, const int32_t* ids, int ni, double* U, double* s1, double* s2,
-                       unsigned long long* ms, float* Sin, float* Smid, float* Sout_last, cudaStream_t cs) {
+                       unsigned long long* ms, bool write_next, cudaStream_t cs) {
   int rc;
   if (h->precision == HYDRO_MIXED) {
-    rc = enqueue_stage(h, ids, ni, U, Sin, nullptr, 1.0, 0.0, h->d_dt, nullptr, Smid, ms, 0, cs, 1, nullptr, s1);
+    float *A = h->d_shadow[0], *B = h->d_shadow[1], *C = h->d_shadow[2];
+    rc = enqueue_stage(h, ids, ni, U, A, nullptr, 1.0, 0.0, h->d_dt, nullptr, B, ms, 0, cs, 1, nullptr, s1, A);
     if (!rc)
-      rc = enqueue_stage(h, ids, ni, U, Smid, nullptr, 1.0, 0.0, h->d_dt, nullptr, Sin, h->d_ms_tmp, 1, cs, 2, s1,
-                         s2);
+      rc = enqueue_stage(h, ids, ni, U, B, nullptr, 1.0, 0.0, h->d_dt, nullptr, C, h->d_ms_tmp, 1, cs, 2, s1, s2, A);
     if (!rc)
-      rc = enqueue_stage(h, ids, ni, U, Sin, nullptr, 1.0, 0.0, h->d_dt, U, Sout_last, h->d_ms_tmp, 2, cs, 3, s2,
-                         nullptr);
+      rc = enqueue_stage(h, ids, ni, U, C, nullptr, 1.0, 0.0, h->d_dt, U, write_next ? A : nullptr, h->d_ms_tmp, 2,
+                         cs, 3, s2, nullptr, A);
     return rc;
   }
-  rc = enqueue_stage(h, ids, ni, U, Sin, nullptr, 1.0, 0.0, h->d_dt, s1, Smid, ms, 0, cs);
-  if (!rc) rc = enqueue_stage(h, ids, ni, s1, Smid, U, 0.25, 0.0, h->d_dt, s2, Sin, h->d_ms_tmp, 1, cs);
+  rc = enqueue_stage(h, ids, ni, U, nullptr, nullptr, 1.0, 0.0, h->d_dt, s1, nullptr, ms, 0, cs);
+  if (!rc) rc = enqueue_stage(h, ids, ni, s1, nullptr, U, 0.25, 0.0, h->d_dt, s2, nullptr, h->d_ms_tmp, 1, cs);
   if (!rc)
-    rc = enqueue_stage(h, ids, ni, s2, Sin, U, 2.0 / 3.0, 0.0, h->d_dt, U, Sout_last, h->d_ms_tmp, 2, cs);
+    rc = enqueue_stage(h, ids, ni, s2, nullptr, U, 2.0 / 3.0, 0.0, h->d_dt, U, nullptr, h->d_ms_tmp, 2, cs);
   return rc;
 }
 
@@ -465,11 +467,9 @@ int get_graph(hydro_handle* h, const GraphKey& k, GraphEntry** out) {
   // no ghost fill is needed between stages; in mixed precision each stage
   // reads the shadow of its input and writes the shadow of its output
   const bool mixed = h->precision == HYDRO_MIXED;
-  float* Sa = h->d_shadow[0];
-  float* Sb = h->d_shadow[1];
-  int rc = mixed ? enqueue_shadow(h, k.U, Sa, cs) : HYDRO_OK;
+  int rc = mixed ? enqueue_shadow(h, k.U, h->d_shadow[0], cs) : HYDRO_OK;
   if (k.n_steps == 0) {
-    if (!rc) rc = enqueue_rk3_stages(h, k.ids, k.n_items, k.U, k.s1, k.s2, ms, Sa, Sb, nullptr, cs);
+    if (!rc) rc = enqueue_rk3_stages(h, k.ids, k.n_items, k.U, k.s1, k.s2, ms, false, cs);
   } else {
     for (int step = 0; step < k.n_steps && !rc; ++step) {
       cfl_dt<<<1, 1, 0, cs>>>(h->d_dt, k.dms, k.cfl, k.dt_out ? k.dt_out + step : nullptr);
@@ -479,11 +479,8 @@ int get_graph(hydro_handle* h, const GraphKey& k, GraphEntry** out) {
         break;
       }
       h->launches += 1;
-      const bool last = step + 1 == k.n_steps;
-      // step's input shadow in Sa; stage 3 leaves the new state's shadow in Sb
-      rc = enqueue_rk3_stages(h, k.ids, k.n_items, k.U, k.s1, k.s2, ms, mixed ? Sa : nullptr,
-                              mixed ? Sb : nullptr, (mixed && !last) ? Sb : nullptr, cs);
-      std::swap(Sa, Sb);
+      // stage 3 leaves the new state's shadow where the next step reads it
+      rc = enqueue_rk3_stages(h, k.ids, k.n_items, k.U, k.s1, k.s2, ms, mixed && step + 1 < k.n_steps, cs);
       if (!rc && k.totals) {
         e = launch_totals(k.U, h->n, h->d_dx, h->d_partial, k.totals + (size_t)step * NF, cs);
         if (e != cudaSuccess)

@@ -64,9 +64,12 @@ struct StageArgs {
   //   mode 1: Dout = L0,                     Sout ~ shadow of U + L0;
   //   mode 2: Dout = (Din + L1) / 4,         Sout ~ shadow of U + Dout;
   //   mode 3: Uout = U + 2/3 (Din + L2) (FP64), Sout (optional) = its shadow.
+  // Modes 1 and 2 take RN32(U) of their own cells from S0, the shadow of U
+  // (in mode 1 that is Sin itself), and read no FP64 state.
   int32_t mode;
   const double* Din;
   double* Dout;
+  const float* S0;
 };
 
 // Encode the TMA descriptor of a padded state (n sub-grids) used by

@@ -754,7 +754,8 @@ __device__ __forceinline__ void direction_pass(const Shared<T>& sh, const StageA
 // 48 bits; error-free TwoSums and products); the FP64 state is read by every
 // stage but changed only once, by two FP64 additions in stage 3.  Stages 1
 // and 2 write the shadow of their state as RN32(RN32(U) + D_hi), within one
-// FP32 ulp of the rounded state.
+// FP32 ulp of the rounded state, taking RN32(U) from the shadow of U, so they
+// read no FP64 state at all.
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
@@ -800,13 +801,17 @@ __device__ __forceinline__ unsigned update_inc_fields(const StageArgs& a, int s,
                                                       float lh, float ll, size_t cell0, int c0, unsigned& nf) {
   constexpr bool READ_D = MODE >= 2;
   unsigned bad = 0;
-  double u0v[F1 - F0][2], dv[READ_D ? F1 - F0 : 1][2];
+  double u0v[MODE == 3 ? F1 - F0 : 1][2], dv[READ_D ? F1 - F0 : 1][2];
+  float s0v[MODE < 3 ? F1 - F0 : 1][2];
 #pragma unroll
   for (int f = F0; f < F1; ++f)
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       const size_t o = field_offset(s, f) + cell0 + (size_t)r * NP2;
-      u0v[f - F0][r] = a.Uin[o];
+      if constexpr (MODE == 3)
+        u0v[f - F0][r] = a.Uin[o];
+      else
+        s0v[f - F0][r] = a.S0[((size_t)s * NF + f) * SHADOW_FIELD + c0 + r * 64];
       if constexpr (READ_D) dv[f - F0][r] = a.Din[o];
     }
   const float2 lh2 = make_float2(lh, lh), ll2 = make_float2(ll, ll);
@@ -842,7 +847,7 @@ __device__ __forceinline__ unsigned update_inc_fields(const StageArgs& a, int s,
         x[r] = f64_to_f32(v);
       } else {
         a.Dout[o] = pack_pair(dh, dl);
-        x[r] = __fadd_rn(f64_to_f32(u0v[f - F0][r]), dh);
+        x[r] = __fadd_rn(s0v[f - F0][r], dh);
         nf |= (__float_as_uint(x[r]) & 0x7f800000u) == 0x7f800000u ? 0x80000000u : 0u;
         if (f == F_RHO) bad |= !(x[r] > 0.0f);
       }
