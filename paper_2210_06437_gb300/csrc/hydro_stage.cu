@@ -376,6 +376,10 @@ __device__ __forceinline__ void cp_async8(double* dst, const double* src) {  // 
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(a), "l"(src));
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::); }
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {  // 16-byte global -> shared copy
+  const unsigned a = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(src));
+}
 __device__ __forceinline__ void cp_async4(float* dst, const float* src) {  // 4-byte global -> shared copy
   const unsigned a = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(a), "l"(src));
@@ -482,6 +486,47 @@ template <int D>
 __device__ __forceinline__ void gather_halo_shadow(const float* __restrict__ S, int s, const Nbr& nb, float* halo) {
   const int q = (int)threadIdx.x - (THREADS - HALO);
   if (q < 0) return;
+  if constexpr (D == 0) {
+    // x slabs: threads q < 128 take one (side, pencil) each and all 11 fields,
+    // into the pencil's 16-byte chunk: side 0 holds i = 4..7 of the low
+    // neighbour's row (elements 1..3 are the ghost layers -3..-1), side 1
+    // holds i = 0..3 of the high one (elements 0..2 are layers 8..10)
+    if (q >= 2 * NPEN) return;
+    const int p = q & 63, side = q >> 6;
+    const int t1 = p & 7, t2 = p >> 3;  // (j, k)
+    float* dst = halo + (side * NPEN + p) * 4;
+    constexpr int DF = 2 * NPEN * 4;  // per field
+    constexpr size_t FS = SHADOW_FIELD;
+    const int n0 = nb.id[side][0];
+    const int rel = nb.rel[side];
+    if (rel >= 0 && n0 >= 0) {
+      const float* src;
+      if (rel == 0) {
+        src = S + (size_t)n0 * NF * FS + shadow_index(side ? 0 : 4, t1, t2);
+      } else {
+        const int q1 = t1 >> 2, q2 = t2 >> 2;
+        src = S + (size_t)nb.id[side][q1 + 2 * q2] * NF * FS + SHADOW_COARSE + ((t2 - 4 * q2) * 4 + (t1 - 4 * q1)) * 4;
+      }
+#pragma unroll
+      for (int f = 0; f < NF; ++f) cp_async16(dst + f * DF, src + f * FS);
+    } else {
+      int off[NG];
+      const float* base = S + (size_t)(n0 >= 0 ? n0 : s) * NF * FS;
+#pragma unroll
+      for (int l = 0; l < NG; ++l) {
+        const int ga = side ? NX + l : l - NG;
+        const int fa = ga >= 0 ? ga / 2 : -((1 - ga) / 2);
+        off[l] = n0 < 0 ? shadow_index(side ? NX - 1 : 0, t1, t2)
+                        : shadow_index((side ? -4 : 8) + fa, 4 * ((nb.oct >> 1) & 1) + (t1 >> 1),
+                                       4 * ((nb.oct >> 2) & 1) + (t2 >> 1));
+      }
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+#pragma unroll
+        for (int l = 0; l < NG; ++l) cp_async4(dst + f * DF + (side ? l : l + 1), base + f * FS + off[l]);
+    }
+    return;
+  }
   int l, p;
   if (D == 0) {
     p = q / 3;
@@ -543,7 +588,9 @@ __device__ __forceinline__ int tile_index(int d, int p, int n) {
 template <typename T>
 struct StageSmem {
   static constexpr size_t interior = sizeof(T) * NF * ISZ;
-  static constexpr size_t halo = sizeof(T) * NF * 2 * HALO;
+  // FP32: the x slabs as one 16-byte chunk per (field, side, pencil), which is
+  // larger than the y/z layout [NF][2][HALO]
+  static constexpr size_t halo = sizeof(T) * (sizeof(T) == 4 ? NF * 2 * NPEN * 4 : NF * 2 * HALO);
   static constexpr size_t faces = sizeof(T) * 2 * NF * FACES_DIR;
   static constexpr size_t total = interior + halo + faces;
 };
@@ -605,11 +652,16 @@ struct Meta {
 
 // The next work item as warp 7 (threads 224..255, one PPM task fewer than
 // threads 0..191) fetches it while the current one is processed: the queue
-// ticket during x, the sub-grid id during y, the neighbour table during z, so
-// that each dependent load has a whole direction pass to arrive.
+// ticket after the x PPM, the sub-grid id after the y PPM, the neighbour table
+// loads before the z PPM (into registers) and their store after it, so that
+// each dependent load has a whole phase to arrive.
 struct Pf {
-  int item;  // queue ticket (lane 0 until shuffled)
-  int s;     // its sub-grid id, -1 past the end of the queue
+  int item;   // queue ticket (lane 0 until shuffled)
+  int s;      // its sub-grid id, -1 past the end of the queue, -2 bad id
+  int nbv;    // lane l < 24: neighbour entry l of s
+  int relv;   // lane l < 6: level relation of face l
+  int octv;   // lane 0: octant
+  double idx; // lane 0: 1/dx
 };
 
 __device__ __forceinline__ void pf_ticket(const StageArgs& a, Pf& pf) {
@@ -621,34 +673,46 @@ __device__ __forceinline__ void pf_id(const StageArgs& a, Pf& pf) {
   pf.s = pf.item < a.n_items ? a.ids[pf.item] : -1;
 }
 
-// Check the fetched id and read its neighbour table into m.
-__device__ __forceinline__ void pf_finish(const StageArgs& a, double dt, const Pf& pf, Meta& m) {
+// Check the fetched id and issue the loads of its neighbour table.
+__device__ __forceinline__ void pf_load(const StageArgs& a, Pf& pf) {
   const int lane = threadIdx.x & 31;
-  const int item = pf.item;
   int s = -1;
-  if (item < a.n_items) {
+  if (pf.item < a.n_items) {
     s = pf.s;
     if (s < 0 || s >= a.n_sub) {
       if (lane == 0) atomicOr(a.err, ERRBIT_BAD_ID);
       s = -2;
     }
   }
+  pf.s = s;
   if (s >= 0) {
-    if (lane < 24) m.nb.id[lane >> 2][lane & 3] = a.nb[(size_t)s * 24 + lane];
-    if (lane < 6) m.nb.rel[lane] = a.rel[s * 6 + lane];
+    if (lane < 24) pf.nbv = a.nb[(size_t)s * 24 + lane];
+    if (lane < 6) pf.relv = a.rel[s * 6 + lane];
     if (lane == 0) {
-      m.nb.oct = a.oct[s];
-      const double idx = a.inv_dx[s];
-      const double lam = dt * idx;
+      pf.octv = a.oct[s];
+      pf.idx = a.inv_dx[s];
+    }
+  }
+}
+
+// Store the fetched item into m.
+__device__ __forceinline__ void pf_store(double dt, const Pf& pf, Meta& m) {
+  const int lane = threadIdx.x & 31;
+  if (pf.s >= 0) {
+    if (lane < 24) m.nb.id[lane >> 2][lane & 3] = pf.nbv;
+    if (lane < 6) m.nb.rel[lane] = pf.relv;
+    if (lane == 0) {
+      m.nb.oct = pf.octv;
+      const double lam = dt * pf.idx;
       m.lam = lam;
-      m.idx = idx;
+      m.idx = pf.idx;
       m.lh = (float)lam;
       m.ll = (float)(lam - (double)m.lh);
     }
   }
   if (lane == 0) {
-    m.item = item;
-    m.s = s;
+    m.item = pf.item;
+    m.s = pf.s;
   }
 }
 
@@ -657,7 +721,8 @@ __device__ __forceinline__ void prefetch_meta(const StageArgs& a, double dt, Met
   Pf pf;
   pf_ticket(a, pf);
   pf_id(a, pf);
-  pf_finish(a, dt, pf, m);
+  pf_load(a, pf);
+  pf_store(dt, pf, m);
 }
 
 // One direction of the stage: PPM of every (field, pencil), the next
@@ -670,18 +735,26 @@ __device__ __forceinline__ void direction_pass(const Shared<T>& sh, const StageA
                                                T eta) {
   const int tid = threadIdx.x;
   if (D == 1) prefetch_update_rows(a, cur.s);
+  if (D == 2 && (tid >> 5) == THREADS / 32 - 1) pf_load(a, pf);
   // A: PPM, one (field, pencil) task per iteration
 #pragma unroll 1
   for (int task = tid; task < NF * NPEN; task += THREADS) {
     const int f = task >> 6, p = task & 63;
     T q[NP];
-    const T* hl = sh.halo + (f * 2) * HALO + p;
+    if constexpr (sizeof(T) == 4 && D == 0) {
+      const float4* hx = reinterpret_cast<const float4*>(sh.halo) + (f * 2) * NPEN + p;
+      const float4 h0 = hx[0], h1 = hx[NPEN];
+      q[0] = h0.y, q[1] = h0.z, q[2] = h0.w;
+      q[11] = h1.x, q[12] = h1.y, q[13] = h1.z;
+    } else {
+      const T* hl = sh.halo + (f * 2) * HALO + p;
 #pragma unroll
-    for (int m = 0; m < NG; ++m) q[m] = hl[m * NPEN];
+      for (int m = 0; m < NG; ++m) q[m] = hl[m * NPEN];
+#pragma unroll
+      for (int m = 0; m < NG; ++m) q[NG + NX + m] = hl[HALO + m * NPEN];
+    }
 #pragma unroll
     for (int n = 0; n < NX; ++n) q[NG + n] = sh.tile[f * ISZ + tile_index(D, p, n)];
-#pragma unroll
-    for (int m = 0; m < NG; ++m) q[NG + NX + m] = hl[HALO + m * NPEN];
     T ul[NFACE], ur[NFACE];
     ppm_pencil(q, ul, ur);
 #pragma unroll
@@ -693,7 +766,7 @@ __device__ __forceinline__ void direction_pass(const Shared<T>& sh, const StageA
   if ((tid >> 5) == THREADS / 32 - 1) {
     if (D == 0) pf_ticket(a, pf);
     if (D == 1) pf_id(a, pf);
-    if (D == 2) pf_finish(a, dt, pf, nxt);
+    if (D == 2) pf_store(dt, pf, nxt);
   }
   __syncthreads();
   // the halo buffer is free: start gathering the next slabs; after z the tile
