@@ -526,48 +526,49 @@ __device__ __forceinline__ void gather_halo_shadow(const float* __restrict__ S, 
         for (int l = 0; l < NG; ++l) cp_async4(dst + f * DF + (side ? l : l + 1), base + f * FS + off[l]);
     }
     return;
-  }
-  int l, p;
-  if (D == 0) {
-    p = q / 3;
-    l = q - 3 * p;
   } else {
-    l = q >> 6;
-    p = q & 63;
-  }
-  const int t1 = p & 7, t2 = p >> 3;
-  const int b1 = D == 0 ? 1 : 0;
-  const int b2 = D == 2 ? 1 : 2;
-#pragma unroll
-  for (int side = 0; side < 2; ++side) {
+    // y, z slabs: thread q takes one (field parity, side, layer, row t2, half)
+    // of 4 consecutive cells t1 = half*4 .. +3; same level, outflow and finer
+    // neighbours are one 16-byte copy per field, a coarser one four 4-byte
+    // copies
+    constexpr int b1 = 0, b2 = D == 2 ? 1 : 2;
+    constexpr size_t FS = SHADOW_FIELD;
+    const int half = q & 1, t2 = (q >> 1) & 7, rest = q >> 4;  // rest = f0 * 6 + side * 3 + layer
+    const int f0 = rest / (2 * NG), side = (rest % (2 * NG)) / NG, l = rest % NG;
     const int face = 2 * D + side;
     const int ga = side ? NX + l : l - NG;
-    float* dst = halo + side * HALO + l * NPEN + p;
+    float* dst = halo + side * HALO + l * NPEN + t2 * 8 + half * 4;
+    constexpr int DF = 2 * HALO;
     const int n0 = nb.id[face][0];
     const int rel = nb.rel[face];
-    int src_s, off;
-    if (n0 >= 0 && rel == 0) {  // same level
-      src_s = n0;
-      off = shadow_dbb<D>(side ? ga - NX : ga + NX, t1, t2);
-    } else if (n0 < 0) {  // domain boundary: outflow
-      src_s = s;
-      off = shadow_dbb<D>(side ? NX - 1 : 0, t1, t2);
-    } else if (rel < 0) {  // coarser: the coarse cell containing the ghost-cell centre
-      const int fa = ga >= 0 ? ga / 2 : -((1 - ga) / 2);
-      src_s = n0;
-      off = shadow_dbb<D>((side ? -4 : 8) + fa, 4 * ((nb.oct >> b1) & 1) + (t1 >> 1), 4 * ((nb.oct >> b2) & 1) + (t2 >> 1));
-    } else {  // finer: the restricted cell of the quadrant's neighbour
-      const int q1 = t1 >> 2, q2 = t2 >> 2;
-      src_s = nb.id[face][q1 + 2 * q2];
-      int c[3];
-      c[D] = side ? ga - NX : ga + 4;
-      c[b1] = t1 - 4 * q1;
-      c[b2] = t2 - 4 * q2;
-      off = SHADOW_COARSE + (c[2] * 4 + c[1]) * 4 + c[0];
-    }
-    const float* src = S + (size_t)src_s * NF * SHADOW_FIELD + off;
+    if (rel >= 0) {
+      const float* src;
+      if (rel == 0) {
+        const int src_s = n0 >= 0 ? n0 : s;
+        const int cd = n0 >= 0 ? (side ? ga - NX : ga + NX) : (side ? NX - 1 : 0);
+        src = S + (size_t)src_s * NF * FS + shadow_dbb<D>(cd, half * 4, t2);
+      } else {
+        const int q2 = t2 >> 2;
+        const int cdc = side ? ga - NX : ga + 4;
+        const int rr = t2 - 4 * q2;
+        src = S + (size_t)nb.id[face][half + 2 * q2] * NF * FS + SHADOW_COARSE +
+              (D == 1 ? (rr * 4 + cdc) * 4 : (cdc * 4 + rr) * 4);
+      }
 #pragma unroll
-    for (int f = 0; f < NF; ++f) cp_async4(dst + f * 2 * HALO, src + f * SHADOW_FIELD);
+      for (int f = f0; f < NF; f += 2) cp_async16(dst + f * DF, src + f * FS);
+    } else {
+      const int fa = ga >= 0 ? ga / 2 : -((1 - ga) / 2);
+      const float* base = S + (size_t)n0 * NF * FS;
+      int off[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        off[e] = shadow_dbb<D>((side ? -4 : 8) + fa, 4 * ((nb.oct >> b1) & 1) + ((half * 4 + e) >> 1),
+                               4 * ((nb.oct >> b2) & 1) + (t2 >> 1));
+#pragma unroll
+      for (int f = f0; f < NF; f += 2)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) cp_async4(dst + f * DF + e, base + f * FS + off[e]);
+    }
   }
 }
 
