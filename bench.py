@@ -46,10 +46,11 @@ GHOST_BYTES_PER_CELL = 396.0     # ghost fill: read + write 1152 face-slab cells
 SHADOW_BYTES_PER_CELL = 137.5    # FP32 shadow: read 88 B of FP64 interior, write 44 B + 5.5 B of restriction
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 2 FP64 FMA/clk/SM at the 2070 MHz maximum clock
 # DRAM bytes (read + write) per cell-update of the mixed stage kernel from one ncu capture
-# (profiles/stage_mixed_binary4k.md), valid only for the kernel source it was taken on.
-STAGE_TRAFFIC = {"sha256_prefix": "f13eb527fdd2e1d2", "bytes_per_cell": 479.7,
-                 "source": "ncu capture on the 4097-leaf reduced binary octree (beta = 1 stage with shadow "
-                           "output), scaled by cells"}
+# (average of the three RK3 stage launches, profiles/stage_mixed_binary4k.md), valid only for
+# the kernel source it was taken on.
+STAGE_TRAFFIC = {"sha256_prefix": "4ec8fbda4807480a", "bytes_per_cell": 450.3,
+                 "source": "ncu capture of the three RK3 stage launches on the 4097-leaf reduced binary octree "
+                           "(average), scaled by cells"}
 
 
 def stage_traffic_bytes(cells):
