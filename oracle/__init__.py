@@ -62,6 +62,7 @@ def lib():
                                    ctypes.c_void_p, dp, ctypes.c_void_p, ctypes.c_int]
         L.oracle_fill_ghosts.argtypes = [ctypes.POINTER(_Grid), ctypes.c_void_p]
         L.oracle_totals.argtypes = [ctypes.POINTER(_Grid), ctypes.c_void_p, dp]
+        L.oracle_diagnostics.argtypes = [ctypes.POINTER(_Grid), ctypes.c_void_p, ctypes.c_void_p, dp]
         _lib = L
     return _lib
 
@@ -155,3 +156,12 @@ class Oracle:
         t = np.zeros(NF)
         lib().oracle_totals(ctypes.byref(self._g), U.ctypes.data, _dptr(t))
         return t
+
+    def diagnostics(self, U: np.ndarray, origin: Optional[np.ndarray] = None) -> np.ndarray:
+        """[M, Lx, Ly, Lz, M1, X1, Y1, Z1, M2, X2, Y2, Z2] (Section V-B.1 diagnostics)."""
+        self._check(U)
+        o = np.ascontiguousarray(self.grid.origin if origin is None else origin, np.float64)
+        assert o.shape == (self.grid.n, 3)
+        out = np.zeros(12)
+        lib().oracle_diagnostics(ctypes.byref(self._g), U.ctypes.data, o.ctypes.data, _dptr(out))
+        return out

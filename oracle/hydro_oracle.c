@@ -348,3 +348,72 @@ void oracle_totals(const oracle_grid *g, const double *U, double *totals) {
     totals[f] = S + C;
   }
 }
+
+/* ------------------------------------------------------------------------- */
+/* Diagnostics (paper Section V-B.1, diagnostics task: total mass, total     */
+/* angular momentum, centre of mass of each star of a binary).               */
+/*                                                                           */
+/* Per interior cell of sub-grid s, centre (x, y, z) = origin_s + (i + 1/2,  */
+/* j + 1/2, k + 1/2) dx_s, each coordinate rounded as o + ((c + 1/2) * dx):  */
+/*   q0 = rho,                                    total mass M                */
+/*   q1..q3 = r x s = (y sz - z sy, z sx - x sz, x sy - y sx), angular        */
+/*            momentum about the origin, each product rounded separately;     */
+/*   q4 = rho X1, q5..q7 = rho X1 * (x, y, z)      star 1 (scalar field 6)     */
+/*   q8 = rho X2, q9..q11 = rho X2 * (x, y, z)     star 2 (scalar field 7)     */
+/* Q_q = sum_s dx_s^3 sum_cells q (Neumaier, in sub-grid order), then         */
+/* out = {M, Lx, Ly, Lz, M1, X1, Y1, Z1, M2, X2, Y2, Z2}, the centres being    */
+/* Q_{5..7} / Q_4 and Q_{9..11} / Q_8 (0 where the star mass is 0).           */
+/* ------------------------------------------------------------------------- */
+
+enum { NQ = 12 };
+
+static void cell_quantities(const double *U, int s, int k, int j, int i, const double *o, double dx, double *q) {
+  const double x = o[0] + (i + 0.5) * dx, y = o[1] + (j + 0.5) * dx, z = o[2] + (k + 0.5) * dx;
+  const int K = k + NG, J = j + NG, I = i + NG;
+  const double rho = U[at(s, F_RHO, K, J, I)];
+  const double sx = U[at(s, F_SX, K, J, I)], sy = U[at(s, F_SX + 1, K, J, I)], sz = U[at(s, F_SX + 2, K, J, I)];
+  const double m1 = U[at(s, 6, K, J, I)], m2 = U[at(s, 7, K, J, I)];
+  q[0] = rho;
+  q[1] = y * sz - z * sy;
+  q[2] = z * sx - x * sz;
+  q[3] = x * sy - y * sx;
+  q[4] = m1;
+  q[5] = m1 * x;
+  q[6] = m1 * y;
+  q[7] = m1 * z;
+  q[8] = m2;
+  q[9] = m2 * x;
+  q[10] = m2 * y;
+  q[11] = m2 * z;
+}
+
+void oracle_diagnostics(const oracle_grid *g, const double *U, const double *origin, double *out) {
+  double S[NQ], C[NQ];
+  for (int q = 0; q < NQ; ++q) S[q] = C[q] = 0.0;
+  for (int s = 0; s < g->n; ++s) {
+    double ss[NQ], sc[NQ], v[NQ];
+    for (int q = 0; q < NQ; ++q) ss[q] = sc[q] = 0.0;
+    for (int k = 0; k < NX; ++k)
+      for (int j = 0; j < NX; ++j)
+        for (int i = 0; i < NX; ++i) {
+          cell_quantities(U, s, k, j, i, origin + 3 * (size_t)s, g->dx[s], v);
+          for (int q = 0; q < NQ; ++q) neumaier_add(&ss[q], &sc[q], v[q]);
+        }
+    const double vol = g->dx[s] * g->dx[s] * g->dx[s];
+    for (int q = 0; q < NQ; ++q) {
+      neumaier_add(&S[q], &C[q], vol * ss[q]);
+      neumaier_add(&S[q], &C[q], vol * sc[q]);
+    }
+  }
+  double T[NQ];
+  for (int q = 0; q < NQ; ++q) T[q] = S[q] + C[q];
+  out[0] = T[0];
+  out[1] = T[1];
+  out[2] = T[2];
+  out[3] = T[3];
+  for (int star = 0; star < 2; ++star) {
+    const double m = T[4 + 4 * star];
+    out[4 + 4 * star] = m;
+    for (int c = 0; c < 3; ++c) out[5 + 4 * star + c] = m != 0.0 ? T[5 + 4 * star + c] / m : 0.0;
+  }
+}

@@ -17,7 +17,8 @@
  *           Shu-Osher RK blend; the maximum signal speed over all faces.
  *   ghosts: fill of the 6 face ghost slabs (3 layers) from neighbours: copy,
  *           coarse-to-fine injection, fine-to-coarse 2x2x2 mean, outflow.
- *   totals: Neumaier-compensated grid totals of the 11 fields.
+ *   totals: Neumaier-compensated grid totals of the 11 fields;
+ *   diagnostics: total mass, angular momentum, centre of mass of each star.
  *
  * Layout: U[s][f][k][j][i], 14^3 padded cells per field, interior 3..10.
  * Compile with -O2 -ffp-contract=off (no fused multiply-add, no fast-math).
@@ -74,6 +75,12 @@ int oracle_fill_ghosts(const oracle_grid *g, double *U);
 
 /* Grid totals T_f = sum_s dx_s^3 sum_cells U_f, Neumaier-compensated, fixed order. */
 void oracle_totals(const oracle_grid *g, const double *U, double *totals);
+
+/* Diagnostics (Section V-B.1 diagnostics task): out[12] = {M, Lx, Ly, Lz, M1,
+ * X1, Y1, Z1, M2, X2, Y2, Z2}: total mass, angular momentum about the origin,
+ * mass and centre of mass of star 1 (scalar field 6) and star 2 (field 7).
+ * origin[n][3] is the lower corner of each sub-grid's interior. */
+void oracle_diagnostics(const oracle_grid *g, const double *U, const double *origin, double *out);
 
 #ifdef __cplusplus
 }

@@ -442,3 +442,81 @@ def test_totals_match_exact_sum(oracle_mod):
     for f in range(W.NF):
         ex, ab = H.exact_total(w.grid, U, f)
         assert abs(t[f] - ex) <= 1e-15 * ab + 1e-300
+
+
+# ---------------------------------------------------------------------------
+# diagnostics (Section V-B.1: total mass, angular momentum, centre of mass of
+# each star), pinned by closed forms and by an identity between its outputs
+# ---------------------------------------------------------------------------
+
+def _box_state(nb, lo, h, fill):
+    """Padded state on a uniform non-periodic grid from fill(x, y, z) -> list of 11 global fields."""
+    g = W.uniform_grid(nb, lo, h, periodic=(False, False, False))
+    N = [n * W.NX for n in nb]
+    c = [lo[a] + (np.arange(N[a]) + 0.5) * h for a in range(3)]
+    z, y, x = np.meshgrid(c[2], c[1], c[0], indexing="ij")
+    G = np.stack(fill(x, y, z))
+    return g, H.scatter(G, nb)
+
+
+def test_diagnostics_solid_body_rotation_closed_form(oracle_mod):
+    """Uniform density rho0 rotating about z at omega in the cube [-a, a]^3:
+    Lz = rho0 omega sum (x_c^2 + y_c^2) h^3, and the midpoint rule for x^2 is
+    exact up to its known error: sum_i x_i^2 h = 2a^3/3 - a h^2/6 per axis."""
+    a, nbs = 1.0, 4
+    N = nbs * W.NX
+    h = 2 * a / N
+    rho0, om = 1.7, 0.3
+    zero = lambda x: np.zeros_like(x)
+
+    def fill(x, y, z):
+        rho = np.full_like(x, rho0)
+        return [rho, -rho0 * om * y, rho0 * om * x, zero(x), rho, rho, rho, zero(x), zero(x), zero(x), zero(x)]
+
+    g, U = _box_state((nbs, nbs, nbs), (-a, -a, -a), h, fill)
+    d = oracle_mod.Oracle(g).diagnostics(U)
+    sum_x2 = (2 * a) ** 2 * (2 * a ** 3 / 3 - a * h ** 2 / 6)   # sum over cells of x_c^2 h^3
+    Lz = rho0 * om * 2 * sum_x2
+    assert abs(d[3] - Lz) <= 1e-13 * Lz
+    assert abs(d[1]) <= 1e-14 * Lz and abs(d[2]) <= 1e-14 * Lz
+    assert abs(d[0] - rho0 * (2 * a) ** 3) <= 1e-13 * rho0 * (2 * a) ** 3
+    assert np.all(np.abs(d[5:8]) <= 1e-14)          # star 1 spread over the whole cube: centre 0
+    assert d[8] == 0.0 and np.all(d[9:12] == 0.0)   # no star 2
+
+
+def test_diagnostics_centre_of_symmetric_ball(oracle_mod):
+    """Star 1 material in a ball whose centre c is a cell corner, star 2 in
+    another: by symmetry each centre of mass is its ball's centre, each mass
+    the sum over the cells inside the ball."""
+    h = 1.0 / 16
+    c1, c2, R = np.array([0.25, -0.125, 0.5]), np.array([-0.375, 0.25, -0.25]), 0.3
+    zero = lambda x: np.zeros_like(x)
+
+    def fill(x, y, z):
+        in1 = ((x - c1[0]) ** 2 + (y - c1[1]) ** 2 + (z - c1[2]) ** 2 < R * R).astype(float)
+        in2 = ((x - c2[0]) ** 2 + (y - c2[1]) ** 2 + (z - c2[2]) ** 2 < R * R).astype(float)
+        rho = 0.1 + 2.0 * in1 + 3.0 * in2
+        return [rho, zero(x), zero(x), zero(x), rho, rho, 2.0 * in1, 3.0 * in2, zero(x), zero(x), zero(x)]
+
+    g, U = _box_state((4, 4, 4), (-1.0, -1.0, -1.0), h, fill)
+    d = oracle_mod.Oracle(g).diagnostics(U)
+    assert np.all(np.abs(d[5:8] - c1) <= 1e-14) and np.all(np.abs(d[9:12] - c2) <= 1e-14)
+    n1 = d[4] / (2.0 * h ** 3)
+    assert abs(n1 - round(n1)) <= 1e-9 and round(n1) > 100    # a whole number of cells
+    assert abs(d[8] / (3.0 * h ** 3) - round(n1)) <= 1e-9      # congruent balls
+
+
+def test_diagnostics_translation_identity(oracle_mod):
+    """For s = rho v with uniform v and star 1 = all the mass, the angular
+    momentum about the origin is M (R1 x v): pins the signs and indices of the
+    cross product against the first moments, on the AMR octree."""
+    w = W.config(3)
+    U = w.state()
+    v = np.array([0.3, -0.7, 1.1])
+    U[:, 1:4] = U[:, 0:1] * v[None, :, None, None, None]
+    U[:, 6] = U[:, 0]
+    d = oracle_mod.Oracle(w.grid).diagnostics(U)
+    expect = d[4] * np.cross(d[5:8], v)
+    scale = d[0] * np.abs(v).max() * 2.0
+    assert np.all(np.abs(d[1:4] - expect) <= 1e-13 * scale), (d[1:4], expect)
+    assert abs(d[4] - d[0]) <= 1e-14 * d[0]
