@@ -240,6 +240,20 @@ int hydro_rk3_run_prepare(hydro_handle *h, const hydro_batch *batch, double *U, 
  *   U DEVICE padded state; d_totals DEVICE double[11]. */
 int hydro_totals(hydro_handle *h, const double *U, double *d_totals, void *stream);
 
+/* Diagnostics (Section V-B.1, the diagnostics task: total mass, total angular
+ * momentum and the centre of mass of each star of a binary), deterministic
+ * like hydro_totals:
+ *   d_out[0]     M  = sum dx^3 rho
+ *   d_out[1..3]  L  = sum dx^3 (r x s), about the coordinate origin
+ *   d_out[4]     M1 = sum dx^3 rho X1   (star 1: scalar field 6)
+ *   d_out[5..7]  R1 = sum dx^3 rho X1 r / M1   (0 when M1 == 0)
+ *   d_out[8..11] M2, R2 likewise for star 2 (scalar field 7)
+ * with r the cell centre, each coordinate rounded as o + ((c + 1/2) * dx), and
+ * each product of r x s and rho X r rounded on its own.
+ *   U DEVICE padded state; d_origin DEVICE double[n_subgrids][3], the lower
+ *   corner of each sub-grid's interior; d_out DEVICE double[12]. */
+int hydro_diagnostics(hydro_handle *h, const double *U, const double *d_origin, double *d_out, void *stream);
+
 /* Allocation-free variant of hydro_totals for callers that cannot allocate
  * device memory (no cudaMalloc available to them: an allocator callback, a
  * framework that owns all device memory, a process with its memory reserved up

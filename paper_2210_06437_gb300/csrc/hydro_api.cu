@@ -71,6 +71,7 @@ struct hydro_handle {
   int* d_err = nullptr;                // device error word
   double* d_partial = nullptr;         // totals scratch (per-sub-grid and per-chunk partials)
   double* d_dt = nullptr;              // [1] time step read by graph replays
+  double* d_diag = nullptr;            // [12] diagnostics sums
   unsigned long long* d_ms_tmp = nullptr;  // [2] speeds of RK stages 2 and 3
   float* d_shadow[3] = {nullptr, nullptr, nullptr};  // mixed precision: FP32 shadows [n][NF][576]
   cudaStream_t cap_stream = nullptr;
@@ -116,6 +117,7 @@ void free_all(hydro_handle* h) {
   cudaFree(h->d_err);
   cudaFree(h->d_partial);
   cudaFree(h->d_dt);
+  cudaFree(h->d_diag);
   cudaFree(h->d_ms_tmp);
   for (float* p : h->d_shadow) cudaFree(p);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -280,6 +282,7 @@ int hydro_create(const hydro_grid_desc* d, hydro_handle** out) {
   ok = ok && cudaMalloc(&h->d_err, sizeof(int)) == cudaSuccess;
   ok = ok && cudaMalloc(&h->d_partial, sizeof(double) * totals_scratch_doubles(n)) == cudaSuccess;
   ok = ok && cudaMalloc(&h->d_dt, sizeof(double)) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->d_diag, 12 * sizeof(double)) == cudaSuccess;
   ok = ok && cudaMalloc(&h->d_ms_tmp, 2 * sizeof(unsigned long long)) == cudaSuccess;
   if (d->precision == HYDRO_MIXED)
     for (int b = 0; b < 3; ++b)
@@ -606,6 +609,18 @@ int hydro_totals(hydro_handle* h, const double* U, double* d_totals, void* strea
   cudaError_t e = launch_totals(U, h->n, h->d_dx, h->d_partial, d_totals, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "totals kernel launch");
   h->launches += 3;
+  return HYDRO_OK;
+}
+
+int hydro_diagnostics(hydro_handle* h, const double* U, const double* d_origin, double* d_out, void* stream) {
+  if (!h) return HYDRO_ERR_INVALID;
+  if (!U || !d_origin || !d_out || !aligned(U, 16) || !aligned(d_origin, 8) || !aligned(d_out, 8))
+    return fail(h, HYDRO_ERR_INVALID, "NULL or misaligned pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  cudaError_t e = launch_diagnostics(U, d_origin, h->n, h->d_dx, h->d_partial, h->d_diag, d_out, st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics kernel launch");
+  h->launches += 4;
   return HYDRO_OK;
 }
 

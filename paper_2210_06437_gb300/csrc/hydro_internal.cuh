@@ -101,6 +101,9 @@ int stage_blocks_per_sm_mixed();
 cudaError_t launch_ghost_fill(const GhostArgs& a, int threads, cudaStream_t st);
 // scratch doubles needed by launch_totals for n sub-grids
 size_t totals_scratch_doubles(int n);
+// Diagnostics sums into sums[12] (device scratch) and the results into out[12].
+cudaError_t launch_diagnostics(const double* U, const double* origin, int n, const double* dx, double* scratch,
+                               double* sums, double* out, cudaStream_t st);
 cudaError_t launch_totals(const double* U, int n, const double* dx, double* scratch, double* totals,
                           cudaStream_t st);
 

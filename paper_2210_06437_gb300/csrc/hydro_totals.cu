@@ -87,19 +87,61 @@ __device__ __forceinline__ void i128_to_dd(__int128 v, int e2, double& hi, doubl
 // (0x7ff: a value is not finite).
 constexpr int PARTIAL_WORDS = 3;
 
-__global__ void __launch_bounds__(TT) totals_subgrid(const double* __restrict__ U, int n,
-                                                     unsigned long long* __restrict__ partial) {
+// Per-cell quantity q of sub-grid s at interior cell c = (k*8 + j)*8 + i.
+// Totals: the 11 fields.
+struct FieldQ {
+  static constexpr int NQ = NF;
+  const double* U;
+  __device__ __forceinline__ double operator()(int s, int q, int c) const {
+    return U[field_offset(s, q) + (size_t)((c >> 6) + NG) * NP2 + (((c >> 3) & 7) + NG) * NP + ((c & 7) + NG)];
+  }
+};
+
+// Diagnostics (the paper's diagnostics task, Section V-B.1): with the cell
+// centre x = o + (i + 1/2) dx (each coordinate rounded as o + ((i + 1/2) * dx)),
+//   q0 rho; q1..3 r x s (each product rounded on its own); q4 rho X1 and
+//   q5..7 rho X1 * (x, y, z) (star 1, scalar field 6); q8..11 likewise for
+//   star 2 (field 7).
+struct DiagQ {
+  static constexpr int NQ = 12;
+  const double* U;
+  const double* origin;  // [n][3]
+  const double* dx;
+  __device__ __forceinline__ double at(int s, int f, int c) const {
+    return U[field_offset(s, f) + (size_t)((c >> 6) + NG) * NP2 + (((c >> 3) & 7) + NG) * NP + ((c & 7) + NG)];
+  }
+  __device__ __forceinline__ double coord(int s, int a, int ic) const {
+    return __dadd_rn(origin[3 * (size_t)s + a], __dmul_rn((double)ic + 0.5, dx[s]));
+  }
+  __device__ __forceinline__ double operator()(int s, int q, int c) const {
+    const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
+    if (q == 0) return at(s, F_RHO, c);
+    if (q <= 3) {
+      const int a = q - 1, b = (a + 1) % 3, e = (a + 2) % 3;  // (r x s)_a = r_b s_e - r_e s_b
+      const int ib = b == 0 ? i : (b == 1 ? j : k), ie = e == 0 ? i : (e == 1 ? j : k);
+      return __dsub_rn(__dmul_rn(coord(s, b, ib), at(s, F_SX + e, c)), __dmul_rn(coord(s, e, ie), at(s, F_SX + b, c)));
+    }
+    const int star = (q - 4) >> 2, m = (q - 4) & 3;
+    const double w = at(s, 6 + star, c);
+    if (m == 0) return w;
+    const int a = m - 1, ia = a == 0 ? i : (a == 1 ? j : k);
+    return __dmul_rn(w, coord(s, a, ia));
+  }
+};
+
+template <class Q>
+__global__ void __launch_bounds__(TT) totals_subgrid(const Q Qf, int n, unsigned long long* __restrict__ partial) {
+  constexpr int NQ = Q::NQ;
   const int gw = blockIdx.x * (TT / 32) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
-  if (gw >= n * NF) return;
-  const int s = gw / NF, f = gw - s * NF;
-  const double* base = U + field_offset(s, f) + NG * NP2 + NG * NP + NG;
+  if (gw >= n * NQ) return;
+  const int s = gw / NQ, f = gw - s * NQ;
   unsigned long long b[16];
   unsigned emax = 1;  // zero and subnormals count as exponent 1
 #pragma unroll
   for (int r = 0; r < 16; ++r) {
     const int c = lane + 32 * r;
-    b[r] = (unsigned long long)__double_as_longlong(base[(c >> 6) * NP2 + ((c >> 3) & 7) * NP + (c & 7)]);
+    b[r] = (unsigned long long)__double_as_longlong(Qf(s, f, c));
     const unsigned e = (unsigned)(b[r] >> 52) & 0x7ffu;
     emax = e > emax ? e : emax;
   }
@@ -128,7 +170,7 @@ __global__ void __launch_bounds__(TT) totals_subgrid(const double* __restrict__ 
     acc += (__int128)(((unsigned __int128)hi << 64) | lo);
   }
   if (lane == 0) {
-    unsigned long long* o = partial + ((size_t)s * NF + f) * PARTIAL_WORDS;
+    unsigned long long* o = partial + ((size_t)s * NQ + f) * PARTIAL_WORDS;
     o[0] = (unsigned long long)acc;
     o[1] = (unsigned long long)((unsigned __int128)acc >> 64);
     o[2] = emax;
@@ -154,14 +196,15 @@ __device__ __forceinline__ void subgrid_partial(const unsigned long long* w, dou
 
 // pass 2: block (f, chunk) sums the partials of its contiguous range of sub-grids
 __global__ void __launch_bounds__(TT) totals_chunks(const unsigned long long* __restrict__ partial,
-                                                    const double* __restrict__ dx, int n, double* __restrict__ chunk) {
+                                                    const double* __restrict__ dx, int n, int nq,
+                                                    double* __restrict__ chunk) {
   __shared__ Pair sh[TT / 32];
   const int f = blockIdx.x, ch = blockIdx.y;
   const int a = (int)((long long)n * ch / CHUNKS), b = (int)((long long)n * (ch + 1) / CHUNKS);
   Pair p{0.0, 0.0};
   for (int s = a + (int)threadIdx.x; s < b; s += TT) {
     double ps, pe;
-    subgrid_partial(partial + ((size_t)s * NF + f) * PARTIAL_WORDS, dx[s], ps, pe);
+    subgrid_partial(partial + ((size_t)s * nq + f) * PARTIAL_WORDS, dx[s], ps, pe);
     neumaier(p, ps);
     neumaier(p, pe);
   }
@@ -188,18 +231,45 @@ __global__ void totals_final(const double* __restrict__ chunk, double* __restric
   if (threadIdx.x == 0) totals[f] = p.s + p.c;
 }
 
+// diagnostics: centres of mass from the 12 sums (0 where a star has no mass)
+__global__ void diag_finish(const double* __restrict__ T, double* __restrict__ out) {
+  const int q = threadIdx.x;
+  if (q >= DiagQ::NQ) return;
+  if (q < 4 || q == 4 || q == 8) {
+    out[q] = T[q];
+  } else {
+    const double m = T[q < 8 ? 4 : 8];
+    out[q] = m != 0.0 ? __ddiv_rn(T[q], m) : 0.0;
+  }
+}
+
+template <class Q>
+void enqueue_sums(const Q& Qf, int n, const double* dx, double* scratch, double* sums, cudaStream_t st) {
+  constexpr int NQ = Q::NQ;
+  unsigned long long* partial = reinterpret_cast<unsigned long long*>(scratch);
+  double* chunk = scratch + (size_t)n * NQ * PARTIAL_WORDS;
+  const int warps = n * NQ;
+  totals_subgrid<Q><<<(warps + TT / 32 - 1) / (TT / 32), TT, 0, st>>>(Qf, n, partial);
+  totals_chunks<<<dim3(NQ, CHUNKS), TT, 0, st>>>(partial, dx, n, NQ, chunk);
+  totals_final<<<NQ, 32, 0, st>>>(chunk, sums);
+}
+
 }  // namespace
 
-size_t totals_scratch_doubles(int n) { return (size_t)n * NF * PARTIAL_WORDS + (size_t)NF * CHUNKS * 2; }
+size_t totals_scratch_doubles(int n) {
+  return (size_t)n * DiagQ::NQ * PARTIAL_WORDS + (size_t)DiagQ::NQ * CHUNKS * 2;  // enough for either
+}
 
 cudaError_t launch_totals(const double* U, int n, const double* dx, double* scratch, double* totals,
                           cudaStream_t st) {
-  unsigned long long* partial = reinterpret_cast<unsigned long long*>(scratch);
-  double* chunk = scratch + (size_t)n * NF * PARTIAL_WORDS;
-  const int warps = n * NF;
-  totals_subgrid<<<(warps + TT / 32 - 1) / (TT / 32), TT, 0, st>>>(U, n, partial);
-  totals_chunks<<<dim3(NF, CHUNKS), TT, 0, st>>>(partial, dx, n, chunk);
-  totals_final<<<NF, 32, 0, st>>>(chunk, totals);
+  enqueue_sums(FieldQ{U}, n, dx, scratch, totals, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diagnostics(const double* U, const double* origin, int n, const double* dx, double* scratch,
+                               double* sums, double* out, cudaStream_t st) {
+  enqueue_sums(DiagQ{U, origin, dx}, n, dx, scratch, sums, st);
+  diag_finish<<<1, 32, 0, st>>>(sums, out);
   return cudaGetLastError();
 }
 

@@ -27,7 +27,7 @@ STATUS = {0: "HYDRO_OK", -1: "HYDRO_ERR_INVALID", -2: "HYDRO_ERR_CUDA", -3: "HYD
 
 # every symbol include/hydro.h declares
 EXPORTS = ("hydro_create", "hydro_step", "hydro_shadow", "hydro_step_shadowed", "hydro_fill_ghosts", "hydro_rk3_step",
-           "hydro_rk3_step_cfl", "hydro_rk3_run_cfl", "hydro_rk3_run_prepare", "hydro_totals",
+           "hydro_rk3_step_cfl", "hydro_rk3_run_cfl", "hydro_rk3_run_prepare", "hydro_totals", "hydro_diagnostics",
            "hydro_totals_noalloc", "hydro_pack_interiors", "hydro_unpack_interiors", "hydro_sync",
            "hydro_last_error", "hydro_launch_count", "hydro_set_param", "hydro_destroy")
 SHADOW_FIELD = NX * NX * NX + (NX // 2) ** 3   # interior, then its 4^3 restriction
@@ -77,6 +77,7 @@ def load_library(path: str = LIB_PATH):
     L.hydro_rk3_run_cfl.argtypes = [vp, ctypes.POINTER(Batch), vp, vp, vp, dbl, i32, vp, vp, vp, vp]
     L.hydro_rk3_run_prepare.argtypes = [vp, ctypes.POINTER(Batch), vp, vp, vp, dbl, i32, vp, vp, vp]
     L.hydro_totals.argtypes = [vp, vp, vp, vp]
+    L.hydro_diagnostics.argtypes = [vp, vp, vp, vp, vp]
     L.hydro_totals_noalloc.argtypes = [vp, vp, i32, vp, vp]
     L.hydro_sync.argtypes = [vp]
     L.hydro_last_error.argtypes = [vp]
@@ -118,6 +119,8 @@ class HydroGrid:
         self.n = int(grid.n)
         self.precision = precision
         self._dx = np.ascontiguousarray(grid.dx, np.float64)
+        self._origin = getattr(grid, "origin", None)
+        self._origin_dev = None
         self._nb = np.ascontiguousarray(grid.neighbor, np.int32)
         self._rel = np.ascontiguousarray(grid.neighbor_rel, np.int8)
         self._oct = np.ascontiguousarray(grid.octant, np.int8)
@@ -311,6 +314,20 @@ class HydroGrid:
         self._state(U)
         out = torch.empty(NF, dtype=torch.float64, device=self.device) if out is None else out
         self._check(self.lib.hydro_totals(self.h, _ptr(U), _ptr(out), _stream_ptr(stream)))
+        return out
+
+    def diagnostics(self, U, out=None, stream=None):
+        """[M, Lx, Ly, Lz, M1, X1, Y1, Z1, M2, X2, Y2, Z2] (hydro_diagnostics);
+        needs the grid's sub-grid origins."""
+        import torch
+        self._state(U)
+        if self._origin_dev is None:
+            if self._origin is None:
+                raise ValueError("the grid descriptor has no sub-grid origins")
+            self._origin_dev = torch.as_tensor(np.ascontiguousarray(self._origin, np.float64), device=self.device)
+        out = torch.empty(12, dtype=torch.float64, device=self.device) if out is None else out
+        self._check(self.lib.hydro_diagnostics(self.h, _ptr(U), _ptr(self._origin_dev), _ptr(out),
+                                               _stream_ptr(stream)))
         return out
 
     def sync(self):

@@ -541,3 +541,39 @@ def test_pack_unpack_interiors(hydro):
     g.download(Ud, P, Ph)
     torch.cuda.synchronize()
     assert np.array_equal(Ph.numpy(), U[IN].reshape(n, 11, 512))
+
+
+# ---------------------------------------------------------------------------
+# diagnostics (total mass, angular momentum, centres of mass of the stars)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("cfg", [3, 5])
+def test_diagnostics_match_oracle(hydro, oracle_mod, cfg):
+    w = W.config(cfg)
+    U = w.state()
+    U[IN][:, 2] += 0.05 * U[IN][:, 0]       # some y momentum, so that Lx, Lz of config 5 are not zero
+    ref = oracle_mod.Oracle(w.grid).diagnostics(U)
+    g = hydro.HydroGrid(w.grid, precision="mixed")
+    got = g.diagnostics(_dev(U)).cpu().numpy()
+    g.sync()
+    # scales: total |mass| and sum |r| |s| dV
+    n = w.grid.n
+    c = (np.arange(8) + 0.5)
+    o, dx = w.grid.origin, w.grid.dx
+    x = o[:, 0, None, None, None] + c[None, None, None, :] * dx[:, None, None, None]
+    y = o[:, 1, None, None, None] + c[None, None, :, None] * dx[:, None, None, None]
+    z = o[:, 2, None, None, None] + c[None, :, None, None] * dx[:, None, None, None]
+    r = np.sqrt(x * x + y * y + z * z)
+    ui = U[IN]
+    vol = (dx ** 3)[:, None, None, None]
+    smag = np.sqrt(ui[:, 1] ** 2 + ui[:, 2] ** 2 + ui[:, 3] ** 2)
+    Lscale = np.sum(r * smag * vol)
+    M = np.sum(np.abs(ui[:, 0]) * vol)
+    assert abs(got[0] - ref[0]) <= 1e-14 * M
+    assert np.all(np.abs(got[1:4] - ref[1:4]) <= 1e-13 * Lscale), (got[1:4], ref[1:4])
+    rmax = r.max()
+    for k in (4, 8):
+        assert abs(got[k] - ref[k]) <= 1e-14 * M
+        assert np.all(np.abs(got[k + 1:k + 4] - ref[k + 1:k + 4]) <= 1e-13 * rmax), (got[k:k + 4], ref[k:k + 4])
+    if cfg == 5:   # two stars at x = -1.5 and +1.5
+        assert got[4] > 0 and got[8] > 0 and got[5] < -1.0 and got[9] > 1.0
