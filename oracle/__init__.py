@@ -41,7 +41,7 @@ def build(force: bool = False) -> str:
 class _Grid(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("gamma", ctypes.c_double), ("de_switch", ctypes.c_double),
                 ("flux_form", ctypes.c_int32), ("dx", ctypes.c_void_p), ("neighbor", ctypes.c_void_p),
-                ("neighbor_rel", ctypes.c_void_p), ("octant", ctypes.c_void_p)]
+                ("neighbor_rel", ctypes.c_void_p), ("octant", ctypes.c_void_p), ("reflux", ctypes.c_int32)]
 
 
 _lib = None
@@ -98,7 +98,8 @@ def face_flux(UL, UR, d, gamma=5.0 / 3.0, eta=1e-3, form=0):
 class Oracle:
     """Oracle bound to one grid descriptor (see ``paper_2210_06437_gb300.workloads.Grid``)."""
 
-    def __init__(self, grid, flux_form: int = 0, gamma: Optional[float] = None, de_switch: Optional[float] = None):
+    def __init__(self, grid, flux_form: int = 0, gamma: Optional[float] = None, de_switch: Optional[float] = None,
+                 reflux: bool = True):
         self.grid = grid
         self._dx = np.ascontiguousarray(grid.dx, np.float64)
         self._nb = np.ascontiguousarray(grid.neighbor, np.int32)
@@ -106,7 +107,8 @@ class Oracle:
         self._oct = np.ascontiguousarray(grid.octant, np.int8)
         self._g = _Grid(grid.n, grid.gamma if gamma is None else gamma,
                         grid.de_switch if de_switch is None else de_switch, flux_form,
-                        self._dx.ctypes.data, self._nb.ctypes.data, self._rel.ctypes.data, self._oct.ctypes.data)
+                        self._dx.ctypes.data, self._nb.ctypes.data, self._rel.ctypes.data, self._oct.ctypes.data,
+                        1 if reflux else 0)
 
     def _check(self, U):
         assert U.dtype == np.float64 and U.flags.c_contiguous and U.shape == (self.grid.n, NF, NP, NP, NP)

@@ -159,8 +159,9 @@ typedef struct {
   double flux[3][NF][NX][NX][NFACE]; /* [d][f][t2][t1][face], face m+1/2 for m = 2..10 */
 } work_t;
 
-static int stage_subgrid(const oracle_grid *g, int s, const double *Uin, const double *U0, double beta,
-                         double dt, double *Uout, double *amax_s, work_t *w) {
+/* Face fluxes of every pencil of sub-grid s into w->flux; returns the largest
+ * face speed. */
+static double flux_subgrid(const oracle_grid *g, int s, const double *Uin, work_t *w) {
   double q[NF][NP], aL[NF][NP], aR[NF][NP];
   double UL[NF], UR[NF], F[NF];
   double amax = 0.0;
@@ -183,7 +184,44 @@ static int stage_subgrid(const oracle_grid *g, int s, const double *Uin, const d
       }
     }
   }
-  *amax_s = amax;
+  return amax;
+}
+
+/* Coarse-fine flux correction (paper Section V-B.1: compute_fluxes corrects the
+ * fluxes on coarse-fine boundaries).  On every face of sub-grid s whose
+ * neighbours are finer, the flux of each coarse boundary face is replaced by
+ * the mean of the four fine fluxes over it, as the fine neighbour computes
+ * them on its own boundary face:
+ *   F = ((F(0,0) + F(1,0)) + (F(0,1) + F(1,1))) * 1/4,
+ * (a, b) the fine offsets along the face's first and second transverse axes.
+ * The fine side loses exactly what the coarse side gains, so the AMR step
+ * conserves to round-off.  w2 is scratch for the neighbours' fluxes. */
+static void correct_fluxes(const oracle_grid *g, int s, const double *Uin, work_t *w, work_t *w2) {
+  for (int face = 0; face < 6; ++face) {
+    if (g->neighbor_rel[s * 6 + face] != 1) continue;
+    const int d = face / 2, side = face % 2;
+    const int32_t *nb = g->neighbor + ((size_t)s * 6 + face) * 4;
+    const int mine = side ? NFACE - 1 : 0, theirs = side ? 0 : NFACE - 1;
+    for (int q = 0; q < 4; ++q) {
+      const int q1 = q & 1, q2 = q >> 1;
+      flux_subgrid(g, nb[q], Uin, w2);
+      for (int c2 = 4 * q2; c2 < 4 * q2 + 4; ++c2)
+        for (int c1 = 4 * q1; c1 < 4 * q1 + 4; ++c1) {
+          const int f1 = 2 * (c1 - 4 * q1), f2 = 2 * (c2 - 4 * q2);
+          for (int f = 0; f < NF; ++f) {
+            const double a00 = w2->flux[d][f][f2][f1][theirs], a10 = w2->flux[d][f][f2][f1 + 1][theirs];
+            const double a01 = w2->flux[d][f][f2 + 1][f1][theirs], a11 = w2->flux[d][f][f2 + 1][f1 + 1][theirs];
+            w->flux[d][f][c2][c1][mine] = ((a00 + a10) + (a01 + a11)) * 0.25;
+          }
+        }
+    }
+  }
+}
+
+static int stage_subgrid(const oracle_grid *g, int s, const double *Uin, const double *U0, double beta,
+                         double dt, double *Uout, double *amax_s, work_t *w, work_t *w2) {
+  *amax_s = flux_subgrid(g, s, Uin, w);
+  if (g->reflux) correct_fluxes(g, s, Uin, w, w2);
   double lam = dt / g->dx[s];
   int bad = 0;
   for (int k = NG; k < NG + NX; ++k) {
@@ -221,19 +259,21 @@ int oracle_stage(const oracle_grid *g, const int32_t *ids, int32_t n_ids, const 
 #endif
   {
     work_t *w = (work_t *)malloc(sizeof(work_t));
+    work_t *w2 = (work_t *)malloc(sizeof(work_t));
 #ifdef _OPENMP
 #pragma omp for schedule(dynamic, 4)
 #endif
     for (int t = 0; t < n; ++t) {
       int s = ids ? ids[t] : t;
       double a = 0.0;
-      bad |= stage_subgrid(g, s, Uin, U0, beta, dt, Uout, &a, w);
+      bad |= stage_subgrid(g, s, Uin, U0, beta, dt, Uout, &a, w, w2);
       if (sub_amax) sub_amax[s] = a;
       if (a != a) bad = 1;
       if (a > amax) amax = a;
       if (a / g->dx[s] > amax_dx) amax_dx = a / g->dx[s];
     }
     free(w);
+    free(w2);
   }
   (void)nthreads;
   max_speed[0] = amax;

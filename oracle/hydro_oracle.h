@@ -13,8 +13,10 @@
  *   stage:  per sub-grid, per direction, PPM (Colella-Woodward) reconstruction
  *           of the 11 conserved fields on the 9 faces of every pencil, face EOS
  *           with dual-energy switch, central-upwind (Kurganov-Noelle-Petrova)
- *           or central (Kurganov-Tadmor) flux, flux-divergence update and
- *           Shu-Osher RK blend; the maximum signal speed over all faces.
+ *           or central (Kurganov-Tadmor) flux, the coarse-fine flux
+ *           correction (coarse boundary faces take the mean of the four fine
+ *           fluxes), flux-divergence update and Shu-Osher RK blend; the
+ *           maximum signal speed over all faces.
  *   ghosts: fill of the 6 face ghost slabs (3 layers) from neighbours: copy,
  *           coarse-to-fine injection, fine-to-coarse 2x2x2 mean, outflow.
  *   totals: Neumaier-compensated grid totals of the 11 fields;
@@ -40,6 +42,7 @@ typedef struct {
   const int32_t *neighbor;     /* [n][6][4] face neighbours, see workloads */
   const int8_t *neighbor_rel;  /* [n][6] level(neighbour) - level(self) */
   const int8_t *octant;        /* [n] position in the parent: bit0 x, bit1 y, bit2 z */
+  int32_t reflux;              /* 1: coarse-fine flux correction (the default), 0: none */
 } oracle_grid;
 
 /* status codes */

@@ -10,7 +10,11 @@ communication the sharded step needs); the stage then runs on the local grid
 exactly as on a single domain, because it reads neighbours' interiors only.
 The maximum signal speed is combined with ``allreduce(MAX)``.
 
-Index logic and data movement only; no solver arithmetic.  One process per
+Index logic and data movement only; no solver arithmetic.  The coarse-fine
+flux correction of a stage needs a finer neighbour's flux on its face toward
+the coarse sub-grid; for a remote finer neighbour that flux is recomputed on
+its proxy slot, from the proxy's interior and the ghosts of that face (the
+owned coarse sub-grid), so the exchange stays interiors only.  One process per
 GPU would run the CUDA library on the local grid; on CPU ranks the same plan
 drives the oracle, which is how the tests validate it.
 """
@@ -79,7 +83,18 @@ def build(grid: Grid, rank: int, world: int) -> Partition:
     o_nb = grid.neighbor[owned]
     nb[:len(owned)] = np.where(o_nb >= 0, lut[np.maximum(o_nb, 0)], -1)
     rel[:len(owned)] = grid.neighbor_rel[owned]
-    # proxy slots are never advanced; their descriptor rows only need to be valid
+    # proxy slots are never advanced; a face of a proxy keeps its neighbours
+    # where they are all local (the coarse-fine flux correction recomputes a
+    # finer proxy's flux on its face toward the owned sub-grid, which needs
+    # that face's ghosts); other faces become outflow, which only changes
+    # fluxes nobody uses
+    for r, gid in enumerate(proxies, start=len(owned)):
+        for face in range(6):
+            relf = grid.neighbor_rel[gid, face]
+            ids = grid.neighbor[gid, face, :4 if relf == 1 else 1]
+            if np.all(ids >= 0) and np.all(lut[ids] >= 0):
+                nb[r, face, :len(ids)] = lut[ids]
+                rel[r, face] = relf
     local = Grid(n=m, dx=grid.dx[gids].copy(), origin=grid.origin[gids].copy(), level=grid.level[gids].copy(),
                  octant=grid.octant[gids].copy(), neighbor=nb, neighbor_rel=rel, periodic=grid.periodic,
                  gamma=grid.gamma, de_switch=grid.de_switch)
