@@ -169,7 +169,7 @@ def oracle_rate(w, U, out, target_s=10.0, seed=0):
     while True:
         ids = np.sort(rng.choice(w.grid.n, min(n, w.grid.n), replace=False)).astype(np.int32)
         t0 = time.perf_counter()
-        o.stage(U, 1e-6, Uout=out, ids=ids)
+        o.stage(U, 1e-6, Uout=out, ids=ids, batch_all=True)
         t = time.perf_counter() - t0
         if t >= target_s or n >= w.grid.n:
             break
@@ -196,7 +196,7 @@ def run_reference(args):
     for k in range(args.warmup + args.steps):
         t0 = time.perf_counter()
         for beta in (1.0, 0.25, 2.0 / 3.0):
-            o.stage(U, 1e-6, U0=U, beta=beta, Uout=out, ids=ids)
+            o.stage(U, 1e-6, U0=U, beta=beta, Uout=out, ids=ids, batch_all=True)
         dt = time.perf_counter() - t0
         if k >= args.warmup:
             times.append(dt)

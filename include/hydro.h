@@ -127,7 +127,14 @@ int hydro_create(const hydro_grid_desc *desc, hydro_handle **out);
  *   stream cudaStream_t (NULL = legacy default stream).
  * A mixed-precision handle first writes the FP32 shadow of U_in (hydro_shadow,
  * all sub-grids, into the handle's own buffer); hydro_step_shadowed skips that
- * pass when the caller already holds the shadow. */
+ * pass when the caller already holds the shadow.
+ * Coarse-fine flux correction (Section V-B.1: compute_fluxes corrects the
+ * fluxes on coarse-fine boundaries; HYDRO_PARAM_REFLUX, on by default): where
+ * a listed sub-grid meets four finer neighbours, each coarse boundary face
+ * takes the flux ((F00 + F10) + (F01 + F11)) / 4 of the fine faces over it, as
+ * the fine neighbours computed them in the same call, so an AMR step conserves
+ * to round-off; a quadrant whose fine neighbour is not listed keeps the coarse
+ * flux.  It runs as a second launch after the stage kernel. */
 int hydro_step(hydro_handle *h, const hydro_batch *batch, const double *U_in, const double *U0, double beta,
                double dt, double *U_out, double *d_max_speed, void *stream);
 
@@ -291,7 +298,8 @@ int hydro_set_param(hydro_handle *h, int32_t key, int32_t value);
 
 typedef enum {
   HYDRO_PARAM_STAGE_CTAS_PER_SM = 0, /* persistent CTAs per SM for the stage kernel, 1..8 (0 = auto) */
-  HYDRO_PARAM_GHOST_THREADS = 1      /* threads per CTA of the ghost-fill kernel, 64..1024 */
+  HYDRO_PARAM_GHOST_THREADS = 1,     /* threads per CTA of the ghost-fill kernel, 64..1024 */
+  HYDRO_PARAM_REFLUX = 2             /* coarse-fine flux correction: 1 (default) or 0 */
 } hydro_param;
 
 /* Release the handle and its device scratch (waits for its work first). */

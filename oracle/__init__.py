@@ -59,7 +59,7 @@ def lib():
         L.oracle_face_flux.restype = ctypes.c_double
         L.oracle_stage.argtypes = [ctypes.POINTER(_Grid), ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
-                                   ctypes.c_void_p, dp, ctypes.c_void_p, ctypes.c_int]
+                                   ctypes.c_void_p, dp, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
         L.oracle_fill_ghosts.argtypes = [ctypes.POINTER(_Grid), ctypes.c_void_p]
         L.oracle_totals.argtypes = [ctypes.POINTER(_Grid), ctypes.c_void_p, dp]
         L.oracle_diagnostics.argtypes = [ctypes.POINTER(_Grid), ctypes.c_void_p, ctypes.c_void_p, dp]
@@ -120,9 +120,12 @@ class Oracle:
 
     def stage(self, Uin: np.ndarray, dt: float, U0: Optional[np.ndarray] = None, beta: float = 1.0,
               Uout: Optional[np.ndarray] = None, ids=None, nthreads: int = 0,
-              sub_amax: Optional[np.ndarray] = None):
+              sub_amax: Optional[np.ndarray] = None, batch_all: bool = False):
         """One RK stage Uout = U0 + beta (U* - U0), U* = Uin + dt/dx dU; returns
-        (Uout, max_speed[2], status).  Uout defaults to a copy of Uin."""
+        (Uout, max_speed[2], status).  Uout defaults to a copy of Uin.  The
+        coarse-fine flux correction uses the finer neighbours advanced by the
+        same call: those in `ids`, or every sub-grid with batch_all (a call on
+        the whole grid of which only `ids` are computed here)."""
         self._check(Uin)
         if Uout is None:
             Uout = Uin.copy()
@@ -135,7 +138,8 @@ class Oracle:
         st = lib().oracle_stage(ctypes.byref(self._g), None if ids is None else ids.ctypes.data,
                                 0 if ids is None else len(ids), Uin.ctypes.data,
                                 None if U0 is None else U0.ctypes.data, beta, dt, Uout.ctypes.data,
-                                _dptr(ms), None if sub_amax is None else sub_amax.ctypes.data, nthreads)
+                                _dptr(ms), None if sub_amax is None else sub_amax.ctypes.data, nthreads,
+                                1 if batch_all else 0)
         return Uout, ms, st
 
     def rk3_step(self, U: np.ndarray, dt: float, nthreads: int = 0):

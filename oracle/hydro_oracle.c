@@ -195,8 +195,11 @@ static double flux_subgrid(const oracle_grid *g, int s, const double *Uin, work_
  *   F = ((F(0,0) + F(1,0)) + (F(0,1) + F(1,1))) * 1/4,
  * (a, b) the fine offsets along the face's first and second transverse axes.
  * The fine side loses exactly what the coarse side gains, so the AMR step
- * conserves to round-off.  w2 is scratch for the neighbours' fluxes. */
-static void correct_fluxes(const oracle_grid *g, int s, const double *Uin, work_t *w, work_t *w2) {
+ * conserves to round-off.  Only fine neighbours advanced in the same call
+ * (listed in `in_batch`, or all when it is NULL) count; elsewhere the coarse
+ * flux stays.  w2 is scratch for the neighbours' fluxes. */
+static void correct_fluxes(const oracle_grid *g, int s, const double *Uin, const unsigned char *in_batch, work_t *w,
+                           work_t *w2) {
   for (int face = 0; face < 6; ++face) {
     if (g->neighbor_rel[s * 6 + face] != 1) continue;
     const int d = face / 2, side = face % 2;
@@ -204,6 +207,7 @@ static void correct_fluxes(const oracle_grid *g, int s, const double *Uin, work_
     const int mine = side ? NFACE - 1 : 0, theirs = side ? 0 : NFACE - 1;
     for (int q = 0; q < 4; ++q) {
       const int q1 = q & 1, q2 = q >> 1;
+      if (in_batch && !in_batch[nb[q]]) continue;
       flux_subgrid(g, nb[q], Uin, w2);
       for (int c2 = 4 * q2; c2 < 4 * q2 + 4; ++c2)
         for (int c1 = 4 * q1; c1 < 4 * q1 + 4; ++c1) {
@@ -219,9 +223,10 @@ static void correct_fluxes(const oracle_grid *g, int s, const double *Uin, work_
 }
 
 static int stage_subgrid(const oracle_grid *g, int s, const double *Uin, const double *U0, double beta,
-                         double dt, double *Uout, double *amax_s, work_t *w, work_t *w2) {
+                         double dt, double *Uout, double *amax_s, const unsigned char *in_batch, work_t *w,
+                         work_t *w2) {
   *amax_s = flux_subgrid(g, s, Uin, w);
-  if (g->reflux) correct_fluxes(g, s, Uin, w, w2);
+  if (g->reflux) correct_fluxes(g, s, Uin, in_batch, w, w2);
   double lam = dt / g->dx[s];
   int bad = 0;
   for (int k = NG; k < NG + NX; ++k) {
@@ -247,12 +252,19 @@ static int stage_subgrid(const oracle_grid *g, int s, const double *Uin, const d
 }
 
 int oracle_stage(const oracle_grid *g, const int32_t *ids, int32_t n_ids, const double *Uin, const double *U0,
-                 double beta, double dt, double *Uout, double *max_speed, double *sub_amax, int nthreads) {
+                 double beta, double dt, double *Uout, double *max_speed, double *sub_amax, int nthreads,
+                 int batch_all) {
   if (!g || !Uin || !Uout || !max_speed || n_ids < 0) return ORACLE_ERR_INVALID;
   if (beta != 1.0 && !U0) return ORACLE_ERR_INVALID;
   int n = ids ? n_ids : g->n;
   double amax = 0.0, amax_dx = 0.0;
   int bad = 0;
+  unsigned char *in_batch = NULL;
+  if (ids && !batch_all) {
+    in_batch = (unsigned char *)calloc((size_t)g->n, 1);
+    for (int t = 0; t < n_ids; ++t)
+      if (ids[t] >= 0 && ids[t] < g->n) in_batch[ids[t]] = 1;
+  }
 #ifdef _OPENMP
   if (nthreads <= 0) nthreads = omp_get_max_threads();
 #pragma omp parallel num_threads(nthreads) reduction(max : amax, amax_dx) reduction(| : bad)
@@ -266,7 +278,7 @@ int oracle_stage(const oracle_grid *g, const int32_t *ids, int32_t n_ids, const 
     for (int t = 0; t < n; ++t) {
       int s = ids ? ids[t] : t;
       double a = 0.0;
-      bad |= stage_subgrid(g, s, Uin, U0, beta, dt, Uout, &a, w, w2);
+      bad |= stage_subgrid(g, s, Uin, U0, beta, dt, Uout, &a, in_batch, w, w2);
       if (sub_amax) sub_amax[s] = a;
       if (a != a) bad = 1;
       if (a > amax) amax = a;
@@ -276,6 +288,7 @@ int oracle_stage(const oracle_grid *g, const int32_t *ids, int32_t n_ids, const 
     free(w2);
   }
   (void)nthreads;
+  free(in_batch);
   max_speed[0] = amax;
   max_speed[1] = amax_dx;
   return bad ? ORACLE_ERR_NONFINITE : ORACLE_OK;

@@ -69,9 +69,13 @@ double oracle_face_flux(const double *UL, const double *UR, int d, double gamma,
  * max_speed[0] = max amax_s, max_speed[1] = max amax_s/dx_s over the listed
  * sub-grids; sub_amax (optional, [n]) receives amax_s.  nthreads <= 0 uses the
  * OpenMP default.  Returns ORACLE_ERR_NONFINITE if an output is not finite or
- * a density is not positive (outputs are still written). */
+ * a density is not positive (outputs are still written).
+ * batch_all: the coarse-fine flux correction counts every sub-grid as advanced
+ * by this call (a batch that lists all of them, of which only `ids` are
+ * computed here); 0: only the listed ones. */
 int oracle_stage(const oracle_grid *g, const int32_t *ids, int32_t n_ids, const double *Uin, const double *U0,
-                 double beta, double dt, double *Uout, double *max_speed, double *sub_amax, int nthreads);
+                 double beta, double dt, double *Uout, double *max_speed, double *sub_amax, int nthreads,
+                 int batch_all);
 
 /* Fill the six face ghost slabs of every sub-grid from the interiors. */
 int oracle_fill_ghosts(const oracle_grid *g, double *U);

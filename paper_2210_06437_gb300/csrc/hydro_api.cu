@@ -74,6 +74,13 @@ struct hydro_handle {
   double* d_diag = nullptr;            // [12] diagnostics sums
   unsigned long long* d_ms_tmp = nullptr;  // [2] speeds of RK stages 2 and 3
   float* d_shadow[3] = {nullptr, nullptr, nullptr};  // mixed precision: FP32 shadows [n][NF][576]
+  // coarse-fine flux correction
+  int reflux = 1;
+  int n_cf = 0;                        // coarse sub-grids with a finer face neighbour
+  int32_t* d_cf = nullptr;             // [n_cf]
+  void* d_fb = nullptr;                // [n][6][NF][64] exported boundary fluxes (T)
+  int32_t* d_fb_stamp = nullptr;       // [n]
+  int32_t call_counter = 0;
   cudaStream_t cap_stream = nullptr;
   cudaStream_t last_stream = nullptr;
   int64_t launches = 0;
@@ -120,6 +127,9 @@ void free_all(hydro_handle* h) {
   cudaFree(h->d_diag);
   cudaFree(h->d_ms_tmp);
   for (float* p : h->d_shadow) cudaFree(p);
+  cudaFree(h->d_cf);
+  cudaFree(h->d_fb);
+  cudaFree(h->d_fb_stamp);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
 }
 
@@ -203,10 +213,40 @@ int enqueue_stage(hydro_handle* h, const int32_t* ids, int n_items, const double
   a.queue = h->d_queue + queue_slot;
   a.err = h->d_err;
   a.max_speed = ms;
+  const bool reflux = h->reflux && h->n_cf > 0;
+  if (reflux) {
+    a.fb = h->d_fb;
+    a.fb_stamp = h->d_fb_stamp;
+    a.call_id = ++h->call_counter;
+  }
   const int grid = stage_grid(h, n_items);
   cudaError_t e = h->precision == HYDRO_MIXED ? launch_stage_mixed(a, grid, st) : launch_stage_fp64(a, grid, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "stage kernel launch");
   h->launches += 1;
+  if (reflux) {
+    RefluxArgs r;
+    std::memset(&r, 0, sizeof(r));
+    r.list = h->d_cf;
+    r.n_list = h->n_cf;
+    r.fb = h->d_fb;
+    r.fb_stamp = h->d_fb_stamp;
+    r.call_id = a.call_id;
+    r.nb = h->d_nb;
+    r.rel = h->d_rel;
+    r.inv_dx = h->d_inv_dx;
+    r.dt = dt;
+    r.dt_dev = dt_dev;
+    r.mode = mode;
+    r.beta = beta;
+    r.U = Uout;
+    r.D = Dout;
+    r.S0 = S0;
+    r.Sout = Sout;
+    r.err = h->d_err;
+    e = h->precision == HYDRO_MIXED ? launch_reflux_mixed(r, st) : launch_reflux_fp64(r, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "flux correction kernel launch");
+    h->launches += 1;
+  }
   return HYDRO_OK;
 }
 
@@ -284,6 +324,24 @@ int hydro_create(const hydro_grid_desc* d, hydro_handle** out) {
   ok = ok && cudaMalloc(&h->d_dt, sizeof(double)) == cudaSuccess;
   ok = ok && cudaMalloc(&h->d_diag, 12 * sizeof(double)) == cudaSuccess;
   ok = ok && cudaMalloc(&h->d_ms_tmp, 2 * sizeof(unsigned long long)) == cudaSuccess;
+  {
+    std::vector<int32_t> cf;
+    for (int s = 0; s < n; ++s)
+      for (int f = 0; f < 6; ++f)
+        if (d->neighbor_rel[s * 6 + f] == 1) {
+          cf.push_back(s);
+          break;
+        }
+    h->n_cf = (int)cf.size();
+    if (h->n_cf > 0) {
+      const size_t tsize = d->precision == HYDRO_MIXED ? sizeof(float) : sizeof(double);
+      ok = ok && cudaMalloc(&h->d_cf, sizeof(int32_t) * cf.size()) == cudaSuccess;
+      ok = ok && cudaMalloc(&h->d_fb, tsize * (size_t)n * 6 * NF * NPEN) == cudaSuccess;
+      ok = ok && cudaMalloc(&h->d_fb_stamp, sizeof(int32_t) * n) == cudaSuccess;
+      ok = ok && cudaMemcpy(h->d_cf, cf.data(), sizeof(int32_t) * cf.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+      ok = ok && cudaMemset(h->d_fb_stamp, 0, sizeof(int32_t) * n) == cudaSuccess;
+    }
+  }
   if (d->precision == HYDRO_MIXED)
     for (int b = 0; b < 3; ++b)
       ok = ok && cudaMalloc(&h->d_shadow[b], sizeof(float) * (size_t)n * NF * SHADOW_FIELD) == cudaSuccess;
@@ -644,6 +702,13 @@ int hydro_set_param(hydro_handle* h, int32_t key, int32_t value) {
   if (key == HYDRO_PARAM_STAGE_CTAS_PER_SM) {
     if (value < 0 || value > 8) return fail(h, HYDRO_ERR_INVALID, "ctas per SM out of range");
     h->ctas_per_sm = value;
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+    return HYDRO_OK;
+  }
+  if (key == HYDRO_PARAM_REFLUX) {
+    if (value != 0 && value != 1) return fail(h, HYDRO_ERR_INVALID, "reflux must be 0 or 1");
+    h->reflux = value;
     for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
     h->graphs.clear();
     return HYDRO_OK;

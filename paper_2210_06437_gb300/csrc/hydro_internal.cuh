@@ -70,6 +70,35 @@ struct StageArgs {
   const double* Din;
   double* Dout;
   const float* S0;
+  // coarse-fine flux correction: when fb is set, each sub-grid stamps
+  // fb_stamp[s] = call_id and stores its fluxes on every coarse-fine face:
+  // fb[(s*6 + face)][f][pencil] (T), pencil = t2*8 + t1 across the face
+  void* fb;
+  int32_t* fb_stamp;
+  int32_t call_id;
+};
+
+// Coarse-fine flux correction after a stage (one CTA per coarse sub-grid of
+// `list`): each coarse boundary face flux is replaced by the mean of the four
+// fine fluxes over it, for the finer neighbours advanced by the same call.
+struct RefluxArgs {
+  const int32_t* list;   // coarse sub-grids with at least one finer face neighbour
+  int32_t n_list;
+  const void* fb;        // stage flux export (see StageArgs)
+  const int32_t* fb_stamp;
+  int32_t call_id;
+  const int32_t* nb;     // [n][6][4]
+  const int8_t* rel;     // [n][6]
+  const double* inv_dx;
+  double dt;
+  const double* dt_dev;
+  int32_t mode;          // the stage's mode (StageArgs)
+  double beta;           // mode 0
+  double* U;             // mode 0 and 3: the stage's FP64 output
+  double* D;             // modes 1, 2: the stage's increment output
+  const float* S0;       // modes 1, 2: shadow of the step's input state
+  float* Sout;           // the stage's shadow output, refreshed where corrected (may be null)
+  int* err;
 };
 
 // Encode the TMA descriptor of a padded state (n sub-grids) used by
@@ -92,6 +121,8 @@ constexpr int SHADOW_FIELD = CELLS + CELLS / 8;  // 576 floats per field
 
 // launchers (defined in the .cu files)
 cudaError_t launch_shadow(const double* U, float* S, int n, cudaStream_t st);
+cudaError_t launch_reflux_fp64(const RefluxArgs& r, cudaStream_t st);
+cudaError_t launch_reflux_mixed(const RefluxArgs& r, cudaStream_t st);
 cudaError_t launch_pack(const double* U, double* P, int n, cudaStream_t st);
 cudaError_t launch_unpack(const double* P, double* U, int n, cudaStream_t st);
 cudaError_t launch_stage_fp64(const StageArgs& a, int grid, cudaStream_t st);

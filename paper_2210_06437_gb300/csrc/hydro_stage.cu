@@ -30,6 +30,7 @@
 // is done in FP64 (2 FP64 operations per value in stage 1, 3 with the blend).
 #include <cmath>
 
+#include "hydro_fp.cuh"
 #include "hydro_internal.cuh"
 
 namespace hydro {
@@ -43,31 +44,6 @@ constexpr int HALO = 3 * NPEN;   // cells per halo slab (3 layers x 64 pencils)
 // ---------------------------------------------------------------------------
 // precision traits
 // ---------------------------------------------------------------------------
-
-// FP64 -> FP32 with integer operations: round to nearest on the magnitude
-// (ties away from zero); values below the FP32 normal range become signed
-// zero, larger finite values infinity, NaN stays NaN.
-__device__ __forceinline__ float f64_to_f32(double x) {
-  const unsigned lo = (unsigned)__double2loint(x), hi = (unsigned)__double2hiint(x);
-  const unsigned mag = hi & 0x7fffffffu;
-  unsigned r = __funnelshift_l(lo, hi, 3) + ((lo >> 28) & 1u) - 0xC0000000u;
-  if (mag - 0x38100000u >= 0x0FE00000u) {
-    r = mag < 0x38100000u ? 0u : ((mag > 0x7ff00000u || (mag == 0x7ff00000u && lo)) ? 0x7fc00000u : 0x7f800000u);
-  }
-  return __uint_as_float(r | (hi & 0x80000000u));
-}
-
-// FP32 -> FP64, exact, with integer operations (FP32 subnormals become zero).
-__device__ __forceinline__ double f32_to_f64(float f) {
-  const unsigned b = __float_as_uint(f), mag = b & 0x7fffffffu;
-  unsigned hi = (mag >> 3) + 0x38000000u, lo = b << 29;
-  if (mag - 0x00800000u >= 0x7f000000u) {
-    const bool small = mag < 0x00800000u;
-    hi = small ? 0u : (0x7ff00000u | (mag >> 3));
-    lo = small ? 0u : lo;
-  }
-  return __hiloint2double((int)(hi | (b & 0x80000000u)), (int)lo);
-}
 
 template <typename T>
 struct Arith;
@@ -813,6 +789,17 @@ __device__ __forceinline__ void direction_pass(const Shared<T>& sh, const StageA
         acc[f].add_diff(lo0, hi0, lo1, hi1);
     }
   }
+  // coarse-fine faces: export this direction's boundary fluxes for the
+  // correction pass
+  if (a.fb) {
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      if (cur.nb.rel[2 * D + side] == 0) continue;
+      T* dst = static_cast<T*>(a.fb) + ((size_t)cur.s * 6 + 2 * D + side) * NF * NPEN;
+      const int m = side ? NFACE - 1 : 0;
+      for (int e = tid; e < NF * NPEN; e += THREADS) dst[e] = sh.fsl[(e >> 6) * FACES_DIR + (e & 63) * NFACE + m];
+    }
+  }
   // the next direction's halo is in place and the face buffers are free (after
   // z, the loop head's barrier does both for the next sub-grid)
   if (D < 2) {
@@ -1068,6 +1055,7 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(
     }
     cp_async_wait_all();
     __syncthreads();  // interior tile and x halo in place
+    if (a.fb_stamp && tid == 0) a.fb_stamp[s] = a.call_id;
 
     Acc<T> acc[NF];
     Pf pf;

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libhydro.so")
 NF, NP, NX, NG = 11, 14, 8, 3
 HYDRO_FP64, HYDRO_MIXED = 0, 1
 HYDRO_FLUX_KNP, HYDRO_FLUX_KT = 0, 1
-PARAM_STAGE_CTAS_PER_SM, PARAM_GHOST_THREADS = 0, 1
+PARAM_STAGE_CTAS_PER_SM, PARAM_GHOST_THREADS, PARAM_REFLUX = 0, 1, 2
 RK3_BETA = (1.0, 0.25, 2.0 / 3.0)
 
 STATUS = {0: "HYDRO_OK", -1: "HYDRO_ERR_INVALID", -2: "HYDRO_ERR_CUDA", -3: "HYDRO_ERR_NOMEM",

@@ -84,3 +84,30 @@ def exact_total(grid, U, f):
 
 def quasi_1d_grid(nx_sub, dx, periodic_x):
     return W.uniform_grid((nx_sub, 1, 1), (0.0, 0.0, 0.0), dx, periodic=(periodic_x, True, True))
+
+
+def amr_blob_state(seed=3):
+    """Small outflow octree refined around a blob; density, velocity and
+    scalars vary inside |r| < 0.6 and are uniform (velocity zero) outside, so
+    nothing crosses the domain boundary."""
+    R = 0.6
+
+    def bump(x, y, z):
+        r2 = (x * x + y * y + z * z) / (R * R)
+        return np.where(r2 < 1.0, (1.0 - r2) ** 3, 0.0)
+
+    rng = np.random.Generator(np.random.PCG64(seed))
+    g = W.octree_grid((2, 2, 2), (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0), 2, 9,
+                      lambda x, y, z: 0.05 + bump(x, y, z), rng)
+    U = W.empty_state(g.n)
+    c = (np.arange(W.NX) + 0.5)
+    for s in range(g.n):
+        o, h = g.origin[s], g.dx[s]
+        z, y, x = np.meshgrid(o[2] + c * h, o[1] + c * h, o[0] + c * h, indexing="ij")
+        b = bump(x, y, z)
+        rho = 1.0 + 0.5 * b
+        vx, vy, vz = (-0.6 * y + 0.3) * b, (0.6 * x - 0.2) * b, 0.4 * b
+        X = [b, 1.0 - b, 0.5 * b, np.zeros_like(b), np.zeros_like(b)]
+        U[s, :, W.NG:W.NG + W.NX, W.NG:W.NG + W.NX, W.NG:W.NG + W.NX] = np.stack(
+            W.conserved_from_primitive(rho, vx, vy, vz, np.ones_like(b), X))
+    return g, U

@@ -67,7 +67,9 @@ def _worker(rank, world, port, cfg, steps, out):
             P.exchange(p, Uin, dist)
             o.fill_ghosts(Uin)
             Uout = Uin.copy()
-            _, ms, st = o.stage(Uin, dt, U0=U0, beta=beta, Uout=Uout, ids=own, nthreads=2)
+            # every sub-grid of the global grid is advanced by this stage (the
+            # proxies by their owners), which the flux correction needs to know
+            _, ms, st = o.stage(Uin, dt, U0=U0, beta=beta, Uout=Uout, ids=own, nthreads=2, batch_all=True)
             assert st == 0
             return Uout, P.allreduce_max(ms, dist)
 
