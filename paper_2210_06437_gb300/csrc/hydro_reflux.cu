@@ -43,8 +43,8 @@ template <typename T>
 __global__ void __launch_bounds__(RT) reflux_kernel(const RefluxArgs r) {
   const int s = r.list[blockIdx.x];
   if (r.fb_stamp[s] != r.call_id) return;  // not advanced by this call
-  __shared__ unsigned char touched[CELLS];
-  for (int c = threadIdx.x; c < CELLS; c += RT) touched[c] = 0;
+  __shared__ unsigned char blocks[64];  // 2x2x2 blocks of the restriction next to a corrected face
+  if (threadIdx.x < 64) blocks[threadIdx.x] = 0;
   const double dt = r.dt_dev ? *r.dt_dev : r.dt;
   const double lam = dt * r.inv_dx[s];
   const T* fb = static_cast<const T*>(r.fb);
@@ -66,7 +66,8 @@ __global__ void __launch_bounds__(RT) reflux_kernel(const RefluxArgs r) {
       face_cell(face, t1, t2, i, j, k);
       const int c = (k * NX + j) * NX + i;
       const size_t o = ((size_t)s * NF + f) * NP3 + interior_offset(i, j, k);
-      touched[c] = 1;
+      if (f == 0) blocks[((k >> 1) * 4 + (j >> 1)) * 4 + (i >> 1)] = 1;
+      float x = 0.0f;  // the cell's new shadow value (mixed)
       if constexpr (sizeof(T) == 8) {
         const double delta = (((double)a00 + (double)a10) + ((double)a01 + (double)a11)) * 0.25 - (double)own[e];
         const double v = fma(r.beta * lam * sgn, delta, r.U[o]);
@@ -90,12 +91,14 @@ __global__ void __launch_bounds__(RT) reflux_kernel(const RefluxArgs r) {
           const double v = fma(w, f32_to_f64(ch), fma(w, f32_to_f64(cl), r.U[o]));
           r.U[o] = v;
           bad |= bad_value(v, f == F_RHO);
+          x = f64_to_f32(v);
         } else if (r.mode == 3) {
           constexpr float th = (float)(2.0 / 3.0), tl = (float)(2.0 / 3.0 - (double)(float)(2.0 / 3.0));
           pair_mul1(ch, cl, th, tl, ch, cl);
           const double v = __dadd_rn(__dadd_rn(r.U[o], f32_to_f64(ch)), f32_to_f64(cl));
           r.U[o] = v;
           bad |= bad_value(v, f == F_RHO);
+          x = f64_to_f32(v);
         } else {
           if (r.mode == 2) {
             ch = __fmul_rn(ch, 0.25f);
@@ -105,31 +108,21 @@ __global__ void __launch_bounds__(RT) reflux_kernel(const RefluxArgs r) {
           float dh = __int_as_float(__double2hiint(d)), dl = __int_as_float(__double2loint(d));
           pair_add1(dh, dl, ch, cl, dh, dl);
           r.D[o] = __hiloint2double(__float_as_int(dh), __float_as_int(dl));
+          x = __fadd_rn(r.S0[((size_t)s * NF + f) * SHADOW_FIELD + c], dh);
+          if (!(x - x == 0.0f) || (f == F_RHO && !(x > 0.0f))) bad = 1;
         }
+        // a cell on two or three corrected faces is rewritten by each in turn
+        if (r.Sout) r.Sout[((size_t)s * NF + f) * SHADOW_FIELD + c] = x;
       }
     }
     __syncthreads();
   }
-  // refresh the shadow of the corrected cells, then the sub-grid's restriction
+  // refresh the restriction blocks next to corrected faces
   if constexpr (sizeof(T) == 4) {
     if (r.Sout) {
-      for (int e = threadIdx.x; e < NF * CELLS; e += RT) {
-        const int f = e >> 9, c = e & (CELLS - 1);
-        if (!touched[c]) continue;
-        const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
-        const size_t o = ((size_t)s * NF + f) * NP3 + interior_offset(i, j, k);
-        float x;
-        if (r.mode == 0 || r.mode == 3) {
-          x = f64_to_f32(r.U[o]);
-        } else {
-          x = __fadd_rn(r.S0[((size_t)s * NF + f) * SHADOW_FIELD + c], __int_as_float(__double2hiint(r.D[o])));
-          if (!(x - x == 0.0f) || (f == F_RHO && !(x > 0.0f))) bad = 1;
-        }
-        r.Sout[((size_t)s * NF + f) * SHADOW_FIELD + c] = x;
-      }
-      __syncthreads();
       for (int e = threadIdx.x; e < NF * 64; e += RT) {
         const int f = e >> 6, cc = e & 63;
+        if (!blocks[cc]) continue;
         const int I = cc & 3, J = (cc >> 2) & 3, K = cc >> 4;
         const float* x = r.Sout + ((size_t)s * NF + f) * SHADOW_FIELD;
         float h[2];
