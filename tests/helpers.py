@@ -111,3 +111,43 @@ def amr_blob_state(seed=3):
         U[s, :, W.NG:W.NG + W.NX, W.NG:W.NG + W.NX, W.NG:W.NG + W.NX] = np.stack(
             W.conserved_from_primitive(rho, vx, vy, vz, np.ones_like(b), X))
     return g, U
+
+
+def neighbours(grid, ids):
+    """Global ids read across the faces of sub-grids ids (same level, coarser, finer)."""
+    nb = grid.neighbor[ids]
+    rel = grid.neighbor_rel[ids]
+    used = np.zeros_like(nb, dtype=bool)
+    used[:, :, 0] = nb[:, :, 0] >= 0
+    used[:, :, 1:] = (rel == 1)[:, :, None]
+    return np.unique(nb[used])
+
+
+def cone_grid(grid, sample, rings):
+    """A standalone grid made of `sample` and `rings` rings of face neighbours
+    around it (faces leaving the set become outflow).  Returns (local grid,
+    global ids in local order, local index of every ring: list of arrays, ring
+    0 = sample).  An RK stage computed on the local grid is exact on ring r
+    when its input is exact on ring r + 1."""
+    rings_g = [np.unique(np.asarray(sample, np.int64))]
+    for _ in range(rings):
+        rings_g.append(np.union1d(rings_g[-1], neighbours(grid, rings_g[-1])))
+    gids = rings_g[-1]
+    lut = np.full(grid.n, -1, np.int64)
+    lut[gids] = np.arange(len(gids))
+    nb = grid.neighbor[gids]
+    rel = grid.neighbor_rel[gids].copy()
+    loc = np.where(nb >= 0, lut[np.maximum(nb, 0)], -1).astype(np.int32)
+    # a face whose neighbours are not all local becomes outflow
+    for r in range(len(gids)):
+        for f in range(6):
+            k = 4 if rel[r, f] == 1 else 1
+            if np.any(loc[r, f, :k] < 0):
+                loc[r, f, :] = -1
+                rel[r, f] = 0
+            elif rel[r, f] != 1:
+                loc[r, f, 1:] = -1
+    g = W.Grid(n=len(gids), dx=grid.dx[gids].copy(), origin=grid.origin[gids].copy(), level=grid.level[gids].copy(),
+               octant=grid.octant[gids].copy(), neighbor=loc, neighbor_rel=rel, periodic=False, gamma=grid.gamma,
+               de_switch=grid.de_switch)
+    return g, gids, [lut[r] for r in rings_g]

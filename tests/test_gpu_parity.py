@@ -614,3 +614,36 @@ def test_amr_step_conserves_and_matches_oracle(hydro, oracle_mod, prec):
         else:
             assert max(drift) > 1e-9, drift
         g.close()
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_full_size_rk3_in_bench_launch(hydro, oracle_mod, prec):
+    """The benchmark's path on its full workload: one hydro_rk3_run_cfl step
+    (graph of the three stage launches with their flux corrections, increment
+    form in mixed precision) on all 65536 sub-grids, against the oracle's
+    SSP-RK3 step on the cone of 48 sampled sub-grids and the three rings of
+    face neighbours that the three stages read."""
+    w = W.config(5)
+    U = _filled(oracle_mod, w)
+    rng = np.random.default_rng(55)
+    sample = np.sort(rng.choice(w.grid.n, 48, replace=False))
+    gl, gids, rings = H.cone_grid(w.grid, sample, 3)
+    o = oracle_mod.Oracle(gl)
+    UL = np.ascontiguousarray(U[gids])
+    _, ms0, st = oracle_mod.Oracle(w.grid).stage(U, 0.0, ids=sample.astype(np.int32), batch_all=True)
+    dt = 0.4 / ms0[1]
+    ref, _, st = o.rk3_step(UL, dt)
+    ref = ref[rings[0]]
+    g = hydro.HydroGrid(w.grid, precision=prec)
+    del U, UL
+    Ud = _dev(w.state())
+    s1, s2 = torch.empty_like(Ud), torch.empty_like(Ud)
+    ids = torch.as_tensor(w.batches.ids, device="cuda")
+    ms = torch.tensor([0.0, 0.4 / dt], dtype=torch.float64, device="cuda")
+    dts = torch.zeros(1, dtype=torch.float64, device="cuda")
+    g.rk3_run_cfl(Ud, 0.4, s1, s2, ms, 1, ids=ids, batch_offsets=w.batches.offsets, dt_out=dts)
+    g.sync()
+    assert abs(dts.item() - dt) <= 1e-15 * dt
+    got = Ud.index_select(0, torch.as_tensor(sample, device="cuda", dtype=torch.long)).cpu().numpy()
+    err = field_errors(got, ref)
+    assert np.all(err <= TOL[prec]), (err, field_errors(got, ref, plain=True))
