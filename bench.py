@@ -48,7 +48,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 2 FP64 FMA/clk/SM at the 207
 # DRAM bytes (read + write) per cell-update of the mixed stage kernel from one ncu capture
 # (average of the three RK3 stage launches, profiles/stage_mixed_binary4k.md), valid only for
 # the kernel source it was taken on.
-STAGE_TRAFFIC = {"sha256_prefix": "4ec8fbda4807480a", "bytes_per_cell": 450.3,
+STAGE_TRAFFIC = {"sha256_prefix": "b8c7442fdce96d30", "bytes_per_cell": 459.0,
                  "source": "ncu capture of the three RK3 stage launches on the 4097-leaf reduced binary octree "
                            "(average), scaled by cells"}
 
@@ -317,7 +317,7 @@ def main():
             t_single = timed(lambda: g.step(U, 1e-9, U_out=s1, ids=ids, batch_offsets=offs, max_speed=ms2))
         # the stage kernel as the RK3 graph launches it: K steps without totals,
         # minus the one shadow pass, over the 3K stage launches (the dt kernels
-        # take microseconds)
+        # take microseconds; each stage's flux-correction pass is counted in)
         U_save = U.clone()
         g.rk3_run_prepare(U, 0.4, s1, s2, ms, args.steps, ids=ids, batch_offsets=offs)
         t_run = timed(lambda: g.rk3_run_cfl(U, 0.4, s1, s2, ms, args.steps, ids=ids, batch_offsets=offs))
@@ -435,7 +435,8 @@ def main():
     roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": traffic,
             "traffic_source": STAGE_TRAFFIC["source"] if traffic else "kernel changed since the last capture",
             "kernel": "stage_kernel<float>, the 3 stage launches of the mixed SSP-RK3 graph (increment form), "
-                      "average", "peak_source": hbm_src,
+                      "average; each launch's time includes the coarse-fine flux-correction pass that follows it "
+                      "(reflux_kernel, about 4 % of it)", "peak_source": hbm_src,
             "bytes_per_cell_update": BYTES_PER_CELL_RK3_STAGE, "launch_ms": t_st * 1e3}
     kernels = {
         "stage_mixed_ms": t_st * 1e3, "stage_mixed_single_beta1_ms": r["t_single"] * 1e3,

@@ -44,7 +44,17 @@ __global__ void __launch_bounds__(RT) reflux_kernel(const RefluxArgs r) {
   const int s = r.list[blockIdx.x];
   if (r.fb_stamp[s] != r.call_id) return;  // not advanced by this call
   __shared__ unsigned char blocks[64];  // 2x2x2 blocks of the restriction next to a corrected face
+  __shared__ int q_fs[6][4];             // the fine neighbour of each face quadrant, -1 if not advanced
   if (threadIdx.x < 64) blocks[threadIdx.x] = 0;
+  if (threadIdx.x < 24) {
+    const int face = threadIdx.x >> 2;
+    int fs = -1;
+    if (r.rel[s * 6 + face] == 1) {
+      fs = r.nb[(size_t)s * 24 + threadIdx.x];
+      if (r.fb_stamp[fs] != r.call_id) fs = -1;
+    }
+    q_fs[face][threadIdx.x & 3] = fs;
+  }
   const double dt = r.dt_dev ? *r.dt_dev : r.dt;
   const double lam = dt * r.inv_dx[s];
   const T* fb = static_cast<const T*>(r.fb);
@@ -57,8 +67,8 @@ __global__ void __launch_bounds__(RT) reflux_kernel(const RefluxArgs r) {
     for (int e = threadIdx.x; e < NF * NPEN; e += RT) {
       const int f = e >> 6, p = e & 63, t1 = p & 7, t2 = p >> 3;
       const int q1 = t1 >> 2, q2 = t2 >> 2;
-      const int fs = r.nb[((size_t)s * 6 + face) * 4 + q1 + 2 * q2];
-      if (r.fb_stamp[fs] != r.call_id) continue;
+      const int fs = q_fs[face][q1 + 2 * q2];
+      if (fs < 0) continue;
       const T* fine = fb + ((size_t)fs * 6 + (face ^ 1)) * NF * NPEN + f * NPEN;
       const int b = (2 * (t2 - 4 * q2)) * NX + 2 * (t1 - 4 * q1);
       const T a00 = fine[b], a10 = fine[b + 1], a01 = fine[b + NX], a11 = fine[b + NX + 1];
