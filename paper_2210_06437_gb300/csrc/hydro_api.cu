@@ -77,7 +77,7 @@ struct hydro_handle {
   // coarse-fine flux correction
   int reflux = 1;
   int n_cf = 0;                        // coarse sub-grids with a finer face neighbour
-  int32_t* d_cf = nullptr;             // [n_cf]
+  int32_t* d_cf = nullptr;             // [n_cf][CF_ENTRY]
   void* d_fb = nullptr;                // [n][6][NF][64] exported boundary fluxes (T)
   int32_t* d_fb_stamp = nullptr;       // [n]
   int32_t call_counter = 0;
@@ -226,13 +226,11 @@ int enqueue_stage(hydro_handle* h, const int32_t* ids, int n_items, const double
   if (reflux) {
     RefluxArgs r;
     std::memset(&r, 0, sizeof(r));
-    r.list = h->d_cf;
+    r.cf = h->d_cf;
     r.n_list = h->n_cf;
     r.fb = h->d_fb;
     r.fb_stamp = h->d_fb_stamp;
     r.call_id = a.call_id;
-    r.nb = h->d_nb;
-    r.rel = h->d_rel;
     r.inv_dx = h->d_inv_dx;
     r.dt = dt;
     r.dt_dev = dt_dev;
@@ -326,13 +324,16 @@ int hydro_create(const hydro_grid_desc* d, hydro_handle** out) {
   ok = ok && cudaMalloc(&h->d_ms_tmp, 2 * sizeof(unsigned long long)) == cudaSuccess;
   {
     std::vector<int32_t> cf;
-    for (int s = 0; s < n; ++s)
+    for (int s = 0; s < n; ++s) {
+      bool any = false;
+      for (int f = 0; f < 6; ++f) any = any || d->neighbor_rel[s * 6 + f] == 1;
+      if (!any) continue;
+      cf.push_back(s);
       for (int f = 0; f < 6; ++f)
-        if (d->neighbor_rel[s * 6 + f] == 1) {
-          cf.push_back(s);
-          break;
-        }
-    h->n_cf = (int)cf.size();
+        for (int q = 0; q < 4; ++q)
+          cf.push_back(d->neighbor_rel[s * 6 + f] == 1 ? d->neighbor[(s * 6 + f) * 4 + q] : -1);
+    }
+    h->n_cf = (int)(cf.size() / CF_ENTRY);
     if (h->n_cf > 0) {
       const size_t tsize = d->precision == HYDRO_MIXED ? sizeof(float) : sizeof(double);
       ok = ok && cudaMalloc(&h->d_cf, sizeof(int32_t) * cf.size()) == cudaSuccess;

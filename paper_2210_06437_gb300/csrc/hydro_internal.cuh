@@ -81,14 +81,17 @@ struct StageArgs {
 // Coarse-fine flux correction after a stage (one CTA per coarse sub-grid of
 // `list`): each coarse boundary face flux is replaced by the mean of the four
 // fine fluxes over it, for the finer neighbours advanced by the same call.
+// One record per coarse sub-grid with at least one finer face neighbour: its
+// id, then for each face and quadrant (face * 4 + q) the fine neighbour's id,
+// -1 where the face does not meet finer sub-grids.
+constexpr int CF_ENTRY = 25;
+
 struct RefluxArgs {
-  const int32_t* list;   // coarse sub-grids with at least one finer face neighbour
+  const int32_t* cf;     // [n_list][CF_ENTRY]
   int32_t n_list;
   const void* fb;        // stage flux export (see StageArgs)
   const int32_t* fb_stamp;
   int32_t call_id;
-  const int32_t* nb;     // [n][6][4]
-  const int8_t* rel;     // [n][6]
   const double* inv_dx;
   double dt;
   const double* dt_dev;

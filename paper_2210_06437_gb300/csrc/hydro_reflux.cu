@@ -27,110 +27,192 @@ __device__ __forceinline__ size_t interior_offset(int i, int j, int k) {
   return (size_t)(k + NG) * NP2 + (j + NG) * NP + (i + NG);
 }
 
-// cell (i, j, k) next to face `face` at transverse position (t1, t2)
-__device__ __forceinline__ void face_cell(int face, int t1, int t2, int& i, int& j, int& k) {
-  const int d = face >> 1, c = (face & 1) ? NX - 1 : 0;
-  i = d == 0 ? c : t1;
-  j = d == 1 ? c : (d == 0 ? t1 : t2);
-  k = d == 2 ? c : t2;
-}
-
 __device__ __forceinline__ bool bad_value(double v, bool density) {
   return !(v == v) || v - v != 0.0 || (density && !(v > 0.0));
 }
 
+// The correction of one (field, cell) by one face: mean of the four fine
+// fluxes over the coarse face minus the coarse flux.  Mixed handles return the
+// scaled correction as a float pair (ch, cl) = sgn * lam * (F' - F), exact in
+// the sum of four floats and their difference; FP64 handles return it in dh.
 template <typename T>
-__global__ void __launch_bounds__(RT) reflux_kernel(const RefluxArgs r) {
-  const int s = r.list[blockIdx.x];
-  if (r.fb_stamp[s] != r.call_id) return;  // not advanced by this call
+struct FaceTerm {
+  T a00, a10, a01, a11, own;
+};
+
+template <typename T>
+__device__ __forceinline__ FaceTerm<T> load_term(const T* __restrict__ fb, int s, int fs, int face, int f, int t1,
+                                                 int t2) {
+  const int q1 = t1 >> 2, q2 = t2 >> 2;
+  const T* fine = fb + ((size_t)fs * 6 + (face ^ 1)) * NF * NPEN + f * NPEN;
+  const int b = (2 * (t2 - 4 * q2)) * NX + 2 * (t1 - 4 * q1);
+  FaceTerm<T> t;
+  t.a00 = __ldg(fine + b);
+  t.a10 = __ldg(fine + b + 1);
+  t.a01 = __ldg(fine + b + NX);
+  t.a11 = __ldg(fine + b + NX + 1);
+  t.own = __ldg(fb + ((size_t)s * 6 + face) * NF * NPEN + f * NPEN + t2 * NX + t1);
+  return t;
+}
+
+__device__ __forceinline__ void scaled_delta(const FaceTerm<float>& t, float lh, float ll, float& ch, float& cl) {
+  float h, l, h2, l2;
+  pair_add1(t.a00, 0.0f, t.a10, 0.0f, h, l);
+  pair_add1(t.a01, 0.0f, t.a11, 0.0f, h2, l2);
+  pair_add1(h, l, h2, l2, h, l);
+  h = __fmul_rn(h, 0.25f);
+  l = __fmul_rn(l, 0.25f);
+  pair_add1(h, l, -t.own, 0.0f, h, l);
+  pair_mul1(h, l, lh, ll, ch, cl);
+}
+
+// the face's transverse position (t1, t2) of cell (i, j, k)
+__device__ __forceinline__ void face_pos(int face, int i, int j, int k, int& t1, int& t2) {
+  const int d = face >> 1;
+  t1 = d == 0 ? j : i;
+  t2 = d == 2 ? j : k;
+}
+
+// the faces of the sub-grid that cell (i, j, k) lies on, as a bit mask
+__device__ __forceinline__ unsigned cell_faces(int i, int j, int k) {
+  return (i == 0 ? 1u : 0u) | (i == NX - 1 ? 2u : 0u) | (j == 0 ? 4u : 0u) | (j == NX - 1 ? 8u : 0u) |
+         (k == 0 ? 16u : 0u) | (k == NX - 1 ? 32u : 0u);
+}
+
+// One CTA per coarse sub-grid.  Work item = (face, field, position) over the
+// corrected faces; a cell on several corrected faces (edge, corner) is handled
+// by the item of its lowest face, which applies the faces in ascending order,
+// so the result does not depend on the thread schedule.  The loads of up to
+// IPT items are issued before any of them is written back.
+constexpr int IPT = 3;
+
+template <typename T>
+__global__ void __launch_bounds__(RT, sizeof(T) == 4 ? 4 : 3) reflux_kernel(const RefluxArgs r) {
+  __shared__ int s_cf[CF_ENTRY];      // id, then the fine neighbour of each face quadrant
+  __shared__ int s_ok[CF_ENTRY];      // stamp check of each of them
+  __shared__ double s_lam;            // dt / dx of the sub-grid
   __shared__ unsigned char blocks[64];  // 2x2x2 blocks of the restriction next to a corrected face
-  __shared__ int q_fs[6][4];             // the fine neighbour of each face quadrant, -1 if not advanced
-  if (threadIdx.x < 64) blocks[threadIdx.x] = 0;
-  if (threadIdx.x < 24) {
-    const int face = threadIdx.x >> 2;
-    int fs = -1;
-    if (r.rel[s * 6 + face] == 1) {
-      fs = r.nb[(size_t)s * 24 + threadIdx.x];
-      if (r.fb_stamp[fs] != r.call_id) fs = -1;
-    }
-    q_fs[face][threadIdx.x & 3] = fs;
+  const int tid = threadIdx.x;
+  if (tid < CF_ENTRY) {
+    const int v = __ldg(r.cf + (size_t)blockIdx.x * CF_ENTRY + tid);
+    s_cf[tid] = v;
+    s_ok[tid] = v >= 0 && __ldg(r.fb_stamp + v) == r.call_id;
+  } else if (tid == 32) {
+    const double dt = r.dt_dev ? *r.dt_dev : r.dt;
+    s_lam = dt * __ldg(r.inv_dx + __ldg(r.cf + (size_t)blockIdx.x * CF_ENTRY));
   }
-  const double dt = r.dt_dev ? *r.dt_dev : r.dt;
-  const double lam = dt * r.inv_dx[s];
-  const T* fb = static_cast<const T*>(r.fb);
-  int bad = 0;
+  if (tid >= 64 && tid < 128) blocks[tid - 64] = 0;
   __syncthreads();
-  for (int face = 0; face < 6; ++face) {
-    if (r.rel[s * 6 + face] != 1) continue;
-    const int sgn = (face & 1) ? -1 : 1;
-    const T* own = fb + ((size_t)s * 6 + face) * NF * NPEN;
-    for (int e = threadIdx.x; e < NF * NPEN; e += RT) {
-      const int f = e >> 6, p = e & 63, t1 = p & 7, t2 = p >> 3;
-      const int q1 = t1 >> 2, q2 = t2 >> 2;
-      const int fs = q_fs[face][q1 + 2 * q2];
-      if (fs < 0) continue;
-      const T* fine = fb + ((size_t)fs * 6 + (face ^ 1)) * NF * NPEN + f * NPEN;
-      const int b = (2 * (t2 - 4 * q2)) * NX + 2 * (t1 - 4 * q1);
-      const T a00 = fine[b], a10 = fine[b + 1], a01 = fine[b + NX], a11 = fine[b + NX + 1];
-      int i, j, k;
-      face_cell(face, t1, t2, i, j, k);
-      const int c = (k * NX + j) * NX + i;
+  if (!s_ok[0]) return;  // this sub-grid was not advanced by this call
+  const int s = s_cf[0];
+  unsigned mask = 0;  // faces with at least one advanced fine quadrant
+#pragma unroll
+  for (int g = 0; g < 6; ++g)
+    mask |= (s_ok[1 + 4 * g] | s_ok[2 + 4 * g] | s_ok[3 + 4 * g] | s_ok[4 + 4 * g]) ? 1u << g : 0u;
+  const double lam = s_lam;
+  const T* __restrict__ fb = static_cast<const T*>(r.fb);
+  const float lh = (float)lam, ll = (float)(lam - (double)lh);
+  const int nface = __popc(mask);
+  const int n_items = nface * NF * NPEN;
+  int bad = 0;
+  for (int base = 0; base < n_items; base += IPT * RT) {
+    FaceTerm<T> term[IPT];
+    double val[IPT];
+    float s0[IPT];
+    int info[IPT];  // cell | field << 9 | lowest face << 13, -1 for no work
+    // decode the items and issue their loads
+#pragma unroll
+    for (int u = 0; u < IPT; ++u) {
+      const int e = base + u * RT + tid;
+      info[u] = -1;
+      if (e >= n_items) continue;
+      const int rank = e / (NF * NPEN), rem = e - rank * (NF * NPEN);
+      int face = __ffs(mask) - 1;
+      for (int q = 0; q < rank; ++q) face = __ffs(mask & ~((2u << face) - 1u)) - 1;
+      const int f = rem >> 6, p = rem & 63, t1 = p & 7, t2 = p >> 3;
+      const int d = face >> 1, c = (face & 1) ? NX - 1 : 0;
+      const int i = d == 0 ? c : t1, j = d == 1 ? c : (d == 0 ? t1 : t2), k = d == 2 ? c : t2;
+      const unsigned cf = cell_faces(i, j, k) & mask;
+      if ((int)(__ffs(cf) - 1) != face) continue;  // handled by the item of a lower face
+      const int fs = s_cf[1 + face * 4 + (t1 >> 2) + 2 * (t2 >> 2)];
+      if (!s_ok[1 + face * 4 + (t1 >> 2) + 2 * (t2 >> 2)]) {
+        // this quadrant's fine neighbour was not advanced; a later face of the
+        // cell may still apply (the apply loop re-checks each face)
+        if ((cf & ~(1u << face)) == 0) continue;
+      }
+      info[u] = ((k * NX + j) * NX + i) | (f << 9) | (face << 13);
+      if (s_ok[1 + face * 4 + (t1 >> 2) + 2 * (t2 >> 2)]) term[u] = load_term(fb, s, fs, face, f, t1, t2);
       const size_t o = ((size_t)s * NF + f) * NP3 + interior_offset(i, j, k);
-      if (f == 0) blocks[((k >> 1) * 4 + (j >> 1)) * 4 + (i >> 1)] = 1;
-      float x = 0.0f;  // the cell's new shadow value (mixed)
-      if constexpr (sizeof(T) == 8) {
-        const double delta = (((double)a00 + (double)a10) + ((double)a01 + (double)a11)) * 0.25 - (double)own[e];
-        const double v = fma(r.beta * lam * sgn, delta, r.U[o]);
-        r.U[o] = v;
-        bad |= bad_value(v, f == F_RHO);
+      if (sizeof(T) == 4 && (r.mode == 1 || r.mode == 2)) {
+        val[u] = r.D[o];
+        s0[u] = __ldg(r.S0 + ((size_t)s * NF + f) * SHADOW_FIELD + (k * NX + j) * NX + i);
       } else {
-        // delta = mean - own as a float pair (the sum of four floats exactly)
-        float h, l, h2, l2;
-        pair_add1((float)a00, 0.0f, (float)a10, 0.0f, h, l);
-        pair_add1((float)a01, 0.0f, (float)a11, 0.0f, h2, l2);
-        pair_add1(h, l, h2, l2, h, l);
-        h = __fmul_rn(h, 0.25f);
-        l = __fmul_rn(l, 0.25f);
-        pair_add1(h, l, -(float)own[e], 0.0f, h, l);
-        // times lam (split as for the stage: lam = lh + ll) and the sign
-        const float lh = (float)lam, ll = (float)(lam - (double)lh);
-        float ch, cl;
-        pair_mul1(h, l, sgn * lh, sgn * ll, ch, cl);
-        if (r.mode == 0) {
-          const double w = r.beta * 1.0;
-          const double v = fma(w, f32_to_f64(ch), fma(w, f32_to_f64(cl), r.U[o]));
-          r.U[o] = v;
-          bad |= bad_value(v, f == F_RHO);
-          x = f64_to_f32(v);
-        } else if (r.mode == 3) {
-          constexpr float th = (float)(2.0 / 3.0), tl = (float)(2.0 / 3.0 - (double)(float)(2.0 / 3.0));
-          pair_mul1(ch, cl, th, tl, ch, cl);
-          const double v = __dadd_rn(__dadd_rn(r.U[o], f32_to_f64(ch)), f32_to_f64(cl));
-          r.U[o] = v;
-          bad |= bad_value(v, f == F_RHO);
-          x = f64_to_f32(v);
-        } else {
-          if (r.mode == 2) {
-            ch = __fmul_rn(ch, 0.25f);
-            cl = __fmul_rn(cl, 0.25f);
-          }
-          const double d = r.D[o];
-          float dh = __int_as_float(__double2hiint(d)), dl = __int_as_float(__double2loint(d));
-          pair_add1(dh, dl, ch, cl, dh, dl);
-          r.D[o] = __hiloint2double(__float_as_int(dh), __float_as_int(dl));
-          x = __fadd_rn(r.S0[((size_t)s * NF + f) * SHADOW_FIELD + c], dh);
-          if (!(x - x == 0.0f) || (f == F_RHO && !(x > 0.0f))) bad = 1;
-        }
-        // a cell on two or three corrected faces is rewritten by each in turn
-        if (r.Sout) r.Sout[((size_t)s * NF + f) * SHADOW_FIELD + c] = x;
+        val[u] = r.U[o];
       }
     }
-    __syncthreads();
+    // apply every corrected face of each item's cell in ascending order
+#pragma unroll
+    for (int u = 0; u < IPT; ++u) {
+      if (info[u] < 0) continue;
+      const int c = info[u] & 511, f = (info[u] >> 9) & 15, face0 = info[u] >> 13;
+      const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
+      const unsigned cf = cell_faces(i, j, k) & mask;
+      double v = val[u];
+      float dh = 0.0f, dl = 0.0f;
+      if (sizeof(T) == 4 && (r.mode == 1 || r.mode == 2)) {
+        dh = __int_as_float(__double2hiint(v));
+        dl = __int_as_float(__double2loint(v));
+      }
+      for (unsigned rest = cf; rest; rest &= rest - 1) {
+        const int face = __ffs(rest) - 1;
+        int t1, t2;
+        face_pos(face, i, j, k, t1, t2);
+        const int qi = 1 + face * 4 + (t1 >> 2) + 2 * (t2 >> 2);
+        if (!s_ok[qi]) continue;
+        const FaceTerm<T> t = face == face0 ? term[u] : load_term(fb, s, s_cf[qi], face, f, t1, t2);
+        const int sgn = (face & 1) ? -1 : 1;
+        if constexpr (sizeof(T) == 8) {
+          const double delta = (((double)t.a00 + (double)t.a10) + ((double)t.a01 + (double)t.a11)) * 0.25 - (double)t.own;
+          v = fma(r.beta * lam * sgn, delta, v);
+        } else {
+          float ch, cl;
+          scaled_delta(t, sgn * lh, sgn * ll, ch, cl);
+          if (r.mode == 0) {
+            const double w = r.beta * 1.0;
+            v = fma(w, f32_to_f64(ch), fma(w, f32_to_f64(cl), v));
+          } else if (r.mode == 3) {
+            constexpr float th = (float)(2.0 / 3.0), tl = (float)(2.0 / 3.0 - (double)(float)(2.0 / 3.0));
+            pair_mul1(ch, cl, th, tl, ch, cl);
+            v = __dadd_rn(__dadd_rn(v, f32_to_f64(ch)), f32_to_f64(cl));
+          } else {
+            if (r.mode == 2) {
+              ch = __fmul_rn(ch, 0.25f);
+              cl = __fmul_rn(cl, 0.25f);
+            }
+            pair_add1(dh, dl, ch, cl, dh, dl);
+          }
+        }
+      }
+      const size_t o = ((size_t)s * NF + f) * NP3 + interior_offset(i, j, k);
+      float x;  // the cell's new shadow value (mixed)
+      if (sizeof(T) == 4 && (r.mode == 1 || r.mode == 2)) {
+        r.D[o] = __hiloint2double(__float_as_int(dh), __float_as_int(dl));
+        x = __fadd_rn(s0[u], dh);
+        if (!(x - x == 0.0f) || (f == F_RHO && !(x > 0.0f))) bad = 1;
+      } else {
+        r.U[o] = v;
+        bad |= bad_value(v, f == F_RHO);
+        x = sizeof(T) == 4 ? f64_to_f32(v) : 0.0f;
+      }
+      if (sizeof(T) == 4 && r.Sout) r.Sout[((size_t)s * NF + f) * SHADOW_FIELD + c] = x;
+      if (f == 0) blocks[((k >> 1) * 4 + (j >> 1)) * 4 + (i >> 1)] = 1;
+    }
   }
+  __syncthreads();
   // refresh the restriction blocks next to corrected faces
   if constexpr (sizeof(T) == 4) {
     if (r.Sout) {
-      for (int e = threadIdx.x; e < NF * 64; e += RT) {
+      for (int e = tid; e < NF * 64; e += RT) {
         const int f = e >> 6, cc = e & 63;
         if (!blocks[cc]) continue;
         const int I = cc & 3, J = (cc >> 2) & 3, K = cc >> 4;
