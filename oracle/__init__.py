@@ -63,6 +63,8 @@ def lib():
         L.oracle_fill_ghosts.argtypes = [ctypes.POINTER(_Grid), ctypes.c_void_p]
         L.oracle_totals.argtypes = [ctypes.POINTER(_Grid), ctypes.c_void_p, dp]
         L.oracle_diagnostics.argtypes = [ctypes.POINTER(_Grid), ctypes.c_void_p, ctypes.c_void_p, dp]
+        L.oracle_tau_resync.argtypes = [ctypes.POINTER(_Grid), ctypes.c_void_p]
+        L.oracle_tau_resync.restype = ctypes.c_long
         _lib = L
     return _lib
 
@@ -142,9 +144,10 @@ class Oracle:
                                 1 if batch_all else 0)
         return Uout, ms, st
 
-    def rk3_step(self, U: np.ndarray, dt: float, nthreads: int = 0):
+    def rk3_step(self, U: np.ndarray, dt: float, nthreads: int = 0, tau_resync: bool = False):
         """One SSP-RK3 step from U (ghosts filled); returns (U_new with ghosts filled,
-        max_speed of the first stage, worst status)."""
+        max_speed of the first stage, worst status).  tau_resync: reset the
+        entropy tracer from the internal energy at the end of the step."""
         st_all = 0
         U1, ms, st = self.stage(U, dt, nthreads=nthreads)
         st_all = min(st_all, st)
@@ -154,8 +157,16 @@ class Oracle:
         self.fill_ghosts(U2)
         U3, _, st = self.stage(U2, dt, U0=U, beta=RK3_BETA[2], nthreads=nthreads)
         st_all = min(st_all, st)
+        if tau_resync:
+            self.tau_resync(U3)
         self.fill_ghosts(U3)
         return U3, ms, st_all
+
+    def tau_resync(self, U: np.ndarray) -> int:
+        """Dual-energy reset tau = e_i^(1/gamma) where e_i >= eta E (interior
+        cells, in place); returns the number of cells reset."""
+        self._check(U)
+        return int(lib().oracle_tau_resync(ctypes.byref(self._g), U.ctypes.data))
 
     def totals(self, U: np.ndarray) -> np.ndarray:
         self._check(U)

@@ -470,3 +470,39 @@ void oracle_diagnostics(const oracle_grid *g, const double *U, const double *ori
     for (int c = 0; c < 3; ++c) out[5 + 4 * star + c] = m != 0.0 ? T[5 + 4 * star + c] / m : 0.0;
   }
 }
+
+/* ------------------------------------------------------------------------- */
+/* Dual-energy resynchronisation of the entropy tracer (the paper names the   */
+/* dual-energy formalism of its solver but prints no formula; reading R5').   */
+/* Per interior cell, with the same kinetic and internal energies as the face */
+/* EOS:                                                                       */
+/*   e_k = (sx^2 + sy^2 + sz^2) / 2 rho,   e_i = E - e_k;                      */
+/* where the switch takes e_i from the total energy (eta > 0, e_i > 0 and     */
+/* e_i >= eta E: the complement of the face EOS test e_i < eta E), the tracer */
+/* is reset to the value that reproduces it, tau = e_i^(1/gamma); every other */
+/* cell and field is left as it is.  Returns the number of cells reset.       */
+/* ------------------------------------------------------------------------- */
+
+long oracle_tau_resync(const oracle_grid *g, double *U) {
+  const double eta = g->de_switch;
+  if (!(eta > 0.0)) return 0;
+  const double inv_gamma = 1.0 / g->gamma;
+  long reset = 0;
+  for (int s = 0; s < g->n; ++s)
+    for (int k = 0; k < NX; ++k)
+      for (int j = 0; j < NX; ++j)
+        for (int i = 0; i < NX; ++i) {
+          const double rho = U[at(s, F_RHO, k + NG, j + NG, i + NG)];
+          const double sx = U[at(s, F_SX, k + NG, j + NG, i + NG)];
+          const double sy = U[at(s, F_SX + 1, k + NG, j + NG, i + NG)];
+          const double sz = U[at(s, F_SX + 2, k + NG, j + NG, i + NG)];
+          const double E = U[at(s, F_EGAS, k + NG, j + NG, i + NG)];
+          const double ek = 0.5 * (sx * sx + sy * sy + sz * sz) / rho;
+          const double ei = E - ek;
+          if (ei > 0.0 && ei >= eta * E) {
+            U[at(s, F_TAU, k + NG, j + NG, i + NG)] = pow(ei, inv_gamma);
+            ++reset;
+          }
+        }
+  return reset;
+}

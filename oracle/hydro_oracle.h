@@ -20,7 +20,8 @@
  *   ghosts: fill of the 6 face ghost slabs (3 layers) from neighbours: copy,
  *           coarse-to-fine injection, fine-to-coarse 2x2x2 mean, outflow.
  *   totals: Neumaier-compensated grid totals of the 11 fields;
- *   diagnostics: total mass, angular momentum, centre of mass of each star.
+ *   diagnostics: total mass, angular momentum, centre of mass of each star;
+ *   resync: dual-energy reset of the entropy tracer tau from the internal energy.
  *
  * Layout: U[s][f][k][j][i], 14^3 padded cells per field, interior 3..10.
  * Compile with -O2 -ffp-contract=off (no fused multiply-add, no fast-math).
@@ -88,6 +89,11 @@ void oracle_totals(const oracle_grid *g, const double *U, double *totals);
  * mass and centre of mass of star 1 (scalar field 6) and star 2 (field 7).
  * origin[n][3] is the lower corner of each sub-grid's interior. */
 void oracle_diagnostics(const oracle_grid *g, const double *U, const double *origin, double *out);
+
+/* Dual-energy resynchronisation of the entropy tracer: tau = e_i^(1/gamma) in
+ * every interior cell where e_i = E - |s|^2 / 2 rho > 0 and e_i >= eta E
+ * (eta = de_switch; nothing when eta <= 0).  Returns the number of cells reset. */
+long oracle_tau_resync(const oracle_grid *g, double *U);
 
 #ifdef __cplusplus
 }
