@@ -44,6 +44,7 @@ BYTES_PER_CELL_RK3_STAGE = (374.0 + 2 * 462.0) / 3.0
 FLOPS_PER_CELL_STAGE = 2200.0    # algorithmic operation count per cell-update of one stage
 GHOST_BYTES_PER_CELL = 396.0     # ghost fill: read + write 1152 face-slab cells per 512 interior cells
 SHADOW_BYTES_PER_CELL = 137.5    # FP32 shadow: read 88 B of FP64 interior, write 44 B + 5.5 B of restriction
+TAU_RESYNC_BYTES_PER_CELL = 56.0  # tracer reset: read rho, s, E, tau (48 B), write tau (8 B)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 2 FP64 FMA/clk/SM at the 2070 MHz maximum clock
 # DRAM bytes (read + write) per cell-update of the mixed stage kernel from one ncu capture
 # (average of the three RK3 stage launches, profiles/stage_mixed_binary4k.md), valid only for
@@ -326,10 +327,14 @@ def main():
         t_stage = (t_run - t_shadow) / (3 * args.steps)
         t_ghost = timed(lambda: g.fill_ghosts(s1))
         t_tot = timed(lambda: g.totals(U, out=tot))
+        # the optional dual-energy tracer reset, standalone (not part of the
+        # timed step); it leaves U's tracer reset, and U is not read again
+        t_resync = timed(lambda: g.tau_resync(U)) if prec == "mixed" else 0.0
         g.sync()
         g.close()
         return dict(t_step=t_step, clocks=clocks, launches=launches, t_stage=t_stage, t_single=t_single,
-                    t_ghost=t_ghost, t_tot=t_tot, t_shadow=t_shadow, totals=tot.cpu().numpy(), tuned=tuned)
+                    t_ghost=t_ghost, t_tot=t_tot, t_shadow=t_shadow, t_resync=t_resync, totals=tot.cpu().numpy(),
+                    tuned=tuned)
 
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     smi_index = vis.split(",")[local] if vis and len(vis.split(",")) > local else str(local)
@@ -444,8 +449,10 @@ def main():
         "totals_ms": r["t_tot"] * 1e3, "shadow_gbs": SHADOW_BYTES_PER_CELL * cells / r["t_shadow"] / 1e9,
         "ghost_fill_gbs": GHOST_BYTES_PER_CELL * cells / r["t_ghost"] / 1e9,
         "stage_share_of_step": 3 * t_st / r["t_step"], "totals_share_of_step": r["t_tot"] / r["t_step"],
-        "note": "the stage kernel gathers halos from neighbour interiors; the ghost-fill kernel is not part of "
-                "the step (timed standalone for reference)"}
+        "tau_resync_ms": r["t_resync"] * 1e3,
+        "tau_resync_gbs": TAU_RESYNC_BYTES_PER_CELL * cells / r["t_resync"] / 1e9 if r["t_resync"] > 0 else None,
+        "note": "the stage kernel gathers halos from neighbour interiors; the ghost-fill kernel and the optional "
+                "dual-energy tracer reset are not part of the step (timed standalone for reference)"}
     line = {"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["t_step"] * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",

@@ -261,6 +261,23 @@ int hydro_totals(hydro_handle *h, const double *U, double *d_totals, void *strea
  *   corner of each sub-grid's interior; d_out DEVICE double[12]. */
 int hydro_diagnostics(hydro_handle *h, const double *U, const double *d_origin, double *d_out, void *stream);
 
+/* Dual-energy reset of the entropy tracer (the solver's dual-energy formalism;
+ * the paper prints no formula).  In every interior cell where the internal
+ * energy e_i = E - (sx^2 + sy^2 + sz^2) / (2 rho) is positive and at least
+ * eta E (eta = the handle's de_switch; the complement of the face EOS test
+ * that takes e_i = tau^gamma), set tau = e_i^(1/gamma); every other cell and
+ * field is unchanged, and nothing happens when de_switch <= 0.  e_k and e_i
+ * are formed in FP64 on both handles; the power is FP64 on an FP64 handle and
+ * FP32 (powf, about 1 ulp) on a mixed one.
+ *   U  DEVICE padded state (interior tau overwritten in place; 16-byte aligned);
+ *   S  optional DEVICE FP32 shadow of U (layout of hydro_shadow, mixed handles
+ *      only, else HYDRO_ERR_INVALID): its tau field and tau restriction are
+ *      rewritten from the new state, as hydro_shadow would write them.
+ * With HYDRO_PARAM_TAU_RESYNC set, the RK3 entry points apply the same reset
+ * at the end of every step (before the totals of hydro_rk3_run_cfl).
+ * Returns HYDRO_OK, HYDRO_ERR_INVALID or HYDRO_ERR_CUDA. */
+int hydro_tau_resync(hydro_handle *h, double *U, float *S, void *stream);
+
 /* Allocation-free variant of hydro_totals for callers that cannot allocate
  * device memory (no cudaMalloc available to them: an allocator callback, a
  * framework that owns all device memory, a process with its memory reserved up
@@ -299,7 +316,8 @@ int hydro_set_param(hydro_handle *h, int32_t key, int32_t value);
 typedef enum {
   HYDRO_PARAM_STAGE_CTAS_PER_SM = 0, /* persistent CTAs per SM for the stage kernel, 1..8 (0 = auto) */
   HYDRO_PARAM_GHOST_THREADS = 1,     /* threads per CTA of the ghost-fill kernel, 64..1024 */
-  HYDRO_PARAM_REFLUX = 2             /* coarse-fine flux correction: 1 (default) or 0 */
+  HYDRO_PARAM_REFLUX = 2,            /* coarse-fine flux correction: 1 (default) or 0 */
+  HYDRO_PARAM_TAU_RESYNC = 3         /* dual-energy tracer reset after every RK3 step: 0 (default) or 1 */
 } hydro_param;
 
 /* Release the handle and its device scratch (waits for its work first). */

@@ -75,6 +75,7 @@ struct hydro_handle {
   unsigned long long* d_ms_tmp = nullptr;  // [2] speeds of RK stages 2 and 3
   float* d_shadow[3] = {nullptr, nullptr, nullptr};  // mixed precision: FP32 shadows [n][NF][576]
   // coarse-fine flux correction
+  int tau_resync = 0;                  // dual-energy tracer reset after every RK3 step
   int reflux = 1;
   int n_cf = 0;                        // coarse sub-grids with a finer face neighbour
   int32_t* d_cf = nullptr;             // [n_cf][CF_ENTRY]
@@ -245,6 +246,14 @@ int enqueue_stage(hydro_handle* h, const int32_t* ids, int n_items, const double
     if (e != cudaSuccess) return cuda_fail(h, e, "flux correction kernel launch");
     h->launches += 1;
   }
+  return HYDRO_OK;
+}
+
+int enqueue_tau_resync(hydro_handle* h, double* U, float* S, cudaStream_t st) {
+  if (!(h->eta > 0.0)) return HYDRO_OK;
+  cudaError_t e = launch_tau_resync(U, S, h->n, h->gamma, h->eta, h->precision == HYDRO_MIXED, st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "tau resync kernel launch");
+  h->launches += 1;
   return HYDRO_OK;
 }
 
@@ -502,12 +511,14 @@ int enqueue_rk3_stages(hydro_handle* h, const int32_t* ids, int ni, double* U, d
     if (!rc)
       rc = enqueue_stage(h, ids, ni, U, C, nullptr, 1.0, 0.0, h->d_dt, U, write_next ? A : nullptr, h->d_ms_tmp, 2,
                          cs, 3, s2, nullptr, A);
+    if (!rc && h->tau_resync) rc = enqueue_tau_resync(h, U, write_next ? A : nullptr, cs);
     return rc;
   }
   rc = enqueue_stage(h, ids, ni, U, nullptr, nullptr, 1.0, 0.0, h->d_dt, s1, nullptr, ms, 0, cs);
   if (!rc) rc = enqueue_stage(h, ids, ni, s1, nullptr, U, 0.25, 0.0, h->d_dt, s2, nullptr, h->d_ms_tmp, 1, cs);
   if (!rc)
     rc = enqueue_stage(h, ids, ni, s2, nullptr, U, 2.0 / 3.0, 0.0, h->d_dt, U, nullptr, h->d_ms_tmp, 2, cs);
+  if (!rc && h->tau_resync) rc = enqueue_tau_resync(h, U, nullptr, cs);
   return rc;
 }
 
@@ -683,6 +694,15 @@ int hydro_diagnostics(hydro_handle* h, const double* U, const double* d_origin, 
   return HYDRO_OK;
 }
 
+int hydro_tau_resync(hydro_handle* h, double* U, float* S, void* stream) {
+  if (!h) return HYDRO_ERR_INVALID;
+  if (!U || !aligned(U, 16) || (S && !aligned(S, 16))) return fail(h, HYDRO_ERR_INVALID, "NULL or misaligned pointer");
+  if (S && h->precision != HYDRO_MIXED) return fail(h, HYDRO_ERR_INVALID, "a shadow needs a mixed-precision handle");
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  return enqueue_tau_resync(h, U, S, st);
+}
+
 int hydro_sync(hydro_handle* h) {
   if (!h) return HYDRO_ERR_INVALID;
   CUDA_TRY(h, cudaStreamSynchronize(h->last_stream));
@@ -710,6 +730,13 @@ int hydro_set_param(hydro_handle* h, int32_t key, int32_t value) {
   if (key == HYDRO_PARAM_REFLUX) {
     if (value != 0 && value != 1) return fail(h, HYDRO_ERR_INVALID, "reflux must be 0 or 1");
     h->reflux = value;
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+    return HYDRO_OK;
+  }
+  if (key == HYDRO_PARAM_TAU_RESYNC) {
+    if (value != 0 && value != 1) return fail(h, HYDRO_ERR_INVALID, "tau resync must be 0 or 1");
+    h->tau_resync = value;
     for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
     h->graphs.clear();
     return HYDRO_OK;

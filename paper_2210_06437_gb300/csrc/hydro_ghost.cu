@@ -148,7 +148,64 @@ __global__ void __launch_bounds__(256) shadow_kernel(const double* __restrict__ 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Dual-energy reset of the entropy tracer (the dual-energy formalism of the
+// paper's solver; the paper prints no formula): in every interior cell where
+// the internal energy e_i = E - |s|^2 / 2 rho is positive and at least eta E
+// (the complement of the face EOS test e_i < eta E), tau = e_i^(1/gamma).
+// e_k and e_i are formed in FP64 as the face EOS forms them; the power is FP64
+// for FP64 handles and FP32 (powf, about 1 ulp) for mixed ones.  One CTA per
+// sub-grid; with a shadow S (mixed), its tau field and tau restriction are
+// rewritten exactly as the shadow kernel would write them from the new state.
+// ---------------------------------------------------------------------------
+template <bool MIXED>
+__global__ void __launch_bounds__(256) tau_resync_kernel(double* __restrict__ U, float* __restrict__ S,
+                                                         double inv_gamma, double eta) {
+  __shared__ float st[CELLS];  // RN32 of the new tracer (mixed shadow)
+  double* u = U + (size_t)blockIdx.x * NF * NP3;
+  for (int c = threadIdx.x; c < CELLS; c += blockDim.x) {
+    const size_t o = (size_t)((c >> 6) + NG) * NP2 + (((c >> 3) & 7) + NG) * NP + ((c & 7) + NG);
+    const double rho = u[o], sx = u[NP3 + o], sy = u[2 * NP3 + o], sz = u[3 * NP3 + o], E = u[4 * NP3 + o];
+    double tau = u[(size_t)F_TAU * NP3 + o];
+    const double s2 = __dadd_rn(__dadd_rn(__dmul_rn(sx, sx), __dmul_rn(sy, sy)), __dmul_rn(sz, sz));
+    const double ek = __ddiv_rn(__dmul_rn(0.5, s2), rho);
+    const double ei = __dsub_rn(E, ek);
+    if (ei > 0.0 && ei >= __dmul_rn(eta, E)) {
+      if constexpr (MIXED)
+        tau = (double)powf((float)ei, (float)inv_gamma);
+      else
+        tau = pow(ei, inv_gamma);
+      u[(size_t)F_TAU * NP3 + o] = tau;
+    }
+    if constexpr (MIXED) st[c] = shadow_round(tau);
+  }
+  if (!MIXED || !S) return;  // uniform over the block
+  __syncthreads();
+  float* sf = S + ((size_t)blockIdx.x * NF + F_TAU) * SHADOW_FIELD;
+  for (int c = threadIdx.x; c < CELLS; c += blockDim.x) sf[c] = st[c];
+  if (threadIdx.x < CELLS / 8) {
+    const int cc = threadIdx.x, I = cc & 3, J = (cc >> 2) & 3, K = cc >> 4;
+    const float* b = st + (2 * K) * 64 + (2 * J) * 8 + 2 * I;
+    float h[2];  // pairwise, as the shadow kernel: in i, then j, then k
+#pragma unroll
+    for (int dk = 0; dk < 2; ++dk) {
+      const float* bk = b + dk * 64;
+      h[dk] = __fadd_rn(__fadd_rn(bk[0], bk[1]), __fadd_rn(bk[8], bk[9]));
+    }
+    sf[SHADOW_COARSE + cc] = __fmul_rn(__fadd_rn(h[0], h[1]), 0.125f);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_tau_resync(double* U, float* S, int n, double gamma, double eta, bool mixed, cudaStream_t st) {
+  if (n < 1 || !(eta > 0.0)) return cudaSuccess;
+  if (mixed)
+    tau_resync_kernel<true><<<n, 256, 0, st>>>(U, S, 1.0 / gamma, eta);
+  else
+    tau_resync_kernel<false><<<n, 256, 0, st>>>(U, nullptr, 1.0 / gamma, eta);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_shadow(const double* U, float* S, int n, cudaStream_t st) {
   int dev = 0, sms = 0;

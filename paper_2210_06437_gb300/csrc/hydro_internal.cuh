@@ -124,6 +124,9 @@ constexpr int SHADOW_FIELD = CELLS + CELLS / 8;  // 576 floats per field
 
 // launchers (defined in the .cu files)
 cudaError_t launch_shadow(const double* U, float* S, int n, cudaStream_t st);
+// Dual-energy tracer reset of every sub-grid of U (and the tau field of its
+// shadow S when mixed and S is not null); nothing when eta <= 0.
+cudaError_t launch_tau_resync(double* U, float* S, int n, double gamma, double eta, bool mixed, cudaStream_t st);
 cudaError_t launch_reflux_fp64(const RefluxArgs& r, cudaStream_t st);
 cudaError_t launch_reflux_mixed(const RefluxArgs& r, cudaStream_t st);
 cudaError_t launch_pack(const double* U, double* P, int n, cudaStream_t st);

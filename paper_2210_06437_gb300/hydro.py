@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libhydro.so")
 NF, NP, NX, NG = 11, 14, 8, 3
 HYDRO_FP64, HYDRO_MIXED = 0, 1
 HYDRO_FLUX_KNP, HYDRO_FLUX_KT = 0, 1
-PARAM_STAGE_CTAS_PER_SM, PARAM_GHOST_THREADS, PARAM_REFLUX = 0, 1, 2
+PARAM_STAGE_CTAS_PER_SM, PARAM_GHOST_THREADS, PARAM_REFLUX, PARAM_TAU_RESYNC = 0, 1, 2, 3
 RK3_BETA = (1.0, 0.25, 2.0 / 3.0)
 
 STATUS = {0: "HYDRO_OK", -1: "HYDRO_ERR_INVALID", -2: "HYDRO_ERR_CUDA", -3: "HYDRO_ERR_NOMEM",
@@ -28,7 +28,7 @@ STATUS = {0: "HYDRO_OK", -1: "HYDRO_ERR_INVALID", -2: "HYDRO_ERR_CUDA", -3: "HYD
 # every symbol include/hydro.h declares
 EXPORTS = ("hydro_create", "hydro_step", "hydro_shadow", "hydro_step_shadowed", "hydro_fill_ghosts", "hydro_rk3_step",
            "hydro_rk3_step_cfl", "hydro_rk3_run_cfl", "hydro_rk3_run_prepare", "hydro_totals", "hydro_diagnostics",
-           "hydro_totals_noalloc", "hydro_pack_interiors", "hydro_unpack_interiors", "hydro_sync",
+           "hydro_tau_resync", "hydro_totals_noalloc", "hydro_pack_interiors", "hydro_unpack_interiors", "hydro_sync",
            "hydro_last_error", "hydro_launch_count", "hydro_set_param", "hydro_destroy")
 SHADOW_FIELD = NX * NX * NX + (NX // 2) ** 3   # interior, then its 4^3 restriction
 TOTALS_NOALLOC_MAX_SUBGRIDS = 65536
@@ -79,6 +79,7 @@ def load_library(path: str = LIB_PATH):
     L.hydro_totals.argtypes = [vp, vp, vp, vp]
     L.hydro_diagnostics.argtypes = [vp, vp, vp, vp, vp]
     L.hydro_totals_noalloc.argtypes = [vp, vp, i32, vp, vp]
+    L.hydro_tau_resync.argtypes = [vp, vp, vp, vp]
     L.hydro_sync.argtypes = [vp]
     L.hydro_last_error.argtypes = [vp]
     L.hydro_last_error.restype = ctypes.c_char_p
@@ -329,6 +330,15 @@ class HydroGrid:
         self._check(self.lib.hydro_diagnostics(self.h, _ptr(U), _ptr(self._origin_dev), _ptr(out),
                                                _stream_ptr(stream)))
         return out
+
+    def tau_resync(self, U, S=None, stream=None):
+        """Dual-energy reset of the entropy tracer in place (hydro_tau_resync);
+        S (mixed handles) is a shadow of U whose tau field is refreshed."""
+        self._state(U)
+        if S is not None:
+            self._shadow_buf(S)
+        self._check(self.lib.hydro_tau_resync(self.h, _ptr(U), _ptr(S), _stream_ptr(stream)))
+        return U
 
     def sync(self):
         """Wait and return the device status; raises HydroError on a device-side error."""

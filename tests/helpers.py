@@ -1,6 +1,7 @@
 """Shared test helpers: global<->sub-grid layout moves and a time-step driver.
 
-Only data movement and the lagged-CFL driver live here; no solver arithmetic.
+Only data movement, seeded input recipes and the lagged-CFL driver live here;
+no solver arithmetic.
 """
 import math
 
@@ -43,6 +44,12 @@ def prim_to_global(rho, vx, vy, vz, p, X=None, gamma=W.GAMMA):
 
 def random_smooth_global(shape, seed, amp=0.2, vamp=0.3):
     """Random smooth periodic primitive state on a global grid of shape (Z, Y, X)."""
+    rho, vx, vy, vz, p, Xs = random_smooth_primitives(shape, seed, amp, vamp)
+    return prim_to_global(rho, vx, vy, vz, p, Xs)
+
+
+def random_smooth_primitives(shape, seed, amp=0.2, vamp=0.3):
+    """(rho, vx, vy, vz, p, [X1..X5]) of random_smooth_global."""
     rng = np.random.Generator(np.random.PCG64(seed))
     Z, Y, X = shape
     z, y, x = np.meshgrid(np.arange(Z) / Z, np.arange(Y) / Y, np.arange(X) / X, indexing="ij")
@@ -56,7 +63,7 @@ def random_smooth_global(shape, seed, amp=0.2, vamp=0.3):
     p = 1.0 + amp * smooth()
     v = [vamp * smooth() for _ in range(3)]
     Xs = [0.5 + 0.3 * smooth() / 2.5 for _ in range(5)]
-    return prim_to_global(rho, v[0], v[1], v[2], p, Xs)
+    return rho, v[0], v[1], v[2], p, Xs
 
 
 def advance(o, U, t_end, cfl, max_steps=100000):
@@ -151,3 +158,21 @@ def cone_grid(grid, sample, rings):
                octant=grid.octant[gids].copy(), neighbor=loc, neighbor_rel=rel, periodic=False, gamma=grid.gamma,
                de_switch=grid.de_switch)
     return g, gids, [lut[r] for r in rings_g]
+
+
+def resync_case(seed=11):
+    """Periodic 2x2x2 sub-grids (16^3 cells): a random smooth state whose tracer
+    is scrambled (no longer matching the internal energy), with a slab of cold
+    fast cells (x < 4: speed 3, pressure 1e-6, internal energy about 1e-6 of
+    the total, below the dual-energy switch).  Returns (grid, U, cold mask
+    [8, 14, 14, 14] of the padded cells)."""
+    rho, vx, vy, vz, p, Xs = random_smooth_primitives((16, 16, 16), seed)
+    cold = np.zeros(rho.shape, bool)
+    cold[:, :, :4] = True
+    vx = np.where(cold, 3.0, vx)
+    p = np.where(cold, 1e-6, p)
+    G = prim_to_global(rho, vx, vy, vz, p, Xs)
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    G[5] *= rng.uniform(0.5, 1.5, G[5].shape)
+    grid = W.uniform_grid((2, 2, 2), (0.0, 0.0, 0.0), 1.0 / 16, periodic=(True, True, True))
+    return grid, scatter(G, (2, 2, 2)), scatter(cold[None].astype(float), (2, 2, 2))[:, 0] > 0.5

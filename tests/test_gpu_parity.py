@@ -485,14 +485,21 @@ def test_flux_form_and_dual_energy(hydro, oracle_mod, prec, form, de_switch, mac
 # several RK3 steps in one graph
 # ---------------------------------------------------------------------------
 
+@pytest.mark.parametrize("resync", [0, 1])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_rk3_run_matches_separate_steps(hydro, oracle_mod, prec):
+def test_rk3_run_matches_separate_steps(hydro, oracle_mod, prec, resync):
     """hydro_rk3_run_cfl over 3 steps is bit-identical to 3 hydro_rk3_step_cfl
-    calls each followed by hydro_totals (same dt sequence, same totals)."""
+    calls each followed by hydro_totals (same dt sequence, same totals), with
+    and without the tracer reset (which the run applies to its chained shadow)."""
     w = W.config(3)
     U = _filled(oracle_mod, w)
+    if resync:
+        rng = np.random.Generator(np.random.PCG64(22))
+        U[IN[0], 5:6, IN[2], IN[3], IN[4]] *= rng.uniform(0.5, 1.5, U[IN][:, 5:6].shape)
+        oracle_mod.Oracle(w.grid).fill_ghosts(U)
     ids = torch.as_tensor(w.batches.ids, device="cuda")
     g = hydro.HydroGrid(w.grid, precision=prec)
+    g.set_param(hydro.PARAM_TAU_RESYNC, resync)
     res = []
     for mode in ("separate", "run"):
         Ud = _dev(U)
@@ -647,3 +654,68 @@ def test_full_size_rk3_in_bench_launch(hydro, oracle_mod, prec):
     got = Ud.index_select(0, torch.as_tensor(sample, device="cuda", dtype=torch.long)).cpu().numpy()
     err = field_errors(got, ref)
     assert np.all(err <= TOL[prec]), (err, field_errors(got, ref, plain=True))
+
+
+# ---------------------------------------------------------------------------
+# dual-energy tracer reset
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_tau_resync_matches_oracle(hydro, oracle_mod, prec):
+    grid, U, cold = H.resync_case()
+    ref = U.copy()
+    n_reset = oracle_mod.Oracle(grid).tau_resync(ref)
+    assert 0 < n_reset < grid.n * 512
+    g = hydro.HydroGrid(grid, precision=prec)
+    Ud = _dev(U)
+    g.tau_resync(Ud)
+    g.sync()
+    got = _host(Ud)
+    others = [f for f in range(11) if f != 5]
+    assert np.array_equal(got[:, others], U[:, others], equal_nan=True)
+    assert np.array_equal(np.isnan(got[:, 5]), np.isnan(U[:, 5]))
+    gi, ri, ui = got[IN][:, 5], ref[IN][:, 5], U[IN][:, 5]
+    cold_in = cold[:, NG:NG + NX, NG:NG + NX, NG:NG + NX]
+    assert np.array_equal(gi[cold_in], ui[cold_in])       # below the switch: untouched
+    rel = np.abs(gi - ri) / np.abs(ri)
+    # FP64: pow against the host libm; mixed: FP32 powf of the FP64 e_i
+    assert rel.max() <= (1e-14 if prec == "fp64" else 1e-6), rel.max()
+
+
+def test_tau_resync_refreshes_shadow(hydro):
+    grid, U, _ = H.resync_case(seed=13)
+    g = hydro.HydroGrid(grid, precision="mixed")
+    Ud = _dev(U)
+    S = g.shadow(Ud)
+    g.tau_resync(Ud, S)
+    S_new = g.shadow(Ud)
+    g.sync()
+    assert torch.equal(S, S_new)
+    with pytest.raises(hydro.HydroError):
+        hydro.HydroGrid(grid, precision="fp64").tau_resync(Ud, S)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_rk3_step_with_tau_resync_matches_oracle(hydro, oracle_mod, prec):
+    """A step on the AMR configuration whose input tracer is scrambled: with the
+    reset on, the step ends with tau = e_i^(1/gamma) wherever the switch trusts
+    e_i, as in the oracle (without it tau stays far off)."""
+    w = W.config(3)
+    U = w.state()
+    rng = np.random.Generator(np.random.PCG64(21))
+    U[IN[0], 5:6, IN[2], IN[3], IN[4]] *= rng.uniform(0.5, 1.5, U[IN][:, 5:6].shape)
+    o = oracle_mod.Oracle(w.grid)
+    o.fill_ghosts(U)
+    dt, _ = _dt(oracle_mod, w, U)
+    ref, _, st = o.rk3_step(U, dt, tau_resync=True)
+    assert st == 0
+    plain, _, _ = o.rk3_step(U, dt)
+    assert field_errors(plain, ref, plain=True)[5] > 1e-2
+    g = hydro.HydroGrid(w.grid, precision=prec)
+    g.set_param(hydro.PARAM_TAU_RESYNC, 1)
+    Ud = _dev(U)
+    s1, s2 = torch.empty_like(Ud), torch.empty_like(Ud)
+    ids = torch.as_tensor(w.batches.ids, device="cuda")
+    g.rk3_step(Ud, dt, s1, s2, ids=ids, batch_offsets=w.batches.offsets)
+    g.sync()
+    err = field_errors(_host(Ud), ref)
+    assert np.all(err <= TOL[prec]), err

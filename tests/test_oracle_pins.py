@@ -553,27 +553,12 @@ def test_amr_conservation_needs_flux_correction(oracle_mod, reflux):
 # Dual-energy resynchronisation of the entropy tracer
 # ---------------------------------------------------------------------------
 
-def _resync_case(seed=11):
-    """Periodic 2x2x2 sub-grids: a random smooth state whose tracer is scrambled
-    (no longer matching the internal energy), with a slab of cold fast cells
-    whose internal energy is 1e-5 of the kinetic one (below the switch)."""
-    G = H.random_smooth_global((16, 16, 16), seed, vamp=0.3)
-    rng = np.random.Generator(np.random.PCG64(seed))
-    G[5] *= rng.uniform(0.5, 1.5, G[5].shape)
-    ek = 0.5 * (G[1] ** 2 + G[2] ** 2 + G[3] ** 2) / G[0]
-    cold = np.zeros(G[0].shape, bool)
-    cold[:, :, :4] = True
-    G[4] = np.where(cold, ek * (1.0 + 1e-5), G[4])
-    grid = W.uniform_grid((2, 2, 2), (0.0, 0.0, 0.0), 1.0 / 16, periodic=(True, True, True))
-    return grid, H.scatter(G, (2, 2, 2)), H.scatter(cold[None].astype(float), (2, 2, 2))[:, 0] > 0.5
-
-
 def test_tau_resync_tracer_pressure_matches_energy_pressure(oracle_mod):
     # What the reset is for: afterwards the face EOS gives the same pressure
     # whether it takes the internal energy from the total energy (switch off)
     # or from the tracer (switch forced on), in every cell the switch trusts;
     # cells below the switch keep their tracer bit for bit.
-    grid, U, cold = _resync_case()
+    grid, U, cold = H.resync_case()
     o = oracle_mod.Oracle(grid)
     V = U.copy()
     n_reset = o.tau_resync(V)
@@ -614,7 +599,7 @@ def test_tau_resync_fixed_point_of_initial_state(oracle_mod):
 
 
 def test_tau_resync_idempotent_and_switch_off(oracle_mod):
-    grid, U, _ = _resync_case(seed=12)
+    grid, U, _ = H.resync_case(seed=12)
     o = oracle_mod.Oracle(grid)
     V = U.copy()
     o.tau_resync(V)
