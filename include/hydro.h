@@ -261,8 +261,8 @@ int hydro_totals(hydro_handle *h, const double *U, double *d_totals, void *strea
  *   corner of each sub-grid's interior; d_out DEVICE double[12]. */
 int hydro_diagnostics(hydro_handle *h, const double *U, const double *d_origin, double *d_out, void *stream);
 
-/* Dual-energy reset of the entropy tracer (the solver's dual-energy formalism;
- * the paper prints no formula).  In every interior cell where the internal
+/* Dual-energy reset of the entropy tracer (the paper is silent on the EOS;
+ * this completes the dual-energy switch of the face EOS).  In every interior cell where the internal
  * energy e_i = E - (sx^2 + sy^2 + sz^2) / (2 rho) is positive and at least
  * eta E (eta = the handle's de_switch; the complement of the face EOS test
  * that takes e_i = tau^gamma), set tau = e_i^(1/gamma); every other cell and

@@ -472,8 +472,8 @@ void oracle_diagnostics(const oracle_grid *g, const double *U, const double *ori
 }
 
 /* ------------------------------------------------------------------------- */
-/* Dual-energy resynchronisation of the entropy tracer (the paper names the   */
-/* dual-energy formalism of its solver but prints no formula; reading R5').   */
+/* Dual-energy resynchronisation of the entropy tracer (the paper is silent on */
+/* the EOS; a reading that completes the face EOS switch above).              */
 /* Per interior cell, with the same kinetic and internal energies as the face */
 /* EOS:                                                                       */
 /*   e_k = (sx^2 + sy^2 + sz^2) / 2 rho,   e_i = E - e_k;                      */

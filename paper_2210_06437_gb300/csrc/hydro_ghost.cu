@@ -149,8 +149,8 @@ __global__ void __launch_bounds__(256) shadow_kernel(const double* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// Dual-energy reset of the entropy tracer (the dual-energy formalism of the
-// paper's solver; the paper prints no formula): in every interior cell where
+// Dual-energy reset of the entropy tracer (the paper is silent on the EOS;
+// this completes the dual-energy switch of the face EOS): in every interior cell where
 // the internal energy e_i = E - |s|^2 / 2 rho is positive and at least eta E
 // (the complement of the face EOS test e_i < eta E), tau = e_i^(1/gamma).
 // e_k and e_i are formed in FP64 as the face EOS forms them; the power is FP64
