@@ -359,8 +359,10 @@ def main():
         g.step(U, 0.0, U_out=s1, ids=ids, batch_offsets=offs, max_speed=ms)   # first CFL speed
         # copies in 8 chunks, one stream each: chunk k of a step's download and
         # chunk k of the next step's upload follow each other on stream k, so the
-        # two directions of the host link overlap; the compute stream waits for
-        # every upload chunk and the download chunks wait for the packed state
+        # two directions of the host link overlap; each chunk is unpacked on its
+        # stream as soon as it has arrived and packed on its stream before its
+        # download, so those passes overlap the other chunks' copies; the compute
+        # stream waits for every unpacked chunk
         n_chunks = 8
         bounds = [(n * c // n_chunks, n * (c + 1) // n_chunks) for c in range(n_chunks)]
         cstreams = [torch.cuda.Stream() for _ in range(n_chunks)]
@@ -372,21 +374,21 @@ def main():
             for (a_, b_), cs in zip(bounds, cstreams):
                 with torch.cuda.stream(cs):
                     Pd[a_:b_].copy_(Ph[a_:b_], non_blocking=True)
+                    g.unpack(Pd, U, stream=cs, first=a_, count=b_ - a_)
                     ev = torch.cuda.Event()
                     ev.record(cs)
                     ev_up.append(ev)
             for ev in ev_up:
                 stream.wait_event(ev)
-            g.unpack(Pd, U)
             g.rk3_step_cfl(U, 0.4, s1, s2, ms, ids=ids, batch_offsets=offs)
             g.totals(U, out=tot)
-            g.pack(U, Pd)
             toth.copy_(tot, non_blocking=True)
-            ev_packed = torch.cuda.Event()
-            ev_packed.record(stream)
+            ev_done = torch.cuda.Event()
+            ev_done.record(stream)
             for (a_, b_), cs in zip(bounds, cstreams):
-                cs.wait_event(ev_packed)
+                cs.wait_event(ev_done)
                 with torch.cuda.stream(cs):
+                    g.pack(U, Pd, stream=cs, first=a_, count=b_ - a_)
                     Ph[a_:b_].copy_(Pd[a_:b_], non_blocking=True)
 
         def join():
@@ -410,9 +412,10 @@ def main():
         nbytes = Pd.numel() * 8
         e2e = {"value": aggregate_rate(cells, 3, world, t_e2e), "unit": "cell-updates/s", "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes + 88, "ms_per_step": t_e2e * 1e3,
-               "api": "every step: pinned host packed interiors -> device (8 chunks on 8 streams) + "
-                      "HydroGrid.unpack + rk3_step_cfl + totals + pack -> pinned host (same chunks; a step's "
-                      "download overlaps the next step's upload on the full-duplex host link)"}
+               "api": "every step: pinned host packed interiors -> device in 8 chunks on 8 streams, each "
+                      "unpacked on arrival (hydro_unpack_interiors_range) + rk3_step_cfl + totals + per-chunk "
+                      "pack (hydro_pack_interiors_range) -> pinned host (same chunks; a step's download overlaps "
+                      "the next step's upload on the full-duplex host link)"}
         g.close()
         del Ph, Pd
 

@@ -175,6 +175,15 @@ int hydro_step_shadowed(hydro_handle *h, const hydro_batch *batch, const double 
 int hydro_pack_interiors(hydro_handle *h, const double *U, double *P, void *stream);
 int hydro_unpack_interiors(hydro_handle *h, const double *P, double *U, void *stream);
 
+/* The same for the sub-grids first .. first + count - 1 only (U and P are the
+ * whole arrays), so that the packing of one slice can overlap the host copies
+ * of others.  0 <= first, 0 <= count, first + count <= n_subgrids, else
+ * HYDRO_ERR_INVALID; count == 0 launches nothing. */
+int hydro_pack_interiors_range(hydro_handle *h, const double *U, double *P, int32_t first, int32_t count,
+                               void *stream);
+int hydro_unpack_interiors_range(hydro_handle *h, const double *P, double *U, int32_t first, int32_t count,
+                                 void *stream);
+
 /* Fill the six face ghost slabs (3 layers each) of every sub-grid of U from
  * the neighbours' interiors (Section VI: hydro boundary exchange): copy from a
  * same-level neighbour; coarse neighbour: value of the coarse cell containing

@@ -451,6 +451,34 @@ int hydro_unpack_interiors(hydro_handle* h, const double* P, double* U, void* st
   return HYDRO_OK;
 }
 
+int hydro_pack_interiors_range(hydro_handle* h, const double* U, double* P, int32_t first, int32_t count,
+                               void* stream) {
+  if (!h) return HYDRO_ERR_INVALID;
+  if (!U || !P || !aligned(U, 16) || !aligned(P, 16)) return fail(h, HYDRO_ERR_INVALID, "NULL or misaligned pointer");
+  if (first < 0 || count < 0 || (int64_t)first + count > h->n) return fail(h, HYDRO_ERR_INVALID, "range out of bounds");
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  if (count == 0) return HYDRO_OK;
+  cudaError_t e = launch_pack(U + (size_t)first * NF * NP3, P + (size_t)first * NF * CELLS, count, st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "pack kernel launch");
+  h->launches += 1;
+  return HYDRO_OK;
+}
+
+int hydro_unpack_interiors_range(hydro_handle* h, const double* P, double* U, int32_t first, int32_t count,
+                                 void* stream) {
+  if (!h) return HYDRO_ERR_INVALID;
+  if (!U || !P || !aligned(U, 16) || !aligned(P, 16)) return fail(h, HYDRO_ERR_INVALID, "NULL or misaligned pointer");
+  if (first < 0 || count < 0 || (int64_t)first + count > h->n) return fail(h, HYDRO_ERR_INVALID, "range out of bounds");
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  if (count == 0) return HYDRO_OK;
+  cudaError_t e = launch_unpack(P + (size_t)first * NF * CELLS, U + (size_t)first * NF * NP3, count, st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "unpack kernel launch");
+  h->launches += 1;
+  return HYDRO_OK;
+}
+
 int hydro_step_shadowed(hydro_handle* h, const hydro_batch* batch, const double* U_in, const float* S_in,
                         const double* U0, double beta, double dt, double* U_out, float* S_out, double* d_max_speed,
                         void* stream) {

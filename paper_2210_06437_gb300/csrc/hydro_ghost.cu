@@ -153,8 +153,9 @@ __global__ void __launch_bounds__(256) shadow_kernel(const double* __restrict__ 
 // this completes the dual-energy switch of the face EOS): in every interior cell where
 // the internal energy e_i = E - |s|^2 / 2 rho is positive and at least eta E
 // (the complement of the face EOS test e_i < eta E), tau = e_i^(1/gamma).
-// e_k and e_i are formed in FP64 as the face EOS forms them; the power is FP64
-// for FP64 handles and FP32 (powf, about 1 ulp) for mixed ones.  One CTA per
+// e_k and e_i are formed in FP64 (FP64 handles: as the face EOS forms them;
+// mixed: 1/rho from a refined FP32 reciprocal); the power is FP64 for FP64
+// handles and FP32 (powf, about 1 ulp) for mixed ones.  One CTA per
 // sub-grid; with a shadow S (mixed), its tau field and tau restriction are
 // rewritten exactly as the shadow kernel would write them from the new state.
 // ---------------------------------------------------------------------------
@@ -167,8 +168,17 @@ __global__ void __launch_bounds__(256) tau_resync_kernel(double* __restrict__ U,
     const size_t o = (size_t)((c >> 6) + NG) * NP2 + (((c >> 3) & 7) + NG) * NP + ((c & 7) + NG);
     const double rho = u[o], sx = u[NP3 + o], sy = u[2 * NP3 + o], sz = u[3 * NP3 + o], E = u[4 * NP3 + o];
     double tau = u[(size_t)F_TAU * NP3 + o];
-    const double s2 = __dadd_rn(__dadd_rn(__dmul_rn(sx, sx), __dmul_rn(sy, sy)), __dmul_rn(sz, sz));
-    const double ek = __ddiv_rn(__dmul_rn(0.5, s2), rho);
+    double ek;
+    if constexpr (MIXED) {
+      // 1/rho: FP32 reciprocal, one Newton step in FP64 (relative error about
+      // 2^-46), a handful of FP64 operations where a division takes a dozen
+      const double r0 = (double)__frcp_rn((float)rho);
+      const double r = fma(r0, fma(-rho, r0, 1.0), r0);
+      ek = 0.5 * (fma(sx, sx, fma(sy, sy, sz * sz)) * r);
+    } else {
+      const double s2 = __dadd_rn(__dadd_rn(__dmul_rn(sx, sx), __dmul_rn(sy, sy)), __dmul_rn(sz, sz));
+      ek = __ddiv_rn(__dmul_rn(0.5, s2), rho);
+    }
     const double ei = __dsub_rn(E, ek);
     if (ei > 0.0 && ei >= __dmul_rn(eta, E)) {
       if constexpr (MIXED)

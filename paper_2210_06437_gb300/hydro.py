@@ -28,7 +28,8 @@ STATUS = {0: "HYDRO_OK", -1: "HYDRO_ERR_INVALID", -2: "HYDRO_ERR_CUDA", -3: "HYD
 # every symbol include/hydro.h declares
 EXPORTS = ("hydro_create", "hydro_step", "hydro_shadow", "hydro_step_shadowed", "hydro_fill_ghosts", "hydro_rk3_step",
            "hydro_rk3_step_cfl", "hydro_rk3_run_cfl", "hydro_rk3_run_prepare", "hydro_totals", "hydro_diagnostics",
-           "hydro_tau_resync", "hydro_totals_noalloc", "hydro_pack_interiors", "hydro_unpack_interiors", "hydro_sync",
+           "hydro_tau_resync", "hydro_totals_noalloc", "hydro_pack_interiors", "hydro_unpack_interiors",
+           "hydro_pack_interiors_range", "hydro_unpack_interiors_range", "hydro_sync",
            "hydro_last_error", "hydro_launch_count", "hydro_set_param", "hydro_destroy")
 SHADOW_FIELD = NX * NX * NX + (NX // 2) ** 3   # interior, then its 4^3 restriction
 TOTALS_NOALLOC_MAX_SUBGRIDS = 65536
@@ -72,6 +73,8 @@ def load_library(path: str = LIB_PATH):
     L.hydro_fill_ghosts.argtypes = [vp, vp, vp]
     L.hydro_pack_interiors.argtypes = [vp, vp, vp, vp]
     L.hydro_unpack_interiors.argtypes = [vp, vp, vp, vp]
+    L.hydro_pack_interiors_range.argtypes = [vp, vp, vp, i32, i32, vp]
+    L.hydro_unpack_interiors_range.argtypes = [vp, vp, vp, i32, i32, vp]
     L.hydro_rk3_step.argtypes = [vp, ctypes.POINTER(Batch), vp, vp, vp, dbl, vp, vp]
     L.hydro_rk3_step_cfl.argtypes = [vp, ctypes.POINTER(Batch), vp, vp, vp, dbl, vp, vp, vp]
     L.hydro_rk3_run_cfl.argtypes = [vp, ctypes.POINTER(Batch), vp, vp, vp, dbl, i32, vp, vp, vp, vp]
@@ -231,18 +234,28 @@ class HydroGrid:
         assert P.numel() == self.n * NF * NX ** 3
         return P
 
-    def pack(self, U, P=None, stream=None):
-        """Interiors of U into the packed array P (hydro_pack_interiors)."""
+    def pack(self, U, P=None, stream=None, first=None, count=None):
+        """Interiors of U into the packed array P (hydro_pack_interiors); with
+        first/count, only those sub-grids (hydro_pack_interiors_range)."""
         self._state(U)
         P = self.empty_interiors() if P is None else self._packed(P)
-        self._check(self.lib.hydro_pack_interiors(self.h, _ptr(U), _ptr(P), _stream_ptr(stream)))
+        if first is None:
+            self._check(self.lib.hydro_pack_interiors(self.h, _ptr(U), _ptr(P), _stream_ptr(stream)))
+        else:
+            self._check(self.lib.hydro_pack_interiors_range(self.h, _ptr(U), _ptr(P), first, count,
+                                                            _stream_ptr(stream)))
         return P
 
-    def unpack(self, P, U, stream=None):
-        """Interiors of U from the packed array P (hydro_unpack_interiors)."""
+    def unpack(self, P, U, stream=None, first=None, count=None):
+        """Interiors of U from the packed array P (hydro_unpack_interiors); with
+        first/count, only those sub-grids (hydro_unpack_interiors_range)."""
         self._state(U)
         self._packed(P)
-        self._check(self.lib.hydro_unpack_interiors(self.h, _ptr(P), _ptr(U), _stream_ptr(stream)))
+        if first is None:
+            self._check(self.lib.hydro_unpack_interiors(self.h, _ptr(P), _ptr(U), _stream_ptr(stream)))
+        else:
+            self._check(self.lib.hydro_unpack_interiors_range(self.h, _ptr(P), _ptr(U), first, count,
+                                                              _stream_ptr(stream)))
         return U
 
     def upload(self, P_host, U, P_dev, stream=None):

@@ -548,6 +548,23 @@ def test_pack_unpack_interiors(hydro):
     g.download(Ud, P, Ph)
     torch.cuda.synchronize()
     assert np.array_equal(Ph.numpy(), U[IN].reshape(n, 11, 512))
+    # ranged variants: a ragged slice in the middle, the tail, an empty range
+    a, b = 777, 2049
+    Q = torch.full_like(P, -7.0)
+    g.pack(Ud, Q, first=a, count=b - a)
+    g.pack(Ud, Q, first=n - 3, count=3)
+    g.pack(Ud, Q, first=n, count=0)
+    W2 = torch.full_like(Ud, -5.0)
+    g.unpack(P * 3.0, W2, first=a, count=b - a)
+    g.sync()
+    q, w2, ref = _host(Q), _host(W2), U[IN].reshape(n, 11, 512)
+    assert np.array_equal(q[a:b], ref[a:b]) and np.array_equal(q[n - 3:], ref[n - 3:])
+    assert np.all(q[:a] == -7.0) and np.all(q[b:n - 3] == -7.0)
+    assert np.array_equal(w2[a:b][IN], 3.0 * U[a:b][IN])
+    assert np.all(w2[:a] == -5.0) and np.all(w2[b:] == -5.0)
+    for first, count in ((-1, 2), (0, n + 1), (n - 1, 2), (5, -1)):
+        with pytest.raises(hydro.HydroError):
+            g.pack(Ud, Q, first=first, count=count)
 
 
 # ---------------------------------------------------------------------------
