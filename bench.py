@@ -76,6 +76,9 @@ def parse():
     p.add_argument("--skip-e2e", action="store_true")
     p.add_argument("--skip-fp64", action="store_true")
     p.add_argument("--skip-cpu", action="store_true")
+    p.add_argument("--sweep", action="store_true",
+                   help="per-configuration table (one JSON line per configuration and precision, errors against "
+                        "the oracle, oracle timings); not the benchmark line")
     return p.parse_args()
 
 
@@ -217,6 +220,101 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# per-configuration sweep
+# ---------------------------------------------------------------------------
+
+def field_errors(x, r, gamma=5.0 / 3.0):
+    """Per-field error of interior cells: max|x_f - r_f| / S_f, S_f = max|r_f|,
+    and for the three momenta the momentum-density scale max(|s|, rho c)."""
+    sl = (slice(None), slice(None), slice(3, 11), slice(3, 11), slice(3, 11))
+    xi, ri = x[sl], r[sl]
+    d = np.abs(xi - ri).max(axis=(0, 2, 3, 4))
+    S = np.abs(ri).max(axis=(0, 2, 3, 4))
+    rho = ri[:, 0]
+    s2 = ri[:, 1] ** 2 + ri[:, 2] ** 2 + ri[:, 3] ** 2
+    p = (gamma - 1.0) * np.maximum(ri[:, 4] - 0.5 * s2 / rho, 0.0)
+    S[1:4] = max(np.sqrt(s2).max(), np.sqrt(gamma * rho * p).max())
+    return np.where(S > 0, d / np.where(S > 0, S, 1.0), np.where(d == 0, 0.0, np.inf))
+
+
+def run_sweep(args):
+    """Every workload configuration: one stage and one SSP-RK3 step of each
+    precision against the oracle on the same input (the error metric of the
+    parity tests), the RK3 step rate of the multi-step graph, and the oracle's
+    own rates (all host threads on the whole grid; one thread on a sample)."""
+    import torch
+    import oracle
+    from paper_2210_06437_gb300 import build, hydro as HY
+    from paper_2210_06437_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    build.build()
+    oracle.build()
+    hbm, _ = peaks()
+    stream = torch.cuda.current_stream()
+    for cfg in (1, 2, 3, 4, 5):
+        w = W.config(cfg)
+        U = w.state()
+        o = oracle.Oracle(w.grid)
+        o.fill_ghosts(U)
+        _, ms0, _ = o.stage(U, 0.0)
+        dt = 0.4 / ms0[1]
+        ref1 = np.empty_like(U)   # interiors written by the stage (allocated outside the timing)
+        t0 = time.perf_counter()
+        o.stage(U, dt, Uout=ref1)
+        t_o_stage = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        ref3, _, _ = o.rk3_step(U, dt)   # as it stands: its stage copies and ghost fills included
+        t_o_rk3 = time.perf_counter() - t0
+        ids1 = np.arange(min(w.grid.n, 16), dtype=np.int32)
+        tmp = np.empty_like(U)
+        t0 = time.perf_counter()
+        o.stage(U, dt, Uout=tmp, ids=ids1, nthreads=1, batch_all=True)
+        t_o_1 = time.perf_counter() - t0
+        del tmp
+        row = {"config": cfg, "workload": w.name, "subgrids": w.grid.n, "cells": w.cells,
+               "oracle": {"stage_rate_all_threads": w.cells / t_o_stage, "rk3_step_s_all_threads": t_o_rk3,
+                          "threads": os.cpu_count(), "stage_rate_1_thread": len(ids1) * 512 / t_o_1,
+                          "sample_1_thread": "%d sub-grids" % len(ids1)}}
+        ids = torch.as_tensor(w.batches.ids, device="cuda")
+        offs = w.batches.offsets
+        for prec in ("mixed", "fp64"):
+            g = HY.HydroGrid(w.grid, precision=prec)
+            Ud = torch.from_numpy(U).cuda()
+            out = Ud.clone()
+            g.step(Ud, dt, U_out=out, ids=ids, batch_offsets=offs)
+            err1 = field_errors(out.cpu().numpy(), ref1)
+            V = Ud.clone()
+            s1, s2 = torch.empty_like(Ud), torch.empty_like(Ud)
+            g.rk3_step(V, dt, s1, s2, ids=ids, batch_offsets=offs)
+            g.fill_ghosts(V)
+            err3 = field_errors(V.cpu().numpy(), ref3)
+            del out
+            k = 5 if prec == "mixed" else 2
+            msd = torch.zeros(2, dtype=torch.float64, device="cuda")
+            g.step(V, 0.0, U_out=s1, ids=ids, batch_offsets=offs, max_speed=msd)
+            g.rk3_run_prepare(V, 0.4, s1, s2, msd, k, ids=ids, batch_offsets=offs)
+            g.rk3_run_cfl(V, 0.4, s1, s2, msd, k, ids=ids, batch_offsets=offs)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.rk3_run_cfl(V, 0.4, s1, s2, msd, k, ids=ids, batch_offsets=offs)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            g.sync()
+            t_step = e0.elapsed_time(e1) / 1e3 / k
+            g.close()
+            del Ud, V, s1, s2
+            torch.cuda.empty_cache()
+            row[prec] = {"rk3_step_ms": t_step * 1e3, "cell_updates_per_s": w.cells * 3 / t_step,
+                         "hbm_frac_of_measured": BYTES_PER_CELL_RK3_STAGE * w.cells * 3 / t_step / 1e9 / hbm,
+                         "err_one_stage": float(err1.max()), "err_rk3_step": float(err3.max()),
+                         "tolerance": 1e-5 if prec == "mixed" else 1e-12}
+        row["mixed_speedup_vs_fp64"] = row["fp64"]["rk3_step_ms"] / row["mixed"]["rk3_step_ms"]
+        print(json.dumps(row), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 
@@ -224,6 +322,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep:
+        return run_sweep(args)
     import torch
     rank, world, local = dist_info()
     pg = None
