@@ -265,7 +265,7 @@ def run_sweep(args):
         t0 = time.perf_counter()
         ref3, _, _ = o.rk3_step(U, dt)   # as it stands: its stage copies and ghost fills included
         t_o_rk3 = time.perf_counter() - t0
-        ids1 = np.arange(min(w.grid.n, 16), dtype=np.int32)
+        ids1 = np.sort(np.random.default_rng(cfg).choice(w.grid.n, min(w.grid.n, 64), replace=False)).astype(np.int32)
         tmp = np.empty_like(U)
         t0 = time.perf_counter()
         o.stage(U, dt, Uout=tmp, ids=ids1, nthreads=1, batch_all=True)
