@@ -180,10 +180,11 @@ int enqueue_stage(hydro_handle* h, const int32_t* ids, int n_items, const double
   CUDA_TRY(h, cudaMemsetAsync(h->d_queue + queue_slot, 0, sizeof(unsigned int), st));
   StageArgs a;
   std::memset(&a, 0, sizeof(a));
-  // the FP64-layout arrays the update reads: Uin (and U0) in mode 0, nothing in
-  // mode 1, the increment in mode 2, U and the increment in mode 3
-  const double* first = mode == 0 || mode == 3 ? Uin : (mode == 2 ? Din : nullptr);
-  const double* second = mode == 3 ? Din : (mode == 0 ? U0 : nullptr);
+  // the padded FP64 arrays the update reads, prefetched by tensor map: Uin
+  // (and U0) in mode 0, U in mode 3 (the increments, packed, are prefetched
+  // as plain blocks)
+  const double* first = mode == 0 || mode == 3 ? Uin : nullptr;
+  const double* second = mode == 0 ? U0 : nullptr;
   if (first && encode_state_map(&a.tm_in, first, h->n)) {
     a.has_tm = 1;
     if (second && encode_state_map(&a.tm_u0, second, h->n)) a.has_tm |= 2;

@@ -67,7 +67,7 @@ struct StageArgs {
   // Modes 1 and 2 take RN32(U) of their own cells from S0, the shadow of U
   // (in mode 1 that is Sin itself), and read no FP64 state.
   int32_t mode;
-  const double* Din;
+  const double* Din;     // increments as float pairs, packed interiors [s][f][512]
   double* Dout;
   const float* S0;
   // coarse-fine flux correction: when fb is set, each sub-grid stamps
@@ -98,7 +98,7 @@ struct RefluxArgs {
   int32_t mode;          // the stage's mode (StageArgs)
   double beta;           // mode 0
   double* U;             // mode 0 and 3: the stage's FP64 output
-  double* D;             // modes 1, 2: the stage's increment output
+  double* D;             // modes 1, 2: the stage's increment output (packed interiors [s][f][512])
   const float* S0;       // modes 1, 2: shadow of the step's input state
   float* Sout;           // the stage's shadow output, refreshed where corrected (may be null)
   int* err;

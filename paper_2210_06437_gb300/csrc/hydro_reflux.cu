@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(RT, sizeof(T) == 4 ? 4 : 3) reflux_kernel(cons
       if (s_ok[1 + face * 4 + (t1 >> 2) + 2 * (t2 >> 2)]) term[u] = load_term(fb, s, fs, face, f, t1, t2);
       const size_t o = ((size_t)s * NF + f) * NP3 + interior_offset(i, j, k);
       if (sizeof(T) == 4 && (r.mode == 1 || r.mode == 2)) {
-        val[u] = r.D[o];
+        val[u] = r.D[((size_t)s * NF + f) * CELLS + (k * NX + j) * NX + i];  // packed increment layout
         s0[u] = __ldg(r.S0 + ((size_t)s * NF + f) * SHADOW_FIELD + (k * NX + j) * NX + i);
       } else {
         val[u] = r.U[o];
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(RT, sizeof(T) == 4 ? 4 : 3) reflux_kernel(cons
       const size_t o = ((size_t)s * NF + f) * NP3 + interior_offset(i, j, k);
       float x;  // the cell's new shadow value (mixed)
       if (sizeof(T) == 4 && (r.mode == 1 || r.mode == 2)) {
-        r.D[o] = __hiloint2double(__float_as_int(dh), __float_as_int(dl));
+        r.D[((size_t)s * NF + f) * CELLS + c] = __hiloint2double(__float_as_int(dh), __float_as_int(dl));
         x = __fadd_rn(s0[u], dh);
         if (!(x - x == 0.0f) || (f == F_RHO && !(x > 0.0f))) bad = 1;
       } else {

@@ -607,6 +607,11 @@ __device__ __forceinline__ void stage_interior_async(const float* __restrict__ S
 // read too) into L2 ahead of time: one TMA tensor prefetch per array (the box
 // starts at i = 2, a 16-byte boundary).
 __device__ __forceinline__ void prefetch_update_rows(const StageArgs& a, int s) {
+  if (a.Din && threadIdx.x < NF) {  // the previous increment: one 4 KB block per field
+    const double* p = a.Din + ((size_t)s * NF + threadIdx.x) * CELLS;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"((unsigned)(CELLS * sizeof(double)))
+                 : "memory");
+  }
   if (threadIdx.x != 0 || !(a.has_tm & 1)) return;
   asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"(&a.tm_in), "r"(NG - 1),
                "r"(NG), "r"(NG), "r"(s * NF)
@@ -856,6 +861,12 @@ __device__ __forceinline__ void write_shadow(float* So, int c0, float x0, float 
   if ((tid & 9) == 0) So[SHADOW_COARSE + cc] = __fmul_rn(__fadd_rn(t.x, t.y), 0.125f);  // i and j even
 }
 
+// The increments live in the scratch arrays as packed interiors, one float
+// pair per 8-byte slot at [s][f][(k*8 + j)*8 + i]: 64-byte rows on 64-byte
+// boundaries (the padded layout's rows start 24 bytes into a 32-byte sector,
+// so every row write there also read back two partial sectors).
+__device__ __forceinline__ size_t inc_offset(int s, int f) { return ((size_t)s * NF + f) * CELLS; }
+
 // Fields [F0, F1) of update_inc below.
 template <int MODE, bool SHADOW, int F0, int F1>
 __device__ __forceinline__ unsigned update_inc_fields(const StageArgs& a, int s, const Acc<float> (&acc)[NF],
@@ -873,7 +884,7 @@ __device__ __forceinline__ unsigned update_inc_fields(const StageArgs& a, int s,
         u0v[f - F0][r] = a.Uin[o];
       else
         s0v[f - F0][r] = a.S0[((size_t)s * NF + f) * SHADOW_FIELD + c0 + r * 64];
-      if constexpr (READ_D) dv[f - F0][r] = a.Din[o];
+      if constexpr (READ_D) dv[f - F0][r] = a.Din[inc_offset(s, f) + c0 + r * 64];
     }
   const float2 lh2 = make_float2(lh, lh), ll2 = make_float2(ll, ll);
 #pragma unroll
@@ -907,7 +918,7 @@ __device__ __forceinline__ unsigned update_inc_fields(const StageArgs& a, int s,
         if (f == F_RHO) bad |= bad64(v, true);
         x[r] = f64_to_f32(v);
       } else {
-        a.Dout[o] = pack_pair(dh, dl);
+        a.Dout[inc_offset(s, f) + c0 + r * 64] = pack_pair(dh, dl);
         x[r] = __fadd_rn(s0v[f - F0][r], dh);
         nf |= (__float_as_uint(x[r]) & 0x7f800000u) == 0x7f800000u ? 0x80000000u : 0u;
         if (f == F_RHO) bad |= !(x[r] > 0.0f);
