@@ -109,16 +109,22 @@ __device__ __forceinline__ T limited_slope2(T qm, T q0, T qp) {
 
 // CW84 eq. 1.10: flatten at an extremum, else move the far face so that the
 // parabola has no interior extremum.
+// In the differences u = r - a, w = a - l: flat where u w <= 0; with
+// D = u + w (= r - l) and E = w - u (= 2 (a - (l + r)/2)), the tests
+// (r - l)(a - (l + r)/2) > (r - l)^2 / 6 and its mirror become 3 D E > D^2 and
+// -D^2 > 3 D E, and the moved faces are 3a - 2r = a - 2u and 3a - 2l = a + 2w.
+// Mirroring (l <-> r) maps (u, w) to (-w, -u): D changes sign, E and D^2 do
+// not, so the two tests swap exactly.
 template <typename T>
 __device__ __forceinline__ void parabola_limit(T a, T& l, T& r) {
-  bool flat = (r - a) * (a - l) <= T(0);
-  T da = r - l;
-  T lhs = da * (a - T(0.5) * (l + r));
-  T rhs = da * da * T(1.0 / 6.0);
-  bool lo = lhs > rhs;
-  bool hi = (!lo) && (-rhs > lhs);
-  T nl = lo ? T(3) * a - T(2) * r : l;
-  T nr = hi ? T(3) * a - T(2) * l : r;
+  const T u = r - a, w = a - l;
+  const bool flat = u * w <= T(0);
+  const T D = u + w, E = w - u;
+  const T X = T(3) * (D * E), Y = D * D;
+  const bool lo = X > Y;
+  const bool hi = (!lo) && (-Y > X);
+  const T nl = lo ? a - T(2) * u : l;
+  const T nr = hi ? a + T(2) * w : r;
   l = flat ? a : nl;
   r = flat ? a : nr;
 }
