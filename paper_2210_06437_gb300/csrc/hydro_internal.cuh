@@ -105,7 +105,7 @@ struct RefluxArgs {
 };
 
 // Encode the TMA descriptor of a padded state (n sub-grids) used by
-// StageArgs::tm_in / tm_u0; returns false if the driver refuses it.
+// StageArgs::tm_in / tm_u0; returns false if cuTensorMapEncodeTiled refuses it.
 bool encode_state_map(CUtensorMap* tm, const double* U, int n);
 
 struct GhostArgs {
