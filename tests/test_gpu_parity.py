@@ -320,6 +320,14 @@ def test_host_argument_errors(hydro):
         g.step(Ud, 1e-3, U_out=torch.empty_like(Ud), beta=0.5)  # U0 missing
     with pytest.raises(hydro.HydroError):
         g.step(Ud, 1e-3, U_out=torch.empty_like(Ud), batch_offsets=[0, 5])  # offsets do not reach n
+    for key, value in ((hydro.PARAM_TAU_RESYNC, 2), (hydro.PARAM_REFLUX, -1), (hydro.PARAM_STAGE_CTAS_PER_SM, 9),
+                       (hydro.PARAM_GHOST_THREADS, 100), (99, 0)):
+        with pytest.raises(hydro.HydroError):
+            g.set_param(key, value)
+    g.set_param(hydro.PARAM_TAU_RESYNC, 1)
+    g.set_param(hydro.PARAM_TAU_RESYNC, 0)
+    with pytest.raises(AssertionError):
+        g.tau_resync(Ud[:, :, ::2])   # not a padded state of this grid (the binding checks shapes)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
