@@ -706,6 +706,17 @@ def test_tau_resync_matches_oracle(hydro, oracle_mod, prec):
     assert rel.max() <= (1e-14 if prec == "fp64" else 1e-6), rel.max()
 
 
+def test_tau_resync_off_without_dual_energy(hydro):
+    grid, U, _ = H.resync_case(seed=14)
+    g = hydro.HydroGrid(grid, precision="mixed", de_switch=0.0)
+    Ud = _dev(U)
+    n0 = g.launches
+    g.tau_resync(Ud)
+    g.sync()
+    assert g.launches == n0                      # nothing to do: no launch
+    assert np.array_equal(_host(Ud), U, equal_nan=True)
+
+
 def test_tau_resync_refreshes_shadow(hydro):
     grid, U, _ = H.resync_case(seed=13)
     g = hydro.HydroGrid(grid, precision="mixed")
