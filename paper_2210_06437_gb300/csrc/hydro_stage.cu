@@ -608,10 +608,11 @@ __device__ __forceinline__ void stage_interior_async(const float* __restrict__ S
   }
 }
 
-// Pull the 10 x 8 x 8 x 11 box around the interior rows of sub-grid s that
-// the update will read (U_in, and U0 or the previous increment when that is
-// read too) into L2 ahead of time: one TMA tensor prefetch per array (the box
-// starts at i = 2, a 16-byte boundary).
+// Pull what the update of sub-grid s will read into L2 ahead of time: the
+// previous increment (packed, one 4 KB bulk prefetch per field), and the
+// 10 x 8 x 8 x 11 box around the interior rows of the padded FP64 arrays it
+// reads (U_in, and U0 in the blended stages): one TMA tensor prefetch per
+// array (the box starts at i = 2, a 16-byte boundary).
 __device__ __forceinline__ void prefetch_update_rows(const StageArgs& a, int s) {
   if (a.Din && threadIdx.x < NF) {  // the previous increment: one 4 KB block per field
     const double* p = a.Din + ((size_t)s * NF + threadIdx.x) * CELLS;
