@@ -50,7 +50,18 @@ struct Arith;
 
 template <>
 struct Arith<double> {
-  static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+  // 1/x by Newton-Raphson from the hardware's approximate FP64 reciprocal:
+  // r <- r + r (1 - x r) squares the relative error each step, so three
+  // steps take even a coarse seed below the final rounding; two FP64 FMAs per
+  // step instead of a full IEEE division.  Used for densities
+  // and positive signal-speed sums only (finite, normal, non-zero).
+  static __device__ __forceinline__ double rcp(double x) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    r = fma(r, fma(-x, r, 1.0), r);
+    r = fma(r, fma(-x, r, 1.0), r);
+    return fma(r, fma(-x, r, 1.0), r);
+  }
   static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
   static __device__ __forceinline__ double pow_(double x, double y) { return pow(x, y); }
   static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
@@ -90,20 +101,31 @@ __device__ __forceinline__ T limited_slope2(T qm, T q0, T qp) {
   T dl = q0 - qm;
   T dr = qp - q0;
   T delta = qp - qm;
-  T m = fabs(delta);
-  T l = T(4) * fabs(dl);
-  T r = T(4) * fabs(dr);
-  m = (l < m) ? l : m;
-  m = (r < m) ? r : m;
   if constexpr (sizeof(T) == 4) {
+    T m = fabs(delta);
+    T l = T(4) * fabs(dl);
+    T r = T(4) * fabs(dr);
+    m = (l < m) ? l : m;
+    m = (r < m) ? r : m;
     // same sign for dl and dr (else 0); then delta has it too (a zero dl or
     // dr already made m zero)
     const unsigned sl = __float_as_uint(dl), sr = __float_as_uint(dr);
     const unsigned keep = ~(unsigned)((int)(sl ^ sr) >> 31);
     return __uint_as_float((__float_as_uint(m) | (sl & 0x80000000u)) & keep);
   } else {
-    T res = (delta > T(0)) ? m : -m;
-    return (dl * dr <= T(0)) ? T(0) : res;
+    // FP64 is scarce: the magnitudes are compared as integers (non-negative
+    // doubles order as their bit patterns) and the sign is taken from the bits,
+    // leaving three FP64 operations (two differences and 4 dr; 4 dl is the
+    // previous cell's 4 dr)
+    constexpr long long MAG = 0x7fffffffffffffffLL;
+    long long m = __double_as_longlong(delta) & MAG;
+    const long long l = __double_as_longlong(T(4) * dl) & MAG;
+    const long long r = __double_as_longlong(T(4) * dr) & MAG;
+    m = l < m ? l : m;
+    m = r < m ? r : m;
+    const long long sl = __double_as_longlong(dl), sr = __double_as_longlong(dr);
+    const long long keep = ~((sl ^ sr) >> 63);
+    return __longlong_as_double((m | (sl & ~MAG)) & keep);
   }
 }
 
@@ -115,18 +137,39 @@ __device__ __forceinline__ T limited_slope2(T qm, T q0, T qp) {
 // -D^2 > 3 D E, and the moved faces are 3a - 2r = a - 2u and 3a - 2l = a + 2w.
 // Mirroring (l <-> r) maps (u, w) to (-w, -u): D changes sign, E and D^2 do
 // not, so the two tests swap exactly.
+// FP64: 3 D E > D^2 is D (w - 2u) > 0 and -D^2 > 3 D E is D (2w - u) < 0 (the
+// differences of the two sides, over 2D), and every sign test is done on the
+// bits, so only the five differences and the two moved faces use the scarce
+// FP64 pipe.
 template <typename T>
 __device__ __forceinline__ void parabola_limit(T a, T& l, T& r) {
   const T u = r - a, w = a - l;
-  const bool flat = u * w <= T(0);
-  const T D = u + w, E = w - u;
-  const T X = T(3) * (D * E), Y = D * D;
-  const bool lo = X > Y;
-  const bool hi = (!lo) && (-Y > X);
-  const T nl = lo ? a - T(2) * u : l;
-  const T nr = hi ? a + T(2) * w : r;
-  l = flat ? a : nl;
-  r = flat ? a : nr;
+  if constexpr (sizeof(T) == 4) {
+    const bool flat = u * w <= T(0);
+    const T D = u + w, E = w - u;
+    const T X = T(3) * (D * E), Y = D * D;
+    const bool lo = X > Y;
+    const bool hi = (!lo) && (-Y > X);
+    const T nl = lo ? a - T(2) * u : l;
+    const T nr = hi ? a + T(2) * w : r;
+    l = flat ? a : nl;
+    r = flat ? a : nr;
+  } else {
+    constexpr long long MAG = 0x7fffffffffffffffLL;
+    const long long bu = __double_as_longlong(u), bw = __double_as_longlong(w);
+    // u w <= 0: a zero or opposite signs (NaN differences count as not flat,
+    // as the product test has them)
+    const bool flat = ((bu & MAG) == 0) || ((bw & MAG) == 0) || ((bu ^ bw) < 0);
+    const T D = u + w, P = fma(T(-2), u, w), Q = fma(T(2), w, -u);
+    const long long bd = __double_as_longlong(D), bp = __double_as_longlong(P), bq = __double_as_longlong(Q);
+    const bool dnz = (bd & MAG) != 0;
+    const bool lo = dnz && ((bp & MAG) != 0) && ((bd ^ bp) >= 0);
+    const bool hi = (!lo) && dnz && ((bq & MAG) != 0) && ((bd ^ bq) < 0);
+    const T nl = lo ? fma(T(-2), u, a) : l;
+    const T nr = hi ? fma(T(2), w, a) : r;
+    l = flat ? a : nl;
+    r = flat ? a : nr;
+  }
 }
 
 // One pencil of 14 values -> face states of faces m+1/2, m = 2..10:
