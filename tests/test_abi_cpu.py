@@ -79,3 +79,45 @@ def test_null_arguments_are_rejected(lib):
     assert L.hydro_totals(None, None, None, None) == -1
     assert L.hydro_sync(None) == -1
     L.hydro_destroy(None)
+
+
+def test_new_entry_points_reject_null_handles(lib):
+    L, hydro = lib
+    assert L.hydro_tau_resync(None, None, None, None) == -1
+    assert L.hydro_pack_interiors_range(None, None, None, 0, 1, None) == -1
+    assert L.hydro_unpack_interiors_range(None, None, None, 0, 1, None) == -1
+    assert L.hydro_diagnostics(None, None, None, None, None) == -1
+
+
+def test_header_is_plain_c_and_links(lib, tmp_path):
+    """The boundary is a C ABI: a C99 program includes the header with every
+    warning an error, links against the library, and gets HYDRO_ERR_INVALID
+    back from calls without a handle (no GPU needed)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi.c"
+    src.write_text(r'''
+#include "hydro.h"
+#include <stdio.h>
+int main(void) {
+  hydro_handle *h = NULL;
+  int bad = 0;
+  bad |= hydro_create(NULL, &h) != HYDRO_ERR_INVALID;
+  bad |= hydro_sync(NULL) != HYDRO_ERR_INVALID;
+  bad |= hydro_totals(NULL, NULL, NULL, NULL) != HYDRO_ERR_INVALID;
+  bad |= hydro_tau_resync(NULL, NULL, NULL, NULL) != HYDRO_ERR_INVALID;
+  bad |= hydro_launch_count(NULL) != 0;
+  printf("%s\n", bad ? "FAIL" : "OK");
+  return bad;
+}
+''')
+    libdir = os.path.join(ROOT, "paper_2210_06437_gb300")
+    exe = tmp_path / "abi"
+    cmd = ["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+           "-L", libdir, "-lhydro", "-Wl,-rpath," + libdir, "-o", str(exe)]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0 and out.stdout.strip() == "OK", (out.stdout, out.stderr)
