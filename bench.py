@@ -49,7 +49,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 2 FP64 FMA/clk/SM at the 207
 # DRAM bytes (read + write) per cell-update of the mixed stage kernel from one ncu capture
 # (average of the three RK3 stage launches, profiles/stage_mixed_binary4k.md), valid only for
 # the kernel source it was taken on.
-STAGE_TRAFFIC = {"sha256_prefix": "f8394769aec71b21", "bytes_per_cell": 303.5,
+STAGE_TRAFFIC = {"sha256_prefix": "026d5c1d4fcba5cf", "bytes_per_cell": 303.5,
                  "source": "ncu capture of the three RK3 stage launches on the 4097-leaf reduced binary octree "
                            "(average), scaled by cells"}
 

@@ -22,12 +22,18 @@
 // largest face speed joins the global maximum (compute_fluxes' time-step
 // reduction) through one ordered-bits atomicMax.
 //
-// T = double: every step in FP64.  T = float (mixed): FP64 inputs are rounded
-// to FP32 once, by integer operations (GB300 runs FP64 and f32<->f64
-// conversions at about 2 per clock per SM, the FP32/INT pipes at 128), the
-// reconstruction and flux run in FP32, the six flux terms of every cell are
-// summed error-free as a float pair (TwoSum cascade), and the conserved update
-// is done in FP64 (2 FP64 operations per value in stage 1, 3 with the blend).
+// T = double: every step in FP64 (tests and reciprocals kept off the scarce
+// FP64 pipe where integer operations or a Newton-Raphson refinement do).
+// T = float (mixed): FP64 inputs are rounded to FP32 once, by integer
+// operations (GB300 runs FP64 and f32<->f64 conversions at about 2 per clock
+// per SM, the FP32/INT pipes at 128), into FP32 shadows the stage reads its
+// interior and halos from; the reconstruction and flux run in FP32, the six
+// flux terms of every cell are summed error-free as a float pair (TwoSum
+// cascade), and the conserved update is done in FP64.  The SSP-RK3 step runs
+// in increment form (modes 1..3, see update_inc): the increments stay float
+// pairs in packed scratch arrays and the FP64 state changes once per step.
+// Stages on coarse-fine faces also export their boundary fluxes for the
+// correction pass (hydro_reflux.cu).
 #include <cmath>
 
 #include "hydro_fp.cuh"
