@@ -65,6 +65,9 @@ def lib():
         L.oracle_diagnostics.argtypes = [ctypes.POINTER(_Grid), ctypes.c_void_p, ctypes.c_void_p, dp]
         L.oracle_tau_resync.argtypes = [ctypes.POINTER(_Grid), ctypes.c_void_p]
         L.oracle_tau_resync.restype = ctypes.c_long
+        L.oracle_margin_cells.argtypes = [ctypes.POINTER(_Grid), ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                          ctypes.c_double, ctypes.c_void_p]
+        L.oracle_margin_cells.restype = ctypes.c_long
         _lib = L
     return _lib
 
@@ -167,6 +170,20 @@ class Oracle:
         cells, in place); returns the number of cells reset."""
         self._check(U)
         return int(lib().oracle_tau_resync(ctypes.byref(self._g), U.ctypes.data))
+
+    def margin_cells(self, U: np.ndarray, eps: float, ids=None, mask: Optional[np.ndarray] = None):
+        """Interior cells near a branch decision of the scheme on input U (ghosts
+        filled): tests within 64 eps of their threshold, spread 3 cells along
+        their pencil.  Returns (mask [n, 8, 8, 8] bool, OR-ed into `mask` when
+        given, number of near decisions)."""
+        self._check(U)
+        m = np.zeros((self.grid.n, 8, 8, 8), np.uint8) if mask is None else mask
+        assert m.dtype == np.uint8 and m.flags.c_contiguous and m.shape == (self.grid.n, 8, 8, 8)
+        if ids is not None:
+            ids = np.ascontiguousarray(ids, np.int32)
+        k = lib().oracle_margin_cells(ctypes.byref(self._g), None if ids is None else ids.ctypes.data,
+                                      0 if ids is None else len(ids), U.ctypes.data, 64.0 * eps, m.ctypes.data)
+        return m, int(k)
 
     def totals(self, U: np.ndarray) -> np.ndarray:
         self._check(U)

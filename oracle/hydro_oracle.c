@@ -295,6 +295,123 @@ int oracle_stage(const oracle_grid *g, const int32_t *ids, int32_t n_ids, const 
 }
 
 /* ------------------------------------------------------------------------- */
+/* Margin cells of the error metric: interior cells near a branch decision     */
+/* ------------------------------------------------------------------------- */
+
+/* The scheme above takes discrete decisions: the slope's extremum test
+ * (dl dr <= 0), the parabola's extremum test ((r - a)(a - l) <= 0), its two
+ * overshoot tests (lhs > rhs, -rhs > lhs), and the dual-energy test at every
+ * face side (e_i < eta E).  An implementation that rounds differently (another
+ * precision, another operation order) may decide such a test the other way
+ * when its operands are within rounding of the threshold.  A test counts as
+ * "near" when its distance from the threshold is at most tol times the
+ * magnitude its operands are computed from:
+ *   slope:     0 < |dl| <= tol S or 0 < |dr| <= tol S,  S = max |q| of the 3 cells;
+ *   extremum:  0 < |r - a| <= tol S or 0 < |a - l| <= tol S,  S = max(|a|, |l|, |r|);
+ *   overshoot: |lhs -+ rhs| <= tol |r - l| S;
+ *   dual energy: |e_i - eta E| <= tol (|E| + e_k).
+ * Differences that are exactly zero are not near: equal inputs stay equal in
+ * any precision.  A near test at pencil position m marks the interior cells of
+ * that pencil within 3 cells of m (the update stencil's reach along the pencil);
+ * a near face test marks those around both of its cells.  mask[s][512]
+ * ((k*8 + j)*8 + i) is OR-ed, for the listed sub-grids, with one bit per kind
+ * of test (MARGIN_* in the header); returns the number of near tests found.
+ * The three PPM tests decide between outcomes that meet where the test is
+ * exactly at its threshold (the limited slope and the pulled faces tend to the
+ * unlimited ones), so a decision taken the other way there moves a face value
+ * by about the distance from the threshold; the dual-energy test switches
+ * between two pressures that differ wherever tau^gamma and E - e_k disagree. */
+static int near_zero(double v, double tol_scale) { return v != 0.0 && fabs(v) <= tol_scale; }
+
+static double max3(double a, double b, double c) {
+  double m = fabs(a);
+  if (fabs(b) > m) m = fabs(b);
+  if (fabs(c) > m) m = fabs(c);
+  return m;
+}
+
+static void mark_pencil(unsigned char *mask, int d, int t1, int t2, int m, unsigned char bit) {
+  for (int c = m - 3; c <= m + 3; ++c) {
+    if (c < NG || c >= NG + NX) continue;
+    int i, j, k;
+    if (d == 0) { i = c; j = t1; k = t2; }
+    else if (d == 1) { i = t1; j = c; k = t2; }
+    else { i = t1; j = t2; k = c; }
+    mask[((k - NG) * NX + (j - NG)) * NX + (i - NG)] |= bit;
+  }
+}
+
+static int dual_energy_near(const double *U, double eta, double tol) {
+  double rho = U[F_RHO], sx = U[F_SX], sy = U[F_SX + 1], sz = U[F_SX + 2], E = U[F_EGAS];
+  double ek = 0.5 * (sx * sx + sy * sy + sz * sz) / rho;
+  double ei = E - ek;
+  return eta > 0.0 && fabs(ei - eta * E) <= tol * (fabs(E) + fabs(ek));
+}
+
+long oracle_margin_cells(const oracle_grid *g, const int32_t *ids, int32_t n_ids, const double *U, double tol,
+                         unsigned char *mask) {
+  int n = ids ? n_ids : g->n;
+  long found = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 4) reduction(+ : found)
+#endif
+  for (int t = 0; t < n; ++t) {
+    int s = ids ? ids[t] : t;
+    unsigned char *ms = mask + (size_t)s * NX * NX * NX;
+    for (int d = 0; d < 3; ++d)
+      for (int t2 = NG; t2 < NG + NX; ++t2)
+        for (int t1 = NG; t1 < NG + NX; ++t1) {
+          double aL[NF][NP], aR[NF][NP];
+          for (int f = 0; f < NF; ++f) {
+            double q[NP], face[NP];
+            for (int m = 0; m < NP; ++m) q[m] = U[pencil_at(s, f, d, t1, t2, m)];
+            for (int m = 1; m <= 12; ++m) {
+              double S = max3(q[m - 1], q[m], q[m + 1]);
+              if (near_zero(q[m] - q[m - 1], tol * S) || near_zero(q[m + 1] - q[m], tol * S)) {
+                mark_pencil(ms, d, t1, t2, m, MARGIN_SLOPE);
+                ++found;
+              }
+            }
+            /* the face values before the limiter, as the PPM above forms them */
+            double dm[NP];
+            for (int m = 1; m <= 12; ++m) dm[m] = limited_slope(q[m - 1], q[m], q[m + 1]);
+            for (int m = 1; m <= 11; ++m) face[m] = 0.5 * (q[m] + q[m + 1]) - (dm[m + 1] - dm[m]) / 6.0;
+            for (int m = 2; m <= 11; ++m) {
+              double a = q[m], l = face[m - 1], r = face[m];
+              double S = max3(a, l, r);
+              if (near_zero(r - a, tol * S) || near_zero(a - l, tol * S)) {
+                mark_pencil(ms, d, t1, t2, m, MARGIN_EXTREMUM);
+                ++found;
+              }
+              if (!((r - a) * (a - l) <= 0.0)) {
+                double da = r - l;
+                double lhs = da * (a - 0.5 * (l + r)), rhs = da * da / 6.0;
+                if (fabs(lhs - rhs) <= tol * fabs(da) * S || fabs(lhs + rhs) <= tol * fabs(da) * S) {
+                  mark_pencil(ms, d, t1, t2, m, MARGIN_OVERSHOOT);
+                  ++found;
+                }
+              }
+            }
+            oracle_ppm_pencil(q, aL[f], aR[f]);
+          }
+          for (int m = 2; m <= 10; ++m) {
+            double UL[NF], UR[NF];
+            for (int f = 0; f < NF; ++f) {
+              UL[f] = aR[f][m];
+              UR[f] = aL[f][m + 1];
+            }
+            if (dual_energy_near(UL, g->de_switch, tol) || dual_energy_near(UR, g->de_switch, tol)) {
+              mark_pencil(ms, d, t1, t2, m, MARGIN_DUAL_ENERGY);
+              mark_pencil(ms, d, t1, t2, m + 1, MARGIN_DUAL_ENERGY);
+              ++found;
+            }
+          }
+        }
+  }
+  return found;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Ghost fill                                                                 */
 /* ------------------------------------------------------------------------- */
 

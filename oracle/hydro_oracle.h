@@ -78,6 +78,19 @@ int oracle_stage(const oracle_grid *g, const int32_t *ids, int32_t n_ids, const 
                  double beta, double dt, double *Uout, double *max_speed, double *sub_amax, int nthreads,
                  int batch_all);
 
+/* Margin cells of the error metric (interior cells near a branch decision of
+ * the scheme, see the definition beside the function): OR-s one MARGIN_* bit
+ * per kind of decision into mask[s][512] ((k*8 + j)*8 + i) for the listed
+ * sub-grids (ids == NULL: all) of the padded state U (ghosts filled);
+ * tol = 64 eps of the compared precision.  Returns the number of near
+ * decisions found. */
+#define MARGIN_SLOPE 1       /* the slope's extremum test */
+#define MARGIN_EXTREMUM 2    /* the parabola's extremum test */
+#define MARGIN_OVERSHOOT 4   /* the parabola's two overshoot tests */
+#define MARGIN_DUAL_ENERGY 8 /* the dual-energy test at a face side */
+long oracle_margin_cells(const oracle_grid *g, const int32_t *ids, int32_t n_ids, const double *U, double tol,
+                         unsigned char *mask);
+
 /* Fill the six face ghost slabs of every sub-grid from the interiors. */
 int oracle_fill_ghosts(const oracle_grid *g, double *U);
 
