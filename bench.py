@@ -47,8 +47,7 @@ SHADOW_BYTES_PER_CELL = 137.5    # FP32 shadow: read 88 B of FP64 interior, writ
 TAU_RESYNC_BYTES_PER_CELL = 56.0  # tracer reset: read rho, s, E, tau (48 B), write tau (8 B)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 2 FP64 FMA/clk/SM at the 2070 MHz maximum clock
 # DRAM bytes (read + write) per cell-update of the mixed stage kernel from one ncu capture
-# (average of the three RK3 stage launches, profiles/stage_mixed_binary4k.md), valid only for
-# the kernel source it was taken on.
+# (average of the three RK3 stage launches), valid only for the kernel source it was taken on.
 STAGE_TRAFFIC = {"sha256_prefix": "026d5c1d4fcba5cf", "bytes_per_cell": 303.5,
                  "source": "ncu capture of the three RK3 stage launches on the 4097-leaf reduced binary octree "
                            "(average), scaled by cells"}

@@ -42,7 +42,7 @@ typedef enum {
   HYDRO_ERR_CUDA = -2,      /* a CUDA runtime call failed; see hydro_last_error */
   HYDRO_ERR_NOMEM = -3,     /* device or host allocation failed in hydro_create */
   HYDRO_ERR_NONFINITE = -4, /* an updated value is not finite, or a density <= 0 */
-  HYDRO_ERR_TIMEOUT = -5,   /* reserved: a bounded device wait gave up */
+  HYDRO_ERR_TIMEOUT = -5,   /* a bounded device wait gave up (HYDRO_PARAM_WAIT_LIMIT) */
   HYDRO_ERR_STATE = -6      /* call not valid in the handle's current state */
 } hydro_status;
 
@@ -134,7 +134,18 @@ int hydro_create(const hydro_grid_desc *desc, hydro_handle **out);
  * takes the flux ((F00 + F10) + (F01 + F11)) / 4 of the fine faces over it, as
  * the fine neighbours computed them in the same call, so an AMR step conserves
  * to round-off; a quadrant whose fine neighbour is not listed keeps the coarse
- * flux.  It runs as a second launch after the stage kernel. */
+ * flux.  FP64 handles correct inside the stage kernel, before the flux
+ * differences, as the plain statement does: the stage takes the listed
+ * sub-grids finest level first (a one-CTA pass orders the batch), each fine
+ * sub-grid publishes its boundary fluxes with a flag, and a coarse one waits
+ * for them (bounded by HYDRO_PARAM_WAIT_LIMIT; HYDRO_ERR_TIMEOUT from
+ * hydro_sync when a wait runs out).  With every operation rounded as written
+ * (no contraction, IEEE quotients), an FP64 stage equals a plain FP64
+ * evaluation of the scheme bit for bit, except at faces where the dual-energy
+ * switch evaluates tau^gamma (pow, correctly rounded by no math library).
+ * Mixed-precision handles correct in a second launch after the stage kernel,
+ * adding the exact float-pair difference (mean - own flux) to what the stage
+ * wrote. */
 int hydro_step(hydro_handle *h, const hydro_batch *batch, const double *U_in, const double *U0, double beta,
                double dt, double *U_out, double *d_max_speed, void *stream);
 
@@ -299,8 +310,13 @@ int hydro_tau_resync(hydro_handle *h, double *U, float *S, void *stream);
  * Needs no handle and allocates nothing: the partial sums live in one fixed
  * device array inside the library (HYDRO_TOTALS_NOALLOC_MAX_SUBGRIDS * 11 * 3
  * words of 8 bytes, 17.3 MB, held on every GPU that loads the library until
- * the process exits).  The first call on a device looks up that array's device address
- * with the device current; make that first call before any stream capture.
+ * the process exits).  Each call looks up that array's device address on the
+ * current device; a call made while its stream is being captured reuses the
+ * address found by the last uncaptured call on that device instead, so make
+ * one call on each device before capturing it.  A device reset (or any other
+ * unload of the module) moves the array: the next uncaptured call finds the
+ * new address, while a graph captured before the reset keeps the old one and
+ * must be captured again.
  * All calls share the array: calls whose work overlaps on the GPU (different
  * streams, or the same stream from several threads without ordering) race and
  * must not be issued.  Returns HYDRO_OK, HYDRO_ERR_INVALID or HYDRO_ERR_CUDA. */
@@ -326,7 +342,13 @@ typedef enum {
   HYDRO_PARAM_STAGE_CTAS_PER_SM = 0, /* persistent CTAs per SM for the stage kernel, 1..8 (0 = auto) */
   HYDRO_PARAM_GHOST_THREADS = 1,     /* threads per CTA of the ghost-fill kernel, 64..1024 */
   HYDRO_PARAM_REFLUX = 2,            /* coarse-fine flux correction: 1 (default) or 0 */
-  HYDRO_PARAM_TAU_RESYNC = 3         /* dual-energy tracer reset after every RK3 step: 0 (default) or 1 */
+  HYDRO_PARAM_TAU_RESYNC = 3,        /* dual-energy tracer reset after every RK3 step: 0 (default) or 1 */
+  HYDRO_PARAM_WAIT_LIMIT = 4,        /* clock cycles a stage CTA waits for a finer neighbour's fluxes, >= 1
+                                        (default 2^31 - 1, about a second); a wait that runs out makes the
+                                        stage stop taking work and hydro_sync return HYDRO_ERR_TIMEOUT */
+  HYDRO_PARAM_QUEUE_ORDER = 5,       /* 0 (default): stages take finer levels first; 1: the batch's own order
+                                        (waits may then be for sub-grids not yet taken) */
+  HYDRO_PARAM_STAGE_GRID = 6         /* stage kernel CTAs in total, >= 1 (0 = the default from the occupancy) */
 } hydro_param;
 
 /* Release the handle and its device scratch (waits for its work first). */

@@ -2,6 +2,6 @@
 
 Modules: ``workloads`` (seeded synthetic inputs), ``hydro`` (binding of the C
 ABI in include/hydro.h), ``build`` (in-tree nvcc build of libhydro.so),
-``driver`` (lagged-CFL time stepping on the device), ``tune`` (launch-shape
-autotuner).
+``partition`` (Morton-range partition and proxy exchange of the sharded step),
+``tune`` (launch-shape autotuner).
 """

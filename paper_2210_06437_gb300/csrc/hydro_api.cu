@@ -12,6 +12,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <utility>
 #include <vector>
@@ -74,13 +75,25 @@ struct hydro_handle {
   double* d_diag = nullptr;            // [12] diagnostics sums
   unsigned long long* d_ms_tmp = nullptr;  // [2] speeds of RK stages 2 and 3
   float* d_shadow[3] = {nullptr, nullptr, nullptr};  // mixed precision: FP32 shadows [n][NF][576]
-  // coarse-fine flux correction
+  // coarse-fine flux correction: FP64 inside the stage kernel, mixed precision
+  // in a pass after it
   int tau_resync = 0;                  // dual-energy tracer reset after every RK3 step
   int reflux = 1;
-  int n_cf = 0;                        // coarse sub-grids with a finer face neighbour
-  int32_t* d_cf = nullptr;             // [n_cf][CF_ENTRY]
+  int n_cf = 0;                        // faces onto a finer neighbour
+  int n_cf_list = 0;                   // mixed: coarse sub-grids with a finer face neighbour
+  int32_t* d_cf = nullptr;             // mixed: [n_cf_list][CF_ENTRY] correction records
+  int32_t* d_fb_stamp = nullptr;       // mixed: [n] call id of the last stage that advanced the sub-grid
+  int n_levels = 1;                    // distinct cell widths
+  int queue_order = 0;                 // 0: finest level first; 1: the batch's own order
+  int grid_cap = 0;                    // stage CTAs (0: from the occupancy)
+  long long wait_limit = 0x7fffffffll;  // clock cycles a CTA waits for a neighbour's fluxes
+  int8_t* d_level = nullptr;           // [n] level rank, 0 = finest
+  int32_t* d_order_all = nullptr;      // [n] every sub-grid, finest level first
+  int32_t* d_order = nullptr;          // [n] the current batch, finest level first
+  int32_t* d_member = nullptr;         // [n] call id of the last batch listing the sub-grid
   void* d_fb = nullptr;                // [n][6][NF][64] exported boundary fluxes (T)
-  int32_t* d_fb_stamp = nullptr;       // [n]
+  int32_t* d_cf_flag = nullptr;        // [n] export progress of the current stage
+  int* d_abort = nullptr;              // a bounded wait gave up during the current stage
   int32_t call_counter = 0;
   cudaStream_t cap_stream = nullptr;
   cudaStream_t last_stream = nullptr;
@@ -129,8 +142,14 @@ void free_all(hydro_handle* h) {
   cudaFree(h->d_ms_tmp);
   for (float* p : h->d_shadow) cudaFree(p);
   cudaFree(h->d_cf);
-  cudaFree(h->d_fb);
   cudaFree(h->d_fb_stamp);
+  cudaFree(h->d_level);
+  cudaFree(h->d_order_all);
+  cudaFree(h->d_order);
+  cudaFree(h->d_member);
+  cudaFree(h->d_fb);
+  cudaFree(h->d_cf_flag);
+  cudaFree(h->d_abort);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
 }
 
@@ -164,7 +183,7 @@ int check_batch(hydro_handle* h, const hydro_batch* b) {
 
 int stage_grid(hydro_handle* h, int n_items) {
   int per_sm = h->ctas_per_sm > 0 ? h->ctas_per_sm : h->occupancy;
-  int grid = h->sm_count * per_sm;
+  int grid = h->grid_cap > 0 ? h->grid_cap : h->sm_count * per_sm;
   return n_items < grid ? (n_items > 0 ? n_items : 1) : grid;
 }
 
@@ -174,7 +193,7 @@ int stage_grid(hydro_handle* h, int n_items) {
 int enqueue_stage(hydro_handle* h, const int32_t* ids, int n_items, const double* Uin, const float* Sin,
                   const double* U0, double beta, double dt, const double* dt_dev, double* Uout, float* Sout,
                   unsigned long long* ms, int queue_slot, cudaStream_t st, int mode = 0, const double* Din = nullptr,
-                  double* Dout = nullptr, const float* S0 = nullptr) {
+                  double* Dout = nullptr, const float* S0 = nullptr, bool all_items = false) {
   CUDA_TRY(h, cudaMemsetAsync(ms, 0, 2 * sizeof(unsigned long long), st));
   if (n_items == 0) return HYDRO_OK;
   CUDA_TRY(h, cudaMemsetAsync(h->d_queue + queue_slot, 0, sizeof(unsigned int), st));
@@ -198,7 +217,6 @@ int enqueue_stage(hydro_handle* h, const int32_t* ids, int n_items, const double
   a.Uout = Uout;
   a.Sin = Sin;
   a.Sout = Sout;
-  a.ids = ids;
   a.n_items = n_items;
   a.n_sub = h->n;
   a.dx = h->d_dx;
@@ -215,25 +233,49 @@ int enqueue_stage(hydro_handle* h, const int32_t* ids, int n_items, const double
   a.queue = h->d_queue + queue_slot;
   a.err = h->d_err;
   a.max_speed = ms;
-  const bool reflux = h->reflux && h->n_cf > 0;
-  if (reflux) {
+  const bool mixed = h->precision == HYDRO_MIXED;
+  const bool correct = h->reflux && h->n_cf > 0;
+  if (correct && mixed) {
+    // the stage exports its coarse-fine fluxes; a pass after it corrects
     a.fb = h->d_fb;
     a.fb_stamp = h->d_fb_stamp;
     a.call_id = ++h->call_counter;
+  } else if (correct) {
+    // FP64: the correction runs inside the stage: a queue in level order
+    // (finest first), the batch's members, fresh export flags
+    CUDA_TRY(h, cudaMemsetAsync(h->d_cf_flag, 0, sizeof(int32_t) * (size_t)h->n, st));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_abort, 0, sizeof(int), st));
+    a.call_id = ++h->call_counter;
+    if (all_items) {
+      a.member = nullptr;  // the batch lists every sub-grid
+      if (h->queue_order == 0) ids = h->d_order_all;
+    } else {
+      cudaError_t e = launch_order_batch(ids, n_items, h->n, h->d_level, h->n_levels, h->d_order, h->d_member,
+                                         a.call_id, st);
+      if (e != cudaSuccess) return cuda_fail(h, e, "queue order kernel launch");
+      h->launches += 1;
+      a.member = h->d_member;
+      if (h->queue_order == 0) ids = h->d_order;
+    }
+    a.fb = h->d_fb;
+    a.cf_flag = h->d_cf_flag;
+    a.abort_word = h->d_abort;
+    a.wait_limit = h->wait_limit;
   }
+  a.ids = ids;
   const int grid = stage_grid(h, n_items);
-  cudaError_t e = h->precision == HYDRO_MIXED ? launch_stage_mixed(a, grid, st) : launch_stage_fp64(a, grid, st);
+  cudaError_t e = mixed ? launch_stage_mixed(a, grid, st) : launch_stage_fp64(a, grid, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "stage kernel launch");
   h->launches += 1;
-  if (reflux) {
+  if (correct && mixed) {
     RefluxArgs r;
     std::memset(&r, 0, sizeof(r));
     r.cf = h->d_cf;
-    r.n_list = h->n_cf;
+    r.n_list = h->n_cf_list;
     r.fb = h->d_fb;
     r.fb_stamp = h->d_fb_stamp;
     r.call_id = a.call_id;
-    r.inv_dx = h->d_inv_dx;
+    r.dx = h->d_dx;
     r.dt = dt;
     r.dt_dev = dt_dev;
     r.mode = mode;
@@ -243,7 +285,7 @@ int enqueue_stage(hydro_handle* h, const int32_t* ids, int n_items, const double
     r.S0 = S0;
     r.Sout = Sout;
     r.err = h->d_err;
-    e = h->precision == HYDRO_MIXED ? launch_reflux_mixed(r, st) : launch_reflux_fp64(r, st);
+    e = launch_reflux_mixed(r, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "flux correction kernel launch");
     h->launches += 1;
   }
@@ -307,6 +349,12 @@ int hydro_create(const hydro_grid_desc* d, hydro_handle** out) {
           if (nb[q] < 0 || nb[q] >= n) return HYDRO_ERR_INVALID;
     }
   }
+  {
+    // the queue orders sub-grids by cell width: at most 32 distinct widths
+    std::vector<double> widths(d->dx, d->dx + n);
+    std::sort(widths.begin(), widths.end());
+    if (std::unique(widths.begin(), widths.end()) - widths.begin() > 32) return HYDRO_ERR_INVALID;
+  }
   hydro_handle* h = new (std::nothrow) hydro_handle();
   if (!h) return HYDRO_ERR_NOMEM;
   h->n = n;
@@ -332,25 +380,47 @@ int hydro_create(const hydro_grid_desc* d, hydro_handle** out) {
   ok = ok && cudaMalloc(&h->d_dt, sizeof(double)) == cudaSuccess;
   ok = ok && cudaMalloc(&h->d_diag, 12 * sizeof(double)) == cudaSuccess;
   ok = ok && cudaMalloc(&h->d_ms_tmp, 2 * sizeof(unsigned long long)) == cudaSuccess;
+  std::vector<int8_t> level(n);
+  std::vector<int32_t> order(n);
+  std::vector<int32_t> cf;
   {
-    std::vector<int32_t> cf;
-    for (int s = 0; s < n; ++s) {
-      bool any = false;
-      for (int f = 0; f < 6; ++f) any = any || d->neighbor_rel[s * 6 + f] == 1;
-      if (!any) continue;
-      cf.push_back(s);
-      for (int f = 0; f < 6; ++f)
-        for (int q = 0; q < 4; ++q)
-          cf.push_back(d->neighbor_rel[s * 6 + f] == 1 ? d->neighbor[(s * 6 + f) * 4 + q] : -1);
-    }
-    h->n_cf = (int)(cf.size() / CF_ENTRY);
-    if (h->n_cf > 0) {
-      const size_t tsize = d->precision == HYDRO_MIXED ? sizeof(float) : sizeof(double);
+    // level ranks from the cell widths (0 = finest) and the queue of every
+    // sub-grid in level order, for the in-stage coarse-fine correction
+    for (int s = 0; s < n; ++s)
+      for (int f = 0; f < 6; ++f) h->n_cf += d->neighbor_rel[s * 6 + f] == 1 ? 1 : 0;
+    std::vector<double> widths(d->dx, d->dx + n);
+    std::sort(widths.begin(), widths.end());
+    widths.erase(std::unique(widths.begin(), widths.end()), widths.end());
+    h->n_levels = (int)widths.size();
+    for (int s = 0; s < n; ++s)
+      level[s] = (int8_t)(std::lower_bound(widths.begin(), widths.end(), d->dx[s]) - widths.begin());
+    // the queue of a whole-grid stage: every sub-grid, finest level first
+    // (ids ascending within a level)
+    for (int s = 0; s < n; ++s) order[s] = s;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return level[x] < level[y]; });
+    if (h->n_cf > 0 && d->precision == HYDRO_MIXED) {
+      for (int s = 0; s < n; ++s) {
+        bool any = false;
+        for (int f = 0; f < 6; ++f) any = any || d->neighbor_rel[s * 6 + f] == 1;
+        if (!any) continue;
+        cf.push_back(s);
+        for (int f = 0; f < 6; ++f)
+          for (int q = 0; q < 4; ++q)
+            cf.push_back(d->neighbor_rel[s * 6 + f] == 1 ? d->neighbor[(s * 6 + f) * 4 + q] : -1);
+      }
+      h->n_cf_list = (int)(cf.size() / CF_ENTRY);
       ok = ok && cudaMalloc(&h->d_cf, sizeof(int32_t) * cf.size()) == cudaSuccess;
-      ok = ok && cudaMalloc(&h->d_fb, tsize * (size_t)n * 6 * NF * NPEN) == cudaSuccess;
+      ok = ok && cudaMalloc(&h->d_fb, sizeof(float) * (size_t)n * 6 * NF * NPEN) == cudaSuccess;
       ok = ok && cudaMalloc(&h->d_fb_stamp, sizeof(int32_t) * n) == cudaSuccess;
-      ok = ok && cudaMemcpy(h->d_cf, cf.data(), sizeof(int32_t) * cf.size(), cudaMemcpyHostToDevice) == cudaSuccess;
-      ok = ok && cudaMemset(h->d_fb_stamp, 0, sizeof(int32_t) * n) == cudaSuccess;
+    } else if (h->n_cf > 0) {
+      const size_t tsize = sizeof(double);
+      ok = ok && cudaMalloc(&h->d_level, n) == cudaSuccess;
+      ok = ok && cudaMalloc(&h->d_order_all, sizeof(int32_t) * n) == cudaSuccess;
+      ok = ok && cudaMalloc(&h->d_order, sizeof(int32_t) * n) == cudaSuccess;
+      ok = ok && cudaMalloc(&h->d_member, sizeof(int32_t) * n) == cudaSuccess;
+      ok = ok && cudaMalloc(&h->d_fb, tsize * (size_t)n * 6 * NF * NPEN) == cudaSuccess;
+      ok = ok && cudaMalloc(&h->d_cf_flag, sizeof(int32_t) * n) == cudaSuccess;
+      ok = ok && cudaMalloc(&h->d_abort, sizeof(int)) == cudaSuccess;
     }
   }
   if (d->precision == HYDRO_MIXED)
@@ -372,6 +442,16 @@ int hydro_create(const hydro_grid_desc* d, hydro_handle** out) {
   ok = ok && cudaMemcpy(h->d_rel, d->neighbor_rel, n * 6, cudaMemcpyHostToDevice) == cudaSuccess;
   ok = ok && cudaMemcpy(h->d_oct, d->octant, n, cudaMemcpyHostToDevice) == cudaSuccess;
   ok = ok && cudaMemset(h->d_err, 0, sizeof(int)) == cudaSuccess;
+  if (h->n_cf > 0 && d->precision == HYDRO_MIXED) {
+    ok = ok && cudaMemcpy(h->d_cf, cf.data(), sizeof(int32_t) * cf.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemset(h->d_fb_stamp, 0, sizeof(int32_t) * n) == cudaSuccess;
+  } else if (h->n_cf > 0) {
+    ok = ok && cudaMemcpy(h->d_level, level.data(), n, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(h->d_order_all, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemset(h->d_member, 0, sizeof(int32_t) * n) == cudaSuccess;
+    ok = ok && cudaMemset(h->d_cf_flag, 0, sizeof(int32_t) * n) == cudaSuccess;
+    ok = ok && cudaMemset(h->d_abort, 0, sizeof(int)) == cudaSuccess;
+  }
   ok = ok && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
   h->occupancy = h->precision == HYDRO_MIXED ? stage_blocks_per_sm_mixed() : stage_blocks_per_sm_fp64();
   if (!ok) {
@@ -534,19 +614,24 @@ int enqueue_rk3_stages(hydro_handle* h, const int32_t* ids, int ni, double* U, d
   int rc;
   if (h->precision == HYDRO_MIXED) {
     float *A = h->d_shadow[0], *B = h->d_shadow[1], *C = h->d_shadow[2];
-    rc = enqueue_stage(h, ids, ni, U, A, nullptr, 1.0, 0.0, h->d_dt, nullptr, B, ms, 0, cs, 1, nullptr, s1, A);
+    rc = enqueue_stage(h, ids, ni, U, A, nullptr, 1.0, 0.0, h->d_dt, nullptr, B, ms, 0, cs, 1, nullptr, s1, A, true);
     if (!rc)
-      rc = enqueue_stage(h, ids, ni, U, B, nullptr, 1.0, 0.0, h->d_dt, nullptr, C, h->d_ms_tmp, 1, cs, 2, s1, s2, A);
+      rc = enqueue_stage(h, ids, ni, U, B, nullptr, 1.0, 0.0, h->d_dt, nullptr, C, h->d_ms_tmp, 1, cs, 2, s1, s2, A,
+                         true);
     if (!rc)
       rc = enqueue_stage(h, ids, ni, U, C, nullptr, 1.0, 0.0, h->d_dt, U, write_next ? A : nullptr, h->d_ms_tmp, 2,
-                         cs, 3, s2, nullptr, A);
+                         cs, 3, s2, nullptr, A, true);
     if (!rc && h->tau_resync) rc = enqueue_tau_resync(h, U, write_next ? A : nullptr, cs);
     return rc;
   }
-  rc = enqueue_stage(h, ids, ni, U, nullptr, nullptr, 1.0, 0.0, h->d_dt, s1, nullptr, ms, 0, cs);
-  if (!rc) rc = enqueue_stage(h, ids, ni, s1, nullptr, U, 0.25, 0.0, h->d_dt, s2, nullptr, h->d_ms_tmp, 1, cs);
+  rc = enqueue_stage(h, ids, ni, U, nullptr, nullptr, 1.0, 0.0, h->d_dt, s1, nullptr, ms, 0, cs, 0, nullptr, nullptr,
+                     nullptr, true);
   if (!rc)
-    rc = enqueue_stage(h, ids, ni, s2, nullptr, U, 2.0 / 3.0, 0.0, h->d_dt, U, nullptr, h->d_ms_tmp, 2, cs);
+    rc = enqueue_stage(h, ids, ni, s1, nullptr, U, 0.25, 0.0, h->d_dt, s2, nullptr, h->d_ms_tmp, 1, cs, 0, nullptr,
+                       nullptr, nullptr, true);
+  if (!rc)
+    rc = enqueue_stage(h, ids, ni, s2, nullptr, U, 2.0 / 3.0, 0.0, h->d_dt, U, nullptr, h->d_ms_tmp, 2, cs, 0, nullptr,
+                       nullptr, nullptr, true);
   if (!rc && h->tau_resync) rc = enqueue_tau_resync(h, U, nullptr, cs);
   return rc;
 }
@@ -738,6 +823,8 @@ int hydro_sync(hydro_handle* h) {
   int err = 0;
   CUDA_TRY(h, cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   CUDA_TRY(h, cudaMemset(h->d_err, 0, sizeof(int)));
+  if (err & ERRBIT_TIMEOUT)
+    return fail(h, HYDRO_ERR_TIMEOUT, "a stage gave up waiting for a finer neighbour's exported fluxes");
   if (err & ERRBIT_BAD_ID) return fail(h, HYDRO_ERR_INVALID, "a sub-grid id was out of range");
   if (err & ERRBIT_NONFINITE) return fail(h, HYDRO_ERR_NONFINITE, "non-finite value or non-positive density");
   return HYDRO_OK;
@@ -766,6 +853,27 @@ int hydro_set_param(hydro_handle* h, int32_t key, int32_t value) {
   if (key == HYDRO_PARAM_TAU_RESYNC) {
     if (value != 0 && value != 1) return fail(h, HYDRO_ERR_INVALID, "tau resync must be 0 or 1");
     h->tau_resync = value;
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+    return HYDRO_OK;
+  }
+  if (key == HYDRO_PARAM_WAIT_LIMIT) {
+    if (value < 1) return fail(h, HYDRO_ERR_INVALID, "wait limit must be >= 1 clock cycle");
+    h->wait_limit = value;
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+    return HYDRO_OK;
+  }
+  if (key == HYDRO_PARAM_QUEUE_ORDER) {
+    if (value != 0 && value != 1) return fail(h, HYDRO_ERR_INVALID, "queue order must be 0 or 1");
+    h->queue_order = value;
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+    return HYDRO_OK;
+  }
+  if (key == HYDRO_PARAM_STAGE_GRID) {
+    if (value < 0) return fail(h, HYDRO_ERR_INVALID, "stage grid must be >= 0");
+    h->grid_cap = value;
     for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
     h->graphs.clear();
     return HYDRO_OK;

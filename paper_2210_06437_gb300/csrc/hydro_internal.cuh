@@ -24,6 +24,7 @@ constexpr int F_RHO = 0, F_SX = 1, F_EGAS = 4, F_TAU = 5;
 // device error word bits
 constexpr int ERRBIT_NONFINITE = 1;
 constexpr int ERRBIT_BAD_ID = 2;
+constexpr int ERRBIT_TIMEOUT = 4;   // a bounded wait for a neighbour's exported fluxes gave up
 
 __host__ __device__ inline size_t field_offset(int s, int f) { return ((size_t)s * NF + f) * NP3; }
 
@@ -70,20 +71,40 @@ struct StageArgs {
   const double* Din;     // increments as float pairs, packed interiors [s][f][512]
   double* Dout;
   const float* S0;
-  // coarse-fine flux correction: when fb is set, each sub-grid stamps
-  // fb_stamp[s] = call_id and stores its fluxes on every coarse-fine face:
-  // fb[(s*6 + face)][f][pencil] (T), pencil = t2*8 + t1 across the face
+  // Coarse-fine flux correction (when fb is set).
+  // Mixed precision: every sub-grid stamps fb_stamp[s] = call_id and stores
+  // its fluxes on every coarse-fine face, fb[(s*6 + face)][f][pencil] (T),
+  // pencil = t2*8 + t1 across the face; a separate pass (reflux_kernel)
+  // corrects the coarse side after the stage.
+  // FP64: the correction runs inside the stage.  A sub-grid
+  // with a coarser face neighbour stores that face's fluxes,
+  // fb[(s*6 + face)][f][pencil] (T), pencil = t2*8 + t1 across the face, and
+  // after each direction d's faces raises cf_flag[s] to 3 call_id + d + 1
+  // (release).  A sub-grid with finer face neighbours waits (acquire, bounded
+  // by wait_limit clock cycles) until each fine neighbour advanced by this call
+  // has exported direction d, then takes the mean of the four fine fluxes over
+  // each coarse boundary face.  The queue lists finer sub-grids first, so a
+  // wait is only ever for an item taken earlier by a running CTA.  member[s] ==
+  // call_id marks the sub-grids of the call (member == nullptr: all of them).
+  // A wait that gives up sets ERRBIT_TIMEOUT and *abort_word, after which
+  // every CTA stops taking work.  (The queue order of a whole-grid stage is
+  // by level, finest first: measured faster than a Morton order that moves
+  // each sub-grid's finer neighbours just before it, whose waits are longer.)
   void* fb;
-  int32_t* fb_stamp;
+  int32_t* fb_stamp;     // mixed precision only
+  int32_t* cf_flag;      // FP64 only (also member, abort_word, wait_limit)
+  const int32_t* member;
+  int* abort_word;
+  long long wait_limit;
   int32_t call_id;
 };
 
-// Coarse-fine flux correction after a stage (one CTA per coarse sub-grid of
-// `list`): each coarse boundary face flux is replaced by the mean of the four
-// fine fluxes over it, for the finer neighbours advanced by the same call.
-// One record per coarse sub-grid with at least one finer face neighbour: its
-// id, then for each face and quadrant (face * 4 + q) the fine neighbour's id,
-// -1 where the face does not meet finer sub-grids.
+// Coarse-fine flux correction after a mixed-precision stage (one CTA per
+// coarse sub-grid of `list`): each coarse boundary face flux is replaced by the
+// mean of the four fine fluxes over it, for the finer neighbours advanced by
+// the same call.  One record per coarse sub-grid with at least one finer face
+// neighbour: its id, then for each face and quadrant (face * 4 + q) the fine
+// neighbour's id, -1 where the face does not meet finer sub-grids.
 constexpr int CF_ENTRY = 25;
 
 struct RefluxArgs {
@@ -92,7 +113,7 @@ struct RefluxArgs {
   const void* fb;        // stage flux export (see StageArgs)
   const int32_t* fb_stamp;
   int32_t call_id;
-  const double* inv_dx;
+  const double* dx;
   double dt;
   const double* dt_dev;
   int32_t mode;          // the stage's mode (StageArgs)
@@ -127,8 +148,12 @@ cudaError_t launch_shadow(const double* U, float* S, int n, cudaStream_t st);
 // Dual-energy tracer reset of every sub-grid of U (and the tau field of its
 // shadow S when mixed and S is not null); nothing when eta <= 0.
 cudaError_t launch_tau_resync(double* U, float* S, int n, double gamma, double eta, bool mixed, cudaStream_t st);
-cudaError_t launch_reflux_fp64(const RefluxArgs& r, cudaStream_t st);
 cudaError_t launch_reflux_mixed(const RefluxArgs& r, cudaStream_t st);
+// The work queue of a stage over a batch: the batch's ids ordered finest
+// level first (level_rank[s], 0 = finest; ids outside [0, n) first), into
+// `order`, and member[id] = call_id for every valid id.  One CTA.
+cudaError_t launch_order_batch(const int32_t* ids, int n_items, int n_sub, const int8_t* level_rank, int n_levels,
+                               int32_t* order, int32_t* member, int32_t call_id, cudaStream_t st);
 cudaError_t launch_pack(const double* U, double* P, int n, cudaStream_t st);
 cudaError_t launch_unpack(const double* P, double* U, int n, cudaStream_t st);
 cudaError_t launch_stage_fp64(const StageArgs& a, int grid, cudaStream_t st);

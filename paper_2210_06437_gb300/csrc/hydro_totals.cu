@@ -17,6 +17,7 @@
 //   pass 3: per field, the chunk sums combined in a fixed order.
 // No atomics anywhere, so the result is bit-reproducible.
 #include "hydro_internal.cuh"
+#include "hydro_sums.cuh"
 
 namespace hydro {
 namespace {
@@ -84,8 +85,7 @@ __device__ __forceinline__ void i128_to_dd(__int128 v, int e2, double& hi, doubl
 }
 
 // pass 1 output per (sub-grid, field): the 128-bit sum (low, high word) and E
-// (0x7ff: a value is not finite).
-constexpr int PARTIAL_WORDS = 3;
+// (0x7ff: a value is not finite), see hydro_sums.cuh.
 
 // Per-cell quantity q of sub-grid s at interior cell c = (k*8 + j)*8 + i.
 // Totals: the 11 fields.
@@ -136,45 +136,7 @@ __global__ void __launch_bounds__(TT) totals_subgrid(const Q Qf, int n, unsigned
   const int lane = threadIdx.x & 31;
   if (gw >= n * NQ) return;
   const int s = gw / NQ, f = gw - s * NQ;
-  unsigned long long b[16];
-  unsigned emax = 1;  // zero and subnormals count as exponent 1
-#pragma unroll
-  for (int r = 0; r < 16; ++r) {
-    const int c = lane + 32 * r;
-    b[r] = (unsigned long long)__double_as_longlong(Qf(s, f, c));
-    const unsigned e = (unsigned)(b[r] >> 52) & 0x7ffu;
-    emax = e > emax ? e : emax;
-  }
-  emax = __reduce_max_sync(0xffffffffu, emax);
-  __int128 acc = 0;
-#pragma unroll
-  for (int r = 0; r < 16; ++r) {
-    unsigned e = (unsigned)(b[r] >> 52) & 0x7ffu;
-    unsigned long long m = b[r] & 0x000fffffffffffffull;
-    if (e)
-      m |= 0x0010000000000000ull;
-    else
-      e = 1;
-    const int sh = 63 - (int)(emax - e);  // bit position of the significand's last bit
-    unsigned __int128 F;
-    if (sh >= 0)
-      F = (unsigned __int128)m << sh;
-    else
-      F = sh > -64 ? (unsigned __int128)(m >> (-sh)) : (unsigned __int128)0;
-    acc += (b[r] >> 63) ? -(__int128)F : (__int128)F;
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long lo = __shfl_down_sync(0xffffffffu, (unsigned long long)acc, o);
-    const unsigned long long hi = __shfl_down_sync(0xffffffffu, (unsigned long long)((unsigned __int128)acc >> 64), o);
-    acc += (__int128)(((unsigned __int128)hi << 64) | lo);
-  }
-  if (lane == 0) {
-    unsigned long long* o = partial + ((size_t)s * NQ + f) * PARTIAL_WORDS;
-    o[0] = (unsigned long long)acc;
-    o[1] = (unsigned long long)((unsigned __int128)acc >> 64);
-    o[2] = emax;
-  }
+  warp_exact_sum([&](int r) { return Qf(s, f, lane + 32 * r); }, partial + ((size_t)s * NQ + f) * PARTIAL_WORDS);
 }
 
 // Sub-grid partial dx^3 * sum as a double pair (p, e), p + e the exact value
@@ -300,15 +262,21 @@ std::mutex g_noalloc_mu;
 constexpr int kMaxDevices = 64;
 double* g_noalloc_ptr[kMaxDevices] = {nullptr};
 
-// Device address of the scratch array on the current device, looked up once
-// per device (with that device current) and cached.
-cudaError_t noalloc_scratch(double** out) {
+// Device address of the scratch array on the current device.  The host-side
+// name of the array is only a stand-in, so the address is looked up with the
+// device current.  It is looked up again on every call whose stream is not
+// being captured (cheap, and correct after a device reset reloads the module);
+// a captured call reuses the last address found on that device.
+cudaError_t noalloc_scratch(cudaStream_t st, double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(st, &cap);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone || !g_noalloc_ptr[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_partial);
     if (e != cudaSuccess) return e;
@@ -326,7 +294,7 @@ extern "C" int hydro_totals_noalloc(const double* U, const double* d_dx, int32_t
   if (((uintptr_t)U % 16) || ((uintptr_t)d_dx % 8) || ((uintptr_t)d_totals % 8)) return HYDRO_ERR_INVALID;
   if (n_subgrids < 1 || n_subgrids > HYDRO_TOTALS_NOALLOC_MAX_SUBGRIDS) return HYDRO_ERR_INVALID;
   double* scratch = nullptr;
-  if (noalloc_scratch(&scratch) != cudaSuccess) return HYDRO_ERR_CUDA;
+  if (noalloc_scratch((cudaStream_t)stream, &scratch) != cudaSuccess) return HYDRO_ERR_CUDA;
   // every partial the final pass reads is written first by the partial pass,
   // so the stale contents of the shared array never reach the result
   if (hydro::launch_totals(U, n_subgrids, d_dx, scratch, d_totals, (cudaStream_t)stream) != cudaSuccess)

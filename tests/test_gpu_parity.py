@@ -17,6 +17,7 @@ import pytest
 
 from paper_2210_06437_gb300 import workloads as W
 from tests import helpers as H
+from tests import r12 as R
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -755,3 +756,113 @@ def test_rk3_step_with_tau_resync_matches_oracle(hydro, oracle_mod, prec):
     g.sync()
     err = field_errors(_host(Ud), ref)
     assert np.all(err <= TOL[prec]), err
+
+
+# ---------------------------------------------------------------------------
+# the FP64 path evaluates the scheme in the reference order: bit for bit
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("form,de_switch", [(0, 1e-3), (1, 1e-3), (0, 0.0)])
+@pytest.mark.parametrize("cfg", [1, 2])
+def test_fp64_bit_identical_to_oracle(hydro, oracle_mod, cfg, form, de_switch):
+    """On grids without coarse-fine faces the FP64 stage reproduces the oracle
+    bit for bit: one blended stage (beta = 1/4 against a perturbed U0), its
+    maximum speeds, and one full SSP-RK3 step.  (The dual-energy branch uses
+    pow, which is not correctly rounded on either side; these states never
+    take it.)"""
+    w = W.config(cfg)
+    o = oracle_mod.Oracle(w.grid, flux_form=form, de_switch=de_switch)
+    U = w.state()
+    o.fill_ghosts(U)
+    _, ms, st = o.stage(U, 0.0)
+    dt = 0.4 / ms[1]
+    U0 = U.copy()
+    U0[IN] *= 1.0 + 1e-3 * np.sin(np.arange(U0[IN].size).reshape(U0[IN].shape))
+    ref, ms_o, st = o.stage(U, dt, U0=U0, beta=0.25)
+    assert st == 0
+    g = hydro.HydroGrid(w.grid, precision="fp64", flux_form=form, de_switch=de_switch)
+    out, msd = g.step(_dev(w.state()), dt, U0=_dev(U0), beta=0.25, U_out=_dev(w.state()))
+    g.sync()
+    assert np.array_equal(_host(out)[IN], ref[IN])
+    assert np.array_equal(msd.cpu().numpy(), ms_o)
+    ref3, _, st = o.rk3_step(U, dt)
+    Ud = _dev(w.state())
+    g.rk3_step(Ud, dt, torch.empty_like(Ud), torch.empty_like(Ud))
+    g.sync()
+    assert np.array_equal(_host(Ud)[IN], ref3[IN])
+
+
+@pytest.mark.parametrize("de_switch", [0.0, 1e-3])
+@pytest.mark.parametrize("cfg", [3, "blob"])
+def test_fp64_bit_identical_to_oracle_amr(hydro, oracle_mod, cfg, de_switch):
+    """With coarse-fine faces: the in-stage flux correction replaces each
+    coarse boundary flux by the mean of the four fine ones before the flux
+    differences, as the oracle does, so one blended stage over the Zipf
+    batches and one full RK3 step are bit-identical too.  With the
+    dual-energy switch on, evolved states take the tau^gamma branch at a few
+    faces, where pow (correctly rounded in neither libm) may differ by an ulp:
+    there the per-cell error (R12) stays at the 1e-12 gate of the FP64 path."""
+    if cfg == "blob":
+        grid, U = H.amr_blob_state()
+        ids = offs = None
+    else:
+        w = W.config(cfg)
+        grid, U = w.grid, w.state()
+        ids, offs = w.batches.ids, w.batches.offsets
+    o = oracle_mod.Oracle(grid, de_switch=de_switch)
+    o.fill_ghosts(U)
+    _, ms, st = o.stage(U, 0.0)
+    dt = 0.4 / ms[1]
+    U0 = U.copy()
+    U0[IN] *= 1.0 + 1e-3 * np.cos(np.arange(U0[IN].size).reshape(U0[IN].shape))
+    ref, ms_o, st = o.stage(U, dt, U0=U0, beta=2.0 / 3.0)
+    assert st == 0
+    g = hydro.HydroGrid(grid, precision="fp64", de_switch=de_switch)
+    kw = {} if ids is None else {"ids": torch.as_tensor(ids, device="cuda"), "batch_offsets": offs}
+    out, msd = g.step(_dev(U), dt, U0=_dev(U0), beta=2.0 / 3.0, U_out=_dev(U), **kw)
+    g.sync()
+    assert np.array_equal(_host(out)[IN], ref[IN])
+    assert np.array_equal(msd.cpu().numpy(), ms_o)
+    ref3, _, st = o.rk3_step(U, dt)
+    Ud = _dev(U)
+    g.rk3_step(Ud, dt, torch.empty_like(Ud), torch.empty_like(Ud), **kw)
+    g.sync()
+    if de_switch == 0.0:
+        assert np.array_equal(_host(Ud)[IN], ref3[IN])
+    else:
+        res = R.r12(_host(Ud), ref3)
+        assert np.all(res["err"] <= 1e-12), R.summary(res)
+
+
+def test_flux_correction_wait_timeout_is_reported(hydro, oracle_mod):
+    """In an FP64 stage a coarse sub-grid waits for its finer neighbour's
+    exported fluxes.  Made to wait for one that cannot come (one CTA, the batch
+    [coarse, fine] taken in its own order: the fine item is the same CTA's next
+    one), the wait runs out after the set number of clock cycles, the stage
+    stops taking work and hydro_sync reports HYDRO_ERR_TIMEOUT; the same handle
+    then runs a normal stage that matches the oracle bit for bit."""
+    w = W.config(3)
+    rel, nb = w.grid.neighbor_rel, w.grid.neighbor
+    coarse = int(np.flatnonzero((rel == 1).any(axis=1))[0])
+    face = int(np.flatnonzero(rel[coarse] == 1)[0])
+    fine = int(nb[coarse, face, 0])
+    U = _filled(oracle_mod, w)
+    g = hydro.HydroGrid(w.grid, precision="fp64")
+    Ud = _dev(U)
+    g.set_param(hydro.PARAM_QUEUE_ORDER, 1)
+    g.set_param(hydro.PARAM_STAGE_GRID, 1)
+    g.set_param(hydro.PARAM_WAIT_LIMIT, 200000)     # about 0.1 ms
+    g.step(Ud, 1e-3, U_out=torch.empty_like(Ud), ids=np.array([coarse, fine], np.int32))
+    with pytest.raises(hydro.HydroError) as e:
+        g.sync()
+    assert e.value.code == -5
+    g.sync()                                        # the error word was cleared
+    g.set_param(hydro.PARAM_QUEUE_ORDER, 0)
+    g.set_param(hydro.PARAM_STAGE_GRID, 0)
+    g.set_param(hydro.PARAM_WAIT_LIMIT, 2 ** 31 - 1)
+    dt, _ = _dt(oracle_mod, w, U)
+    out, _ = g.step(Ud, dt, U_out=torch.empty_like(Ud), ids=torch.as_tensor(w.batches.ids, device="cuda"),
+                    batch_offsets=w.batches.offsets)
+    g.sync()
+    ref, _, st = oracle_mod.Oracle(w.grid).stage(U, dt)
+    assert np.array_equal(_host(out)[IN], ref[IN])
