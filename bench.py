@@ -223,8 +223,9 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 
 def field_errors(x, r, gamma=5.0 / 3.0):
-    """Per-field error of interior cells: max|x_f - r_f| / S_f, S_f = max|r_f|,
-    and for the three momenta the momentum-density scale max(|s|, rho c)."""
+    """Field-maximum error of interior cells (reported beside the per-cell
+    metric): max|x_f - r_f| / S_f, S_f = max|r_f|, and for the three momenta
+    the momentum-density scale max(|s|, rho c) over the field."""
     sl = (slice(None), slice(None), slice(3, 11), slice(3, 11), slice(3, 11))
     xi, ri = x[sl], r[sl]
     d = np.abs(xi - ri).max(axis=(0, 2, 3, 4))
@@ -245,6 +246,7 @@ def run_sweep(args):
     import oracle
     from paper_2210_06437_gb300 import build, hydro as HY
     from paper_2210_06437_gb300 import workloads as W
+    from tests import r12 as R
     torch.cuda.set_device(0)
     build.build()
     oracle.build()
@@ -281,12 +283,16 @@ def run_sweep(args):
             Ud = torch.from_numpy(U).cuda()
             out = Ud.clone()
             g.step(Ud, dt, U_out=out, ids=ids, batch_offsets=offs)
-            err1 = field_errors(out.cpu().numpy(), ref1)
+            x1 = out.cpu().numpy()
+            err1, r1, m1 = field_errors(x1, ref1), R.r12(x1, ref1), R.momentum_scaled(x1, ref1)
+            del x1
             V = Ud.clone()
             s1, s2 = torch.empty_like(Ud), torch.empty_like(Ud)
             g.rk3_step(V, dt, s1, s2, ids=ids, batch_offsets=offs)
             g.fill_ghosts(V)
-            err3 = field_errors(V.cpu().numpy(), ref3)
+            x3 = V.cpu().numpy()
+            err3, r3, m3 = field_errors(x3, ref3), R.r12(x3, ref3), R.momentum_scaled(x3, ref3)
+            del x3
             del out
             k = 5 if prec == "mixed" else 2
             msd = torch.zeros(2, dtype=torch.float64, device="cuda")
@@ -306,7 +312,9 @@ def run_sweep(args):
             torch.cuda.empty_cache()
             row[prec] = {"rk3_step_ms": t_step * 1e3, "cell_updates_per_s": w.cells * 3 / t_step,
                          "hbm_frac_of_measured": BYTES_PER_CELL_RK3_STAGE * w.cells * 3 / t_step / 1e9 / hbm,
-                         "err_one_stage": float(err1.max()), "err_rk3_step": float(err3.max()),
+                         "r12_one_stage": r1["err"].tolist(), "r12_rk3_step": r3["err"].tolist(),
+                         "momentum_rhoc_one_stage": m1.tolist(), "momentum_rhoc_rk3_step": m3.tolist(),
+                         "err_field_max_one_stage": float(err1.max()), "err_field_max_rk3_step": float(err3.max()),
                          "tolerance": 1e-5 if prec == "mixed" else 1e-12}
         row["mixed_speedup_vs_fp64"] = row["fp64"]["rk3_step_ms"] / row["mixed"]["rk3_step_ms"]
         print(json.dumps(row), flush=True)

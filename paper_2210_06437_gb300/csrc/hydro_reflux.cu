@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(RT, 4) reflux_kernel(const RefluxArgs r) {
       float x;  // the cell's new shadow value (mixed)
       if (sizeof(T) == 4 && (r.mode == 1 || r.mode == 2)) {
         r.D[((size_t)s * NF + f) * CELLS + c] = __hiloint2double(__float_as_int(dh), __float_as_int(dl));
-        x = __fadd_rn(s0[u], dh);
+        x = __fadd_rn(__fadd_rn(s0[u], dh), dl);  // the corrected pair may be unnormalized: both parts
         if (!(x - x == 0.0f) || (f == F_RHO && !(x > 0.0f))) bad = 1;
       } else {
         r.U[o] = v;

@@ -1097,9 +1097,9 @@ __device__ __forceinline__ bool direction_pass(const Shared<T>& sh, const StageA
 // algebraically the Shu-Osher stages.  The increments stay float pairs (about
 // 48 bits; error-free TwoSums and products); the FP64 state is read by every
 // stage but changed only once, by two FP64 additions in stage 3.  Stages 1
-// and 2 write the shadow of their state as RN32(RN32(U) + D_hi), within one
-// FP32 ulp of the rounded state, taking RN32(U) from the shadow of U, so they
-// read no FP64 state at all.
+// and 2 write the shadow of their state as RN32(RN32(RN32(U) + D_hi) + D_lo),
+// about one FP32 ulp from the rounded state, taking RN32(U) from the shadow of
+// U, so they read no FP64 state at all.
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
@@ -1197,7 +1197,10 @@ __device__ __forceinline__ unsigned update_inc_fields(const StageArgs& a, int s,
         x[r] = f64_to_f32(v);
       } else {
         a.Dout[inc_offset(s, f) + c0 + r * 64] = pack_pair(dh, dl);
-        x[r] = __fadd_rn(s0v[f - F0][r], dh);
+        // both parts of the pair: a corrected increment may be unnormalized
+        // (its low part above half an ulp of its high part) after the
+        // correction pass, and the shadow of the next stage reads this value
+        x[r] = __fadd_rn(__fadd_rn(s0v[f - F0][r], dh), dl);
         nf |= (__float_as_uint(x[r]) & 0x7f800000u) == 0x7f800000u ? 0x80000000u : 0u;
         if (f == F_RHO) bad |= !(x[r] > 0.0f);
       }

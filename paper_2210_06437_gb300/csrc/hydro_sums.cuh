@@ -1,7 +1,5 @@
 // hydro_sums.cuh -- exact per-sub-grid sums of 512 doubles (the first pass of
-// the grid totals), shared by the totals kernels, the stage kernel's fused
-// epilogue and the flux-correction kernel, so that all of them produce the same
-// bits for the same values.
+// the grid totals and of the diagnostics sums).
 //
 // One warp sums the 512 values of one (sub-grid, quantity): it finds their
 // largest binary exponent E (zero and subnormals count as exponent 1) and adds

@@ -91,3 +91,28 @@ def margin_union(oracle_obj, states, eps, ids=None):
     for U in states:
         mask, _ = oracle_obj.margin_cells(U, eps, ids=ids, mask=mask)
     return mask
+
+
+def momentum_scaled(x, r, gamma=5.0 / 3.0):
+    """Per field of the three momenta, the largest per-cell error measured
+    against the cell's own momentum-density scale:
+        max_cells |x - r| / max(|r|, rho c, 1e-8 ||r_f||_inf),
+    rho c from the reference cell (c = sqrt(gamma p / rho), p = (gamma - 1)
+    (E - |s|^2 / 2 rho), clipped at 0).  It reads like R12 wherever a cell moves
+    faster than sound and like an error relative to rho c in near-static cells,
+    where the momentum one stage makes is a difference of face pressures far
+    below the pressure itself.  Returns an array of 3."""
+    xi, ri = interiors(x), interiors(r)
+    rho = ri[:, 0]
+    s2 = ri[:, 1] ** 2 + ri[:, 2] ** 2 + ri[:, 3] ** 2
+    with np.errstate(divide="ignore", invalid="ignore"):
+        p = (gamma - 1.0) * np.maximum(ri[:, 4] - 0.5 * s2 / rho, 0.0)
+        rc = np.sqrt(gamma * rho * p)
+    out = np.zeros(3)
+    for k, f in enumerate((1, 2, 3)):
+        d = np.abs(xi[:, f] - ri[:, f])
+        sc = np.maximum(np.maximum(np.abs(ri[:, f]), rc), FLOOR * np.abs(ri[:, f]).max())
+        with np.errstate(divide="ignore", invalid="ignore"):
+            e = np.where(sc > 0, d / np.where(sc > 0, sc, 1.0), np.where(d == 0, 0.0, np.inf))
+        out[k] = e.max()
+    return out
