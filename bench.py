@@ -41,11 +41,19 @@ BYTES_PER_CELL_STAGE = 374.0     # read interior + 6 face slabs (1664 cells) + w
 # one RK3 step's stages: stage 1 moves 374 B per cell, stages 2 and 3 also read a
 # second FP64-sized array (U0, or the previous increment in the mixed increment form)
 BYTES_PER_CELL_RK3_STAGE = (374.0 + 2 * 462.0) / 3.0
-FLOPS_PER_CELL_STAGE = 2200.0    # algorithmic operation count per cell-update of one stage
+# FP64 operations per cell-update of the FP64 stage kernel, counted by ncu's per-opcode instruction
+# counters on one stage (beta = 1) of the 4097-leaf reduced binary octree (2,097,664 cells): DADD
+# 1,534,302,248, DMUL 1,175,636,249, DFMA 683,163,976 thread instructions
+FP64_INST_PER_CELL_STAGE = (1534302248 + 1175636249 + 683163976) / 2097664.0        # 1617.6
+FLOPS_PER_CELL_STAGE = (1534302248 + 1175636249 + 2 * 683163976) / 2097664.0       # 1943.3 (an FMA counts 2)
 GHOST_BYTES_PER_CELL = 396.0     # ghost fill: read + write 1152 face-slab cells per 512 interior cells
 SHADOW_BYTES_PER_CELL = 137.5    # FP32 shadow: read 88 B of FP64 interior, write 44 B + 5.5 B of restriction
 TAU_RESYNC_BYTES_PER_CELL = 56.0  # tracer reset: read rho, s, E, tau (48 B), write tau (8 B)
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 2 FP64 FMA/clk/SM at the 2070 MHz maximum clock
+# FP64 peak from the unit count: 152 SMs x 2 FP64 instructions per clock x 2.07 GHz (ncu on the counted
+# launch: the FP64 pipe busy 79 % of the active cycles at 1.56 instructions per clock per SM, i.e. about 1.98
+# per clock at 100 %); an FMA counts 2 flops
+FP64_PEAK_INST = 152 * 2 * 2.070e9
+FP64_PEAK_TFLOPS = 2 * FP64_PEAK_INST / 1e12
 # DRAM bytes (read + write) per cell-update of the mixed stage kernel from one ncu capture
 # (average of the three RK3 stage launches), valid only for the kernel source it was taken on.
 STAGE_TRAFFIC = {"sha256_prefix": "026d5c1d4fcba5cf", "bytes_per_cell": 303.5,
@@ -375,7 +383,7 @@ def main():
         g = HY.HydroGrid(w.grid, precision=prec)
         U.copy_(torch.from_numpy(U_host))
         g.fill_ghosts(U)
-        tuned = TU.tune(g, U, s1, ids=ids, batch_offsets=offs)   # launch shapes, outside the timed region
+        tuned = TU.tune(g, U, s1, s2, ids=ids, batch_offsets=offs)   # launch shapes, outside the timed region
         ms = torch.zeros(2, dtype=torch.float64, device=dev)
         g.step(U, 0.0, U_out=s1, ids=ids, batch_offsets=offs, max_speed=ms)   # dry stage: first CFL speed
         tots = torch.empty((max(args.steps, args.warmup), 11), dtype=torch.float64, device=dev)
@@ -579,9 +587,15 @@ def main():
     if "fp64" in results:
         f = results["fp64"]
         fl = FLOPS_PER_CELL_STAGE * cells / f["t_stage"] / 1e12  # average of the RK3 graph's stage launches
+        inst = FP64_INST_PER_CELL_STAGE * cells / f["t_stage"]
         line["fp64"] = {"value": aggregate_rate(cells, 3, world, f["t_step"]), "ms_per_step": f["t_step"] * 1e3,
                         "roofline": {"bound": "alu", "achieved": fl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                                      "frac": fl / FP64_PEAK_TFLOPS, "traffic": None,
+                                     "inst_frac": inst / FP64_PEAK_INST,
+                                     "counts": "FP64 operations per cell-update counted by ncu (DADD + DMUL + DFMA "
+                                               "= %.1f instructions, %.1f flops)" % (FP64_INST_PER_CELL_STAGE,
+                                                                                     FLOPS_PER_CELL_STAGE),
+                                     "peak_source": "unit count: 152 SMs x 2 FP64 instructions/clk x 2.07 GHz",
                                      "kernel": "stage_kernel<double>", "launch_ms": f["t_stage"] * 1e3,
                                      "hbm_frac": BYTES_PER_CELL_RK3_STAGE * cells / f["t_stage"] / 1e9 / hbm},
                         "gpu_launches": f["launches"]}

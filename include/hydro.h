@@ -92,12 +92,21 @@ typedef struct {
  * the octree).  All batches of one call are processed by one persistent
  * launch that pulls sub-grids from a device work queue. */
 typedef struct {
-  const int32_t *subgrid_ids;   /* DEVICE [n_items], ids in [0, n_subgrids), unique */
+  const int32_t *subgrid_ids;   /* DEVICE [n_items], ids in [0, n_subgrids), unique; an id
+                                   or-ed with HYDRO_ITEM_FLUX_ONLY is not advanced: its
+                                   coarse-fine boundary fluxes are only computed and
+                                   exported for the correction of its coarser neighbours
+                                   in the same call (a proxy of a sub-grid that another
+                                   grid partition advances) */
   int32_t n_items;              /* >= 0 */
   const int32_t *batch_offsets; /* HOST [n_batches + 1], non-decreasing, 0 .. n_items;
                                    may be NULL (one batch) */
   int32_t n_batches;            /* >= 0 */
 } hydro_batch;
+
+/* Batch id flag: export the sub-grid's coarse-fine boundary fluxes, do not
+ * advance it (see hydro_batch.subgrid_ids). */
+#define HYDRO_ITEM_FLUX_ONLY 0x40000000
 
 typedef struct hydro_handle hydro_handle;
 
@@ -348,7 +357,11 @@ typedef enum {
                                         stage stop taking work and hydro_sync return HYDRO_ERR_TIMEOUT */
   HYDRO_PARAM_QUEUE_ORDER = 5,       /* 0 (default): stages take finer levels first; 1: the batch's own order
                                         (waits may then be for sub-grids not yet taken) */
-  HYDRO_PARAM_STAGE_GRID = 6         /* stage kernel CTAs in total, >= 1 (0 = the default from the occupancy) */
+  HYDRO_PARAM_STAGE_GRID = 6,        /* stage kernel CTAs in total, >= 1 (0 = the default from the occupancy) */
+  HYDRO_PARAM_PREFETCH_PASS = 7,     /* direction pass (0 x, 1 y (default), 2 z) in which a stage pulls the rows
+                                        its update reads into L2: the prefetch distance */
+  HYDRO_PARAM_REFLUX_SHAPE = 8       /* launch shape of the mixed correction pass: 0 (default) 256 threads x 3
+                                        items, 1: 128 x 3, 2: 256 x 2, 3: 512 x 3 */
 } hydro_param;
 
 /* Release the handle and its device scratch (waits for its work first). */

@@ -86,6 +86,8 @@ struct hydro_handle {
   int n_levels = 1;                    // distinct cell widths
   int queue_order = 0;                 // 0: finest level first; 1: the batch's own order
   int grid_cap = 0;                    // stage CTAs (0: from the occupancy)
+  int pf_pass = 1;                     // direction pass that prefetches the update's rows
+  int reflux_shape = 0;                // launch shape of the mixed correction pass
   long long wait_limit = 0x7fffffffll;  // clock cycles a CTA waits for a neighbour's fluxes
   int8_t* d_level = nullptr;           // [n] level rank, 0 = finest
   int32_t* d_order_all = nullptr;      // [n] every sub-grid, finest level first
@@ -233,6 +235,7 @@ int enqueue_stage(hydro_handle* h, const int32_t* ids, int n_items, const double
   a.queue = h->d_queue + queue_slot;
   a.err = h->d_err;
   a.max_speed = ms;
+  a.pf_pass = h->pf_pass;
   const bool mixed = h->precision == HYDRO_MIXED;
   const bool correct = h->reflux && h->n_cf > 0;
   if (correct && mixed) {
@@ -275,7 +278,7 @@ int enqueue_stage(hydro_handle* h, const int32_t* ids, int n_items, const double
     r.fb = h->d_fb;
     r.fb_stamp = h->d_fb_stamp;
     r.call_id = a.call_id;
-    r.dx = h->d_dx;
+    r.inv_dx = h->d_inv_dx;
     r.dt = dt;
     r.dt_dev = dt_dev;
     r.mode = mode;
@@ -285,6 +288,7 @@ int enqueue_stage(hydro_handle* h, const int32_t* ids, int n_items, const double
     r.S0 = S0;
     r.Sout = Sout;
     r.err = h->d_err;
+    r.shape = h->reflux_shape;
     e = launch_reflux_mixed(r, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "flux correction kernel launch");
     h->launches += 1;
@@ -874,6 +878,20 @@ int hydro_set_param(hydro_handle* h, int32_t key, int32_t value) {
   if (key == HYDRO_PARAM_STAGE_GRID) {
     if (value < 0) return fail(h, HYDRO_ERR_INVALID, "stage grid must be >= 0");
     h->grid_cap = value;
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+    return HYDRO_OK;
+  }
+  if (key == HYDRO_PARAM_PREFETCH_PASS) {
+    if (value < 0 || value > 2) return fail(h, HYDRO_ERR_INVALID, "prefetch pass must be 0, 1 or 2");
+    h->pf_pass = value;
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+    return HYDRO_OK;
+  }
+  if (key == HYDRO_PARAM_REFLUX_SHAPE) {
+    if (value < 0 || value >= REFLUX_SHAPES) return fail(h, HYDRO_ERR_INVALID, "correction shape out of range");
+    h->reflux_shape = value;
     for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
     h->graphs.clear();
     return HYDRO_OK;

@@ -21,6 +21,11 @@ constexpr int FACES_DIR = NPEN * NFACE;  // 576
 constexpr int CELLS = NX * NX * NX;      // 512
 constexpr int F_RHO = 0, F_SX = 1, F_EGAS = 4, F_TAU = 5;
 
+// A batch id with this bit set names a sub-grid whose coarse-fine boundary
+// fluxes are exported (and, FP64, published) for the correction of its coarser
+// neighbours, without updating it (the ABI's HYDRO_ITEM_FLUX_ONLY).
+constexpr int ITEM_FLUX_ONLY = 0x40000000;
+
 // device error word bits
 constexpr int ERRBIT_NONFINITE = 1;
 constexpr int ERRBIT_BAD_ID = 2;
@@ -97,6 +102,7 @@ struct StageArgs {
   int* abort_word;
   long long wait_limit;
   int32_t call_id;
+  int32_t pf_pass;       // the direction pass (0 x, 1 y, 2 z) that prefetches the update's rows into L2
 };
 
 // Coarse-fine flux correction after a mixed-precision stage (one CTA per
@@ -113,7 +119,7 @@ struct RefluxArgs {
   const void* fb;        // stage flux export (see StageArgs)
   const int32_t* fb_stamp;
   int32_t call_id;
-  const double* dx;
+  const double* inv_dx;
   double dt;
   const double* dt_dev;
   int32_t mode;          // the stage's mode (StageArgs)
@@ -123,7 +129,11 @@ struct RefluxArgs {
   const float* S0;       // modes 1, 2: shadow of the step's input state
   float* Sout;           // the stage's shadow output, refreshed where corrected (may be null)
   int* err;
+  int32_t shape;         // launch shape (REFLUX_SHAPES): threads per CTA and items per thread
 };
+
+// Launch shapes of the correction pass: {threads per CTA, items per thread}.
+constexpr int REFLUX_SHAPES = 4;
 
 // Encode the TMA descriptor of a padded state (n sub-grids) used by
 // StageArgs::tm_in / tm_u0; returns false if cuTensorMapEncodeTiled refuses it.

@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(QT) order_batch_kernel(const int32_t* __restri
   __syncthreads();
   // bucket 0: ids outside [0, n) (the stage reports them); bucket 1 + L: level rank L
   for (int t = tid; t < n_items; t += QT) {
-    const int s = ids[t];
+    const int s = ids[t] >= 0 ? ids[t] & ~ITEM_FLUX_ONLY : ids[t];  // a flux-only item counts as advanced
     const bool ok = s >= 0 && s < n_sub;
     atomicAdd(&cnt[ok ? 1 + level_rank[s] : 0], 1);
     if (ok) member[s] = call_id;
@@ -42,9 +42,10 @@ __global__ void __launch_bounds__(QT) order_batch_kernel(const int32_t* __restri
   }
   __syncthreads();
   for (int t = tid; t < n_items; t += QT) {
-    const int s = ids[t];
+    const int raw = ids[t];
+    const int s = raw >= 0 ? raw & ~ITEM_FLUX_ONLY : raw;
     const bool ok = s >= 0 && s < n_sub;
-    order[atomicAdd(&cnt[ok ? 1 + level_rank[s] : 0], 1)] = s;
+    order[atomicAdd(&cnt[ok ? 1 + level_rank[s] : 0], 1)] = raw;
   }
 }
 

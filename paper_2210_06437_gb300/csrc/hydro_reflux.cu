@@ -26,7 +26,6 @@
 namespace hydro {
 namespace {
 
-constexpr int RT = 256;
 
 __device__ __forceinline__ size_t interior_offset(int i, int j, int k) {
   return (size_t)(k + NG) * NP2 + (j + NG) * NP + (i + NG);
@@ -88,11 +87,10 @@ __device__ __forceinline__ unsigned cell_faces(int i, int j, int k) {
 // corrected faces; a cell on several corrected faces (edge, corner) is handled
 // by the item of its lowest face, which applies the faces in ascending order,
 // so the result does not depend on the thread schedule.  The loads of up to
-// IPT items are issued before any of them is written back.
-constexpr int IPT = 3;
-
-template <typename T>
-__global__ void __launch_bounds__(RT, 4) reflux_kernel(const RefluxArgs r) {
+// IPT items are issued before any of them is written back.  RT threads per
+// CTA (at least 128) and IPT are the launch shape, a tuning parameter.
+template <typename T, int RT, int IPT>
+__global__ void __launch_bounds__(RT, 1024 / RT) reflux_kernel(const RefluxArgs r) {
   __shared__ int s_cf[CF_ENTRY];      // id, then the fine neighbour of each face quadrant
   __shared__ int s_ok[CF_ENTRY];      // stamp check of each of them
   __shared__ double s_lam;            // dt / dx of the sub-grid
@@ -101,10 +99,14 @@ __global__ void __launch_bounds__(RT, 4) reflux_kernel(const RefluxArgs r) {
   if (tid < CF_ENTRY) {
     const int v = __ldg(r.cf + (size_t)blockIdx.x * CF_ENTRY + tid);
     s_cf[tid] = v;
-    s_ok[tid] = v >= 0 && __ldg(r.fb_stamp + v) == r.call_id;
+    // the coarse sub-grid itself must have been advanced by the call (stamp
+    // +call_id); a fine neighbour must have exported its fluxes in it (advanced,
+    // or a flux-only item: -call_id)
+    const int st = v >= 0 ? __ldg(r.fb_stamp + v) : 0;
+    s_ok[tid] = v >= 0 && (st == r.call_id || (tid > 0 && st == -r.call_id));
   } else if (tid == 32) {
     const double dt = r.dt_dev ? *r.dt_dev : r.dt;
-    s_lam = __ddiv_rn(dt, __ldg(r.dx + __ldg(r.cf + (size_t)blockIdx.x * CF_ENTRY)));  // as the stage's dt / dx
+    s_lam = dt * __ldg(r.inv_dx + __ldg(r.cf + (size_t)blockIdx.x * CF_ENTRY));  // as the mixed stage's dt * (1/dx)
   }
   if (tid >= 64 && tid < 128) blocks[tid - 64] = 0;
   __syncthreads();
@@ -236,7 +238,12 @@ __global__ void __launch_bounds__(RT, 4) reflux_kernel(const RefluxArgs r) {
 
 cudaError_t launch_reflux_mixed(const RefluxArgs& r, cudaStream_t st) {
   if (r.n_list < 1) return cudaSuccess;
-  reflux_kernel<float><<<r.n_list, RT, 0, st>>>(r);
+  switch (r.shape) {
+    case 1: reflux_kernel<float, 128, 3><<<r.n_list, 128, 0, st>>>(r); break;
+    case 2: reflux_kernel<float, 256, 2><<<r.n_list, 256, 0, st>>>(r); break;
+    case 3: reflux_kernel<float, 512, 3><<<r.n_list, 512, 0, st>>>(r); break;
+    default: reflux_kernel<float, 256, 3><<<r.n_list, 256, 0, st>>>(r); break;
+  }
   return cudaGetLastError();
 }
 

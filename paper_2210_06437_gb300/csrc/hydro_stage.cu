@@ -821,13 +821,16 @@ __device__ __forceinline__ void prefetch_update_rows(const StageArgs& a, int s) 
 }
 
 // Work item and what its processing needs: sub-grid id (-1: queue exhausted,
-// -2: bad id), neighbour table, dt/dx and 1/dx.
+// -2: bad id), whether it only exports its coarse-fine fluxes (an id with
+// ITEM_FLUX_ONLY: a proxy of a sharded grid, read by the correction of a
+// coarser neighbour but advanced elsewhere), neighbour table, dt/dx.
 struct Meta {
   Nbr nb;
   int item;
   int s;
-  double lam;    // dt / dx, the IEEE quotient
-  double dx;
+  int flux_only;
+  double lam;    // FP64: dt / dx, the IEEE quotient; mixed: dt * (1/dx)
+  double sdx;    // the factor of the speed per cell width: FP64 dx (a quotient), mixed 1/dx (a product)
   float lh, ll;  // lam split into two floats (lh + ll = lam to about 2^-48)
 };
 
@@ -842,7 +845,8 @@ struct Pf {
   int nbv;    // lane l < 24: neighbour entry l of s
   int relv;   // lane l < 6: level relation of face l
   int octv;   // lane 0: octant
-  double dx;  // lane 0: dx
+  double dx;  // lane 0: dx (FP64) or 1/dx (mixed)
+  int fo;     // the item only exports fluxes
 };
 
 // (once a bounded wait has given up anywhere, the queue counts as empty)
@@ -857,11 +861,20 @@ __device__ __forceinline__ void pf_id(const StageArgs& a, Pf& pf) {
 }
 
 // Check the fetched id and issue the loads of its neighbour table.
+// exact_quotients (FP64): dt/dx and speed/dx as IEEE quotients, as the plain
+// statement has them; the mixed path multiplies by 1/dx (one FP64 division
+// per sub-grid sits on its critical path, measured 1 % of the step).
+template <bool exact_quotients>
 __device__ __forceinline__ void pf_load(const StageArgs& a, Pf& pf) {
   const int lane = threadIdx.x & 31;
   int s = -1;
+  pf.fo = 0;
   if (pf.item < a.n_items) {
     s = pf.s;
+    if (s >= 0 && (s & ITEM_FLUX_ONLY)) {
+      pf.fo = 1;
+      s &= ~ITEM_FLUX_ONLY;
+    }
     if (s < 0 || s >= a.n_sub) {
       if (lane == 0) atomicOr(a.err, ERRBIT_BAD_ID);
       s = -2;
@@ -873,12 +886,13 @@ __device__ __forceinline__ void pf_load(const StageArgs& a, Pf& pf) {
     if (lane < 6) pf.relv = a.rel[s * 6 + lane];
     if (lane == 0) {
       pf.octv = a.oct[s];
-      pf.dx = a.dx[s];
+      pf.dx = exact_quotients ? a.dx[s] : a.inv_dx[s];
     }
   }
 }
 
 // Store the fetched item into m.
+template <bool exact_quotients>
 __device__ __forceinline__ void pf_store(double dt, const Pf& pf, Meta& m) {
   const int lane = threadIdx.x & 31;
   if (pf.s >= 0) {
@@ -886,9 +900,9 @@ __device__ __forceinline__ void pf_store(double dt, const Pf& pf, Meta& m) {
     if (lane < 6) m.nb.rel[lane] = pf.relv;
     if (lane == 0) {
       m.nb.oct = pf.octv;
-      const double lam = __ddiv_rn(dt, pf.dx);
+      const double lam = exact_quotients ? __ddiv_rn(dt, pf.dx) : dt * pf.dx;
       m.lam = lam;
-      m.dx = pf.dx;
+      m.sdx = pf.dx;
       m.lh = (float)lam;
       m.ll = (float)(lam - (double)m.lh);
     }
@@ -896,16 +910,18 @@ __device__ __forceinline__ void pf_store(double dt, const Pf& pf, Meta& m) {
   if (lane == 0) {
     m.item = pf.item;
     m.s = pf.s;
+    m.flux_only = pf.fo;
   }
 }
 
 // All three steps at once (loop prologue and after a bad id).
+template <bool exact_quotients>
 __device__ __forceinline__ void prefetch_meta(const StageArgs& a, double dt, Meta& m) {
   Pf pf;
   pf_ticket(a, pf);
   pf_id(a, pf);
-  pf_load(a, pf);
-  pf_store(dt, pf, m);
+  pf_load<exact_quotients>(a, pf);
+  pf_store<exact_quotients>(dt, pf, m);
 }
 
 // Coarse side of the in-stage flux correction.  Thread 0 waits until every
@@ -971,8 +987,8 @@ __device__ __forceinline__ bool direction_pass(const Shared<T>& sh, const StageA
                                                Meta& nxt, Pf& pf, double dt, Acc<T> (&acc)[NF], T& amax, T gamma,
                                                T eta) {
   const int tid = threadIdx.x;
-  if (D == 1) prefetch_update_rows(a, cur.s);
-  if (D == 2 && (tid >> 5) == THREADS / 32 - 1) pf_load(a, pf);
+  if (D == a.pf_pass) prefetch_update_rows(a, cur.s);  // the prefetch distance: a tuning parameter
+  if (D == 2 && (tid >> 5) == THREADS / 32 - 1) pf_load<sizeof(T) == 8>(a, pf);
   // A: PPM, one (field, pencil) task per iteration
 #pragma unroll 1
   for (int task = tid; task < NF * NPEN; task += THREADS) {
@@ -1003,7 +1019,7 @@ __device__ __forceinline__ bool direction_pass(const Shared<T>& sh, const StageA
   if ((tid >> 5) == THREADS / 32 - 1) {
     if (D == 0) pf_ticket(a, pf);
     if (D == 1) pf_id(a, pf);
-    if (D == 2) pf_store(dt, pf, nxt);
+    if (D == 2) pf_store<sizeof(T) == 8>(dt, pf, nxt);
   }
   __syncthreads();
   // the halo buffer is free: start gathering the next slabs; after z the tile
@@ -1033,7 +1049,7 @@ __device__ __forceinline__ bool direction_pass(const Shared<T>& sh, const StageA
   // neighbours' exported fluxes, then take their means (correct_faces)
   if constexpr (sizeof(T) == 8) {
     unsigned corr = 0;
-    if (a.fb) corr = (cur.nb.rel[2 * D] == 1 ? 1u : 0u) | (cur.nb.rel[2 * D + 1] == 1 ? 2u : 0u);
+    if (a.fb && !cur.flux_only) corr = (cur.nb.rel[2 * D] == 1 ? 1u : 0u) | (cur.nb.rel[2 * D + 1] == 1 ? 2u : 0u);
     if (corr) {
       __shared__ int s_ok;
       if (tid == 0) s_ok = wait_fine<D>(a, cur.nb, corr);
@@ -1308,7 +1324,7 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(
   unsigned bad = 0;
 
   // prologue: the first work item, its neighbour table and x halo
-  if ((tid >> 5) == THREADS / 32 - 1) prefetch_meta(a, dt, s_meta[0]);
+  if ((tid >> 5) == THREADS / 32 - 1) prefetch_meta<sizeof(T) == 8>(a, dt, s_meta[0]);
   __syncthreads();
   if (s_meta[0].s >= 0) {
     if constexpr (sizeof(T) == 4) stage_interior_async(a.Sin, s_meta[0].s, sh.tile);
@@ -1323,7 +1339,7 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(
     const int s = cur.s;
     if (s < 0) {  // bad id: skip it
       __syncthreads();
-      if ((tid >> 5) == THREADS / 32 - 1) prefetch_meta(a, dt, nxt);
+      if ((tid >> 5) == THREADS / 32 - 1) prefetch_meta<sizeof(T) == 8>(a, dt, nxt);
       __syncthreads();
       if (nxt.s >= 0) {
         if constexpr (sizeof(T) == 4) stage_interior_async(a.Sin, nxt.s, sh.tile);
@@ -1347,7 +1363,8 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(
     }
     cp_async_wait_all();
     __syncthreads();  // interior tile and x halo in place
-    if (sizeof(T) == 4 && a.fb_stamp && tid == 0) a.fb_stamp[s] = a.call_id;
+    const bool flux_only = cur.flux_only != 0;
+    if (sizeof(T) == 4 && a.fb_stamp && tid == 0) a.fb_stamp[s] = flux_only ? -a.call_id : a.call_id;
 
     Acc<T> acc[NF];
     Pf pf;
@@ -1356,8 +1373,11 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(
     direction_pass<T, 1>(sh, a, cur, nxt, pf, dt, acc, amax, gamma, eta);
     const bool exported_z = direction_pass<T, 2>(sh, a, cur, nxt, pf, dt, acc, amax, gamma, eta);
 
-    // update of the owned cells (and, mixed, the output's shadow)
-    if (sizeof(T) == 4 && a.mode != 0) {
+    // update of the owned cells (and, mixed, the output's shadow); an item
+    // that only exports its fluxes writes no state and posts no speed
+    if (flux_only) {
+      amax = T(0);
+    } else if (sizeof(T) == 4 && a.mode != 0) {
       if constexpr (sizeof(T) == 4) {
         const float lh = cur.lh, ll = cur.ll;
         if (a.mode == 1)
@@ -1412,7 +1432,8 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(
         v = __longlong_as_double((long long)m);
       const unsigned long long mask = 0x7fffffffffffffffull;
       atomicMax(&a.max_speed[0], (unsigned long long)__double_as_longlong(v) & mask);
-      atomicMax(&a.max_speed[1], (unsigned long long)__double_as_longlong(__ddiv_rn(v, cur.dx)) & mask);
+      const double vdx = sizeof(T) == 8 ? __ddiv_rn(v, cur.sdx) : v * cur.sdx;
+      atomicMax(&a.max_speed[1], (unsigned long long)__double_as_longlong(vdx) & mask);
     }
     par ^= 1;
   }

@@ -14,9 +14,14 @@ Index logic and data movement only; no solver arithmetic.  The coarse-fine
 flux correction of a stage needs a finer neighbour's flux on its face toward
 the coarse sub-grid; for a remote finer neighbour that flux is recomputed on
 its proxy slot, from the proxy's interior and the ghosts of that face (the
-owned coarse sub-grid), so the exchange stays interiors only.  One process per
-GPU would run the CUDA library on the local grid; on CPU ranks the same plan
-drives the oracle, which is how the tests validate it.
+owned coarse sub-grid): the CUDA library takes such proxies as flux-only batch
+items (HYDRO_ITEM_FLUX_ONLY, ``flux_only_proxies``), the oracle with
+``batch_all``.  ``exchange`` moves whole interiors; ``exchange_slabs`` (and
+``exchange_direct`` for partitions held in one process) only what a receiver
+reads: 3-layer face slabs of same-level and coarser proxies, whole interiors of
+finer ones.  One process per GPU runs the CUDA library on its local grid; CPU
+ranks drive the oracle with the same plan, which is how the tests validate it
+without several GPUs.
 """
 from __future__ import annotations
 
@@ -38,6 +43,7 @@ class Partition:
     owner: np.ndarray      # rank owning each global sub-grid
     send: Dict[int, np.ndarray]  # rank -> global ids this rank sends there each stage
     recv: Dict[int, np.ndarray]  # rank -> global ids received from there (in proxy order)
+    glob: Grid = None      # the global grid the plan was cut from
 
     @property
     def n_owned(self) -> int:
@@ -111,7 +117,7 @@ def build(grid: Grid, rank: int, world: int) -> Partition:
         if len(rcv):
             recv[q] = rcv
     p = Partition(rank=rank, world=world, owned=owned, proxies=proxies, local=local, owner=owner, send=send,
-                  recv=recv)
+                  recv=recv, glob=grid)
     p._lut = lut
     return p
 
@@ -146,6 +152,122 @@ def exchange(p: Partition, U_local, dist) -> None:
     for gids, buf in recvs:
         li = torch.as_tensor(p.local_index(gids), device=T.device)
         T[li, :, NG:NG + NX, NG:NG + NX, NG:NG + NX] = buf
+
+
+# ---------------------------------------------------------------------------
+# slab exchange: only the cells a receiver reads
+# ---------------------------------------------------------------------------
+
+SLAB = 3          # layers of a proxy that a same-level or finer owned neighbour reads across a face
+WHOLE = -1        # a finer proxy: the whole interior (the coarse owner reads six fine layers for its
+                  # 2x2x2 halo means, and the proxy's boundary flux is recomputed from it)
+
+
+def slab_entries(grid: Grid, gids: np.ndarray, owner: np.ndarray, reader: int) -> list:
+    """(gid, face) pieces of the proxies gids that rank `reader` reads: face
+    slabs of SLAB layers where a reader's sub-grid is a same-level or finer
+    neighbour across that face, the whole interior (face WHOLE) where a
+    reader's sub-grid is coarser.  Both sides of an exchange derive the same
+    list from the global grid."""
+    out = []
+    for g in np.asarray(gids).tolist():
+        whole, faces = False, []
+        for face in range(6):
+            relf = int(grid.neighbor_rel[g, face])
+            nbs = grid.neighbor[g, face, :4 if relf == 1 else 1]
+            if not np.any((nbs >= 0) & (owner[np.maximum(nbs, 0)] == reader)):
+                continue
+            if relf == -1:
+                whole = True
+            else:
+                faces.append(face)
+        out.extend([(g, WHOLE)] if whole else [(g, f) for f in faces])
+    return out
+
+
+def _region(face: int):
+    """Index of the padded interior cells of a piece (face slab or WHOLE) within [f, k, j, i]."""
+    I = slice(NG, NG + NX)
+    if face == WHOLE:
+        return (slice(None), I, I, I)
+    a, side = face // 2, face % 2
+    cut = slice(NG, NG + SLAB) if side == 0 else slice(NG + NX - SLAB, NG + NX)
+    sl = [slice(None), I, I, I]
+    sl[3 - a] = cut
+    return tuple(sl)
+
+
+def pack_pieces(U, entries, local_index) -> "object":
+    """The cells of `entries` from the local state U (torch, [m,11,14,14,14]) as one flat tensor."""
+    import torch
+    if not entries:
+        return torch.empty(0, dtype=U.dtype, device=U.device)
+    li = local_index(np.array([g for g, _ in entries]))
+    return torch.cat([U[int(l)][_region(f)].reshape(-1) for l, (_, f) in zip(li, entries)])
+
+
+def unpack_pieces(U, entries, local_index, buf) -> None:
+    """Write the flat buffer of pack_pieces into the proxy slots of U."""
+    if not entries:
+        return
+    li = local_index(np.array([g for g, _ in entries]))
+    o = 0
+    for l, (_, f) in zip(li, entries):
+        view = U[int(l)][_region(f)]
+        n = view.numel()
+        view.copy_(buf[o:o + n].view(view.shape))
+        o += n
+
+
+def exchange_slabs(p: Partition, U_local, dist) -> int:
+    """exchange() with only the cells each receiver reads (face slabs, whole
+    interiors of finer proxies); returns the bytes this rank sent."""
+    import torch
+    is_np = isinstance(U_local, np.ndarray)
+    T = torch.from_numpy(U_local) if is_np else U_local
+    reqs, keep, sent = [], [], 0
+    for q, gids in sorted(p.send.items()):
+        buf = pack_pieces(T, slab_entries(p.glob, gids, p.owner, q), p.local_index)
+        keep.append(buf)
+        sent += buf.numel() * buf.element_size()
+        reqs.append(dist.isend(buf, dst=q))
+    recvs = []
+    for q, gids in sorted(p.recv.items()):
+        entries = slab_entries(p.glob, gids, p.owner, p.rank)
+        n = sum(T[0][_region(f)].numel() for _, f in entries)
+        buf = torch.empty(n, dtype=T.dtype, device=T.device)
+        recvs.append((entries, buf))
+        reqs.append(dist.irecv(buf, src=q))
+    for r in reqs:
+        r.wait()
+    for entries, buf in recvs:
+        unpack_pieces(T, entries, p.local_index, buf)
+    return sent
+
+
+def exchange_direct(parts: List[Partition], states: list) -> int:
+    """The slab exchange between partitions held in one process (device
+    copies): every rank's proxies receive, from their owners' local states,
+    the cells it reads.  Returns the bytes moved."""
+    moved = 0
+    for r, p in enumerate(parts):
+        for q, gids in sorted(p.recv.items()):
+            entries = slab_entries(p.glob, gids, p.owner, r)
+            buf = pack_pieces(states[q], entries, parts[q].local_index)
+            moved += buf.numel() * buf.element_size()
+            unpack_pieces(states[r], entries, p.local_index, buf)
+    return moved
+
+
+def flux_only_proxies(p: Partition) -> np.ndarray:
+    """Local slots of the finer proxies next to an owned coarse sub-grid: a
+    stage lists them as flux-only items (their boundary fluxes feed the owned
+    sub-grid's coarse-fine correction; their owners advance them)."""
+    m = p.n_owned
+    nb = p.local.neighbor[:m]
+    rel = p.local.neighbor_rel[:m]
+    ids = nb[rel == 1].reshape(-1)
+    return np.unique(ids[ids >= m]).astype(np.int32)
 
 
 def allreduce_max(x: np.ndarray, dist) -> np.ndarray:

@@ -29,11 +29,12 @@ pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-12, "mixed": 1e-5}
 NONMOM = [0, 4, 5, 6, 7, 8, 9, 10]
-# Mixed RK3 step, density/tracer/scalars: the rotating polytropes' expanding
-# envelope (a few cells at rho 1e-8 .. 1e-7) reaches 5.1e-4 on the 4096-leaf
-# octree and 3.3e-4 on the 32768-leaf one; everywhere else <= 1e-5.
-MIXED_RK3 = {3: 1e-3, 4: 1e-3}
-MIXED_RK3_MOM = {3: 1e-3, 4: 1e-3}
+# Mixed RK3 step on the rotating polytropes (the expanding envelope, cells at
+# rho 1e-8 .. 1e-7 next to coarse-fine faces): density/tracer/scalars measured
+# 9.4e-6 (4096 leaves) and 1.5e-5 (32768 leaves), the momenta 2.0e-5 and
+# 3.1e-5 of max(|s|, rho c); elsewhere <= 1e-5.
+MIXED_RK3 = {3: 5e-5, 4: 5e-5}
+MIXED_RK3_MOM = {3: 1e-4, 4: 1e-4}
 NG, NX = 3, 8
 IN = (slice(None), slice(None), slice(NG, NG + NX), slice(NG, NG + NX), slice(NG, NG + NX))
 
@@ -333,7 +334,9 @@ def test_host_argument_errors(hydro):
     with pytest.raises(hydro.HydroError):
         g.step(Ud, 1e-3, U_out=torch.empty_like(Ud), batch_offsets=[0, 5])  # offsets do not reach n
     for key, value in ((hydro.PARAM_TAU_RESYNC, 2), (hydro.PARAM_REFLUX, -1), (hydro.PARAM_STAGE_CTAS_PER_SM, 9),
-                       (hydro.PARAM_GHOST_THREADS, 100), (99, 0)):
+                       (hydro.PARAM_GHOST_THREADS, 100), (hydro.PARAM_WAIT_LIMIT, 0),
+                       (hydro.PARAM_QUEUE_ORDER, 2), (hydro.PARAM_STAGE_GRID, -1), (hydro.PARAM_PREFETCH_PASS, 3),
+                       (hydro.PARAM_REFLUX_SHAPE, 4), (99, 0)):
         with pytest.raises(hydro.HydroError):
             g.set_param(key, value)
     g.set_param(hydro.PARAM_TAU_RESYNC, 1)
@@ -343,21 +346,36 @@ def test_host_argument_errors(hydro):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_autotuned_launch_keeps_parity(hydro, oracle_mod, prec, tmp_path, monkeypatch):
+def test_autotuner_space_keeps_results_bit_identical(hydro, oracle_mod, prec, tmp_path, monkeypatch):
+    """Every point of the tuner's space gives the same RK3 step bit for bit (only
+    launch shapes change), the tuner restores the state it timed on, caches
+    its choice, and the tuned handle still matches the oracle."""
     from paper_2210_06437_gb300 import tune
     monkeypatch.setenv("HYDRO_TUNE_CACHE", str(tmp_path / "tune.json"))
-    w = W.config(2)
+    w = W.config(3)
     U = _filled(oracle_mod, w)
     dt, _ = _dt(oracle_mod, w, U)
+    ids = torch.as_tensor(w.batches.ids, device="cuda")
     g = hydro.HydroGrid(w.grid, precision=prec)
+    outs = []
+    for params in tune.candidates(tune.space_for(prec)):
+        tune.apply(g, params)
+        Ud = _dev(U)
+        g.rk3_step(Ud, dt, torch.empty_like(Ud), torch.empty_like(Ud), ids=ids, batch_offsets=w.batches.offsets)
+        g.sync()
+        outs.append(_host(Ud)[IN])
+    assert all(np.array_equal(outs[0], o) for o in outs[1:])
     Ud = _dev(U)
-    best = tune.tune(g, Ud, torch.empty_like(Ud), reps=2)
-    assert set(best) == set(tune.SPACE)
-    assert tune.load_cache()            # the result was cached
-    out, _ = g.step(Ud, dt, U_out=torch.empty_like(Ud))
+    s1, s2 = torch.empty_like(Ud), torch.empty_like(Ud)
+    best = tune.tune(g, Ud, s1, s2, ids=ids, batch_offsets=w.batches.offsets, reps=2)
     g.sync()
-    ref, _, _ = oracle_mod.Oracle(w.grid).stage(U, dt)
-    check(_host(out), ref, prec)
+    assert set(best) == set(tune.space_for(prec))
+    assert tune.load_cache()            # the result was cached
+    assert np.array_equal(_host(Ud), U, equal_nan=True)  # the state was restored (NaN edge canaries too)
+    ref, _, _ = oracle_mod.Oracle(w.grid).rk3_step(U, dt)
+    g.rk3_step(Ud, dt, s1, s2, ids=ids, batch_offsets=w.batches.offsets)
+    g.sync()
+    check(_host(Ud), ref, prec, "rk3", 3)
 
 
 # ---------------------------------------------------------------------------
@@ -767,7 +785,9 @@ def test_rk3_step_with_tau_resync_matches_oracle(hydro, oracle_mod, prec):
     ids = torch.as_tensor(w.batches.ids, device="cuda")
     g.rk3_step(Ud, dt, s1, s2, ids=ids, batch_offsets=w.batches.offsets)
     g.sync()
-    check(_host(Ud), ref, prec, "rk3", 3)
+    # the mixed reset takes tau = e_i^(1/gamma) in FP32 (powf) from
+    # e_i = E - |s|^2 / 2 rho: per cell 2.1e-4 where e_i is a small difference
+    check(_host(Ud), ref, prec, "rk3", 3, gate=5e-4 if prec == "mixed" else None)
 
 
 # ---------------------------------------------------------------------------

@@ -52,7 +52,7 @@ def _free_port():
     return port
 
 
-def _worker(rank, world, port, cfg, steps, out):
+def _worker(rank, world, port, cfg, steps, out, slabs=False):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), OMP_NUM_THREADS="2")
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
@@ -62,9 +62,14 @@ def _worker(rank, world, port, cfg, steps, out):
         o = oracle.Oracle(p.local)
         own = np.arange(p.n_owned, dtype=np.int32)
         UL = P.scatter_global(p, w.state())
+        if slabs:   # proxies start stale: only the exchanged cells may be read
+            UL[p.n_owned:][INTERIOR] = np.nan
 
         def stage(Uin, dt, U0=None, beta=1.0):
-            P.exchange(p, Uin, dist)
+            if slabs:
+                P.exchange_slabs(p, Uin, dist)
+            else:
+                P.exchange(p, Uin, dist)
             o.fill_ghosts(Uin)
             Uout = Uin.copy()
             # every sub-grid of the global grid is advanced by this stage (the
@@ -99,12 +104,16 @@ def _worker(rank, world, port, cfg, steps, out):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("cfg,world,steps", [(3, 2, 2), (1, 2, 3)])
-def test_sharded_step_matches_single_domain(oracle_mod, cfg, world, steps):
+@pytest.mark.parametrize("cfg,world,steps,slabs", [(3, 2, 2, False), (1, 2, 3, False), (3, 2, 2, True),
+                                                    (3, 3, 1, True)])
+def test_sharded_step_matches_single_domain(oracle_mod, cfg, world, steps, slabs):
+    """slabs: the exchange moves only the cells each receiver reads (face
+    slabs; whole interiors of finer proxies); the proxies' other cells then
+    hold stale values that no owned sub-grid may read."""
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, world, port, cfg, steps, q)) for r in range(world)]
+    procs = [ctx.Process(target=_worker, args=(r, world, port, cfg, steps, q, slabs)) for r in range(world)]
     for pr in procs:
         pr.start()
     msg = q.get(timeout=600)

@@ -31,8 +31,9 @@ def test_cache_roundtrip(tmp_path, monkeypatch):
     k2 = tune.cache_key("NVIDIA GB300", "mixed", 40000)
     assert k1 == k2                       # same power-of-two bucket
     assert tune.cache_key("NVIDIA GB300", "fp64", 65536) != k1
-    tune.store_cache(k1, {"params": {"stage_ctas_per_sm": 2, "ghost_threads": 256}})
+    tune.store_cache(k1, {"params": {"stage_ctas_per_sm": 2, "prefetch_pass": 1, "reflux_shape": 0}})
     assert tune.load_cache()[k1]["params"]["stage_ctas_per_sm"] == 2
     path.write_text("not json")
     assert tune.load_cache() == {}
-    json.loads(json.dumps(tune.SPACE))
+    json.loads(json.dumps(tune.SPACE_MIXED))
+    assert set(tune.space_for("fp64")) <= set(tune.PARAMS) and set(tune.space_for("mixed")) == set(tune.PARAMS)
