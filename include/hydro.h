@@ -227,6 +227,20 @@ int hydro_fill_ghosts(hydro_handle *h, double *U, void *stream);
  * graph writes the FP32 shadow of U once; each stage writes the shadow of its
  * state for the next (stages 1 and 2 as RN32(RN32(U) + increment), within one
  * float32 ulp of the rounded state).
+ * HYDRO_PARAM_FUSED_RK3 runs the three stages as ONE persistent kernel launch
+ * (Section VI: neighbours' data read in place, no exchange step between
+ * stages): one work queue of the three stages' items, in stage order; the
+ * stage-k item of a sub-grid starts once the sub-grid and the face neighbours
+ * its halo reads have completed stage k - 1 (per-sub-grid completion counters,
+ * release/acquire), and in mixed precision the coarse-fine correction of a
+ * coarse sub-grid runs inside the launch as soon as it and its finer
+ * neighbours are done, applied by the CTA that completes the last of them.
+ * The results are bit-identical to the three-launch form.  Every wait is
+ * bounded by HYDRO_PARAM_WAIT_LIMIT; one that runs out makes the launch stop
+ * taking work and hydro_sync return HYDRO_ERR_TIMEOUT (the state is then
+ * undefined).  The one-launch form needs mutual neighbour tables (every
+ * sub-grid whose halo reads s is read by s, as on an octree); handles whose
+ * tables are not mutual use the three-launch form.
  *   U        DEVICE padded state; its interior is overwritten by the new state
  *            (ghost cells are neither read nor updated: call hydro_fill_ghosts
  *            when they are wanted);
@@ -360,8 +374,13 @@ typedef enum {
   HYDRO_PARAM_STAGE_GRID = 6,        /* stage kernel CTAs in total, >= 1 (0 = the default from the occupancy) */
   HYDRO_PARAM_PREFETCH_PASS = 7,     /* direction pass (0 x, 1 y (default), 2 z) in which a stage pulls the rows
                                         its update reads into L2: the prefetch distance */
-  HYDRO_PARAM_REFLUX_SHAPE = 8       /* launch shape of the mixed correction pass: 0 (default) 256 threads x 3
+  HYDRO_PARAM_REFLUX_SHAPE = 8,      /* launch shape of the mixed correction pass: 0 (default) 256 threads x 3
                                         items, 1: 128 x 3, 2: 256 x 2, 3: 512 x 3 */
+  HYDRO_PARAM_FUSED_RK3 = 9          /* RK3 steps: 0 (default) three stage launches (and, mixed, three
+                                        correction passes); 1 one persistent launch per step; 2 one launch whose queue
+                                        interleaves the stages of each sub-grid, which cannot complete while a
+                                        CTA holds a later stage whose inputs are queued behind it: its bounded
+                                        waits give up (HYDRO_ERR_TIMEOUT), which is all it is for */
 } hydro_param;
 
 /* Release the handle and its device scratch (waits for its work first). */

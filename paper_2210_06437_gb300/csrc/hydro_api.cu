@@ -96,6 +96,15 @@ struct hydro_handle {
   void* d_fb = nullptr;                // [n][6][NF][64] exported boundary fluxes (T)
   int32_t* d_cf_flag = nullptr;        // [n] export progress of the current stage
   int* d_abort = nullptr;              // a bounded wait gave up during the current stage
+  // one-launch RK3 step
+  int fused = 0;                       // 0: three stage launches (and correction passes); 1: one launch; 2: the
+                                       // stage-interleaved queue (its waits give up: for tests of the bound)
+  int fused_ok = 0;                    // the neighbour tables are mutual (the one-launch step relies on it)
+  int occupancy_fused = 1;             // resident CTAs per SM of the one-launch kernel
+  int32_t* d_done = nullptr;           // [n] stages completed in the current launch
+  int32_t* d_arrive = nullptr;         // mixed: [n_cf_list] arrivals at each coarse sub-grid
+  int32_t* d_cf_slot = nullptr;        // mixed: [n] row in d_cf, -1 if none
+  int32_t* d_cf_target = nullptr;      // mixed: [n_cf_list] 1 + finer face neighbours
   int32_t call_counter = 0;
   cudaStream_t cap_stream = nullptr;
   cudaStream_t last_stream = nullptr;
@@ -152,6 +161,10 @@ void free_all(hydro_handle* h) {
   cudaFree(h->d_fb);
   cudaFree(h->d_cf_flag);
   cudaFree(h->d_abort);
+  cudaFree(h->d_done);
+  cudaFree(h->d_arrive);
+  cudaFree(h->d_cf_slot);
+  cudaFree(h->d_cf_target);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
 }
 
@@ -192,14 +205,10 @@ int stage_grid(hydro_handle* h, int n_items) {
 // Enqueue one stage (no validation).  queue_slot selects the counter.
 // mode 0: Shu-Osher stage; 1..3: mixed RK3 in increment form (Din / Dout the
 // increment pairs, see StageArgs)
-int enqueue_stage(hydro_handle* h, const int32_t* ids, int n_items, const double* Uin, const float* Sin,
-                  const double* U0, double beta, double dt, const double* dt_dev, double* Uout, float* Sout,
-                  unsigned long long* ms, int queue_slot, cudaStream_t st, int mode = 0, const double* Din = nullptr,
-                  double* Dout = nullptr, const float* S0 = nullptr, bool all_items = false) {
-  CUDA_TRY(h, cudaMemsetAsync(ms, 0, 2 * sizeof(unsigned long long), st));
-  if (n_items == 0) return HYDRO_OK;
-  CUDA_TRY(h, cudaMemsetAsync(h->d_queue + queue_slot, 0, sizeof(unsigned int), st));
-  StageArgs a;
+// The arguments of one stage that do not depend on how it is launched.
+void fill_stage(hydro_handle* h, StageArgs& a, const int32_t* ids, int n_items, const double* Uin, const float* Sin,
+                const double* U0, double beta, double dt, const double* dt_dev, double* Uout, float* Sout,
+                unsigned long long* ms, int queue_slot, int mode, const double* Din, double* Dout, const float* S0) {
   std::memset(&a, 0, sizeof(a));
   // the padded FP64 arrays the update reads, prefetched by tensor map: Uin
   // (and U0) in mode 0, U in mode 3 (the increments, packed, are prefetched
@@ -236,6 +245,39 @@ int enqueue_stage(hydro_handle* h, const int32_t* ids, int n_items, const double
   a.err = h->d_err;
   a.max_speed = ms;
   a.pf_pass = h->pf_pass;
+  a.ids = ids;
+}
+
+// The mixed correction of the stage described by a (its call id set).
+void fill_reflux(hydro_handle* h, RefluxArgs& r, const StageArgs& a) {
+  std::memset(&r, 0, sizeof(r));
+  r.cf = h->d_cf;
+  r.n_list = h->n_cf_list;
+  r.fb = h->d_fb;
+  r.fb_stamp = h->d_fb_stamp;
+  r.call_id = a.call_id;
+  r.inv_dx = h->d_inv_dx;
+  r.dt = a.dt;
+  r.dt_dev = a.dt_dev;
+  r.mode = a.mode;
+  r.beta = a.beta;
+  r.U = a.Uout;
+  r.D = a.Dout;
+  r.S0 = a.S0;
+  r.Sout = a.Sout;
+  r.err = h->d_err;
+  r.shape = h->reflux_shape;
+}
+
+int enqueue_stage(hydro_handle* h, const int32_t* ids, int n_items, const double* Uin, const float* Sin,
+                  const double* U0, double beta, double dt, const double* dt_dev, double* Uout, float* Sout,
+                  unsigned long long* ms, int queue_slot, cudaStream_t st, int mode = 0, const double* Din = nullptr,
+                  double* Dout = nullptr, const float* S0 = nullptr, bool all_items = false) {
+  CUDA_TRY(h, cudaMemsetAsync(ms, 0, 2 * sizeof(unsigned long long), st));
+  if (n_items == 0) return HYDRO_OK;
+  CUDA_TRY(h, cudaMemsetAsync(h->d_queue + queue_slot, 0, sizeof(unsigned int), st));
+  StageArgs a;
+  fill_stage(h, a, ids, n_items, Uin, Sin, U0, beta, dt, dt_dev, Uout, Sout, ms, queue_slot, mode, Din, Dout, S0);
   const bool mixed = h->precision == HYDRO_MIXED;
   const bool correct = h->reflux && h->n_cf > 0;
   if (correct && mixed) {
@@ -272,23 +314,7 @@ int enqueue_stage(hydro_handle* h, const int32_t* ids, int n_items, const double
   h->launches += 1;
   if (correct && mixed) {
     RefluxArgs r;
-    std::memset(&r, 0, sizeof(r));
-    r.cf = h->d_cf;
-    r.n_list = h->n_cf_list;
-    r.fb = h->d_fb;
-    r.fb_stamp = h->d_fb_stamp;
-    r.call_id = a.call_id;
-    r.inv_dx = h->d_inv_dx;
-    r.dt = dt;
-    r.dt_dev = dt_dev;
-    r.mode = mode;
-    r.beta = beta;
-    r.U = Uout;
-    r.D = Dout;
-    r.S0 = S0;
-    r.Sout = Sout;
-    r.err = h->d_err;
-    r.shape = h->reflux_shape;
+    fill_reflux(h, r, a);
     e = launch_reflux_mixed(r, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "flux correction kernel launch");
     h->launches += 1;
@@ -387,6 +413,30 @@ int hydro_create(const hydro_grid_desc* d, hydro_handle** out) {
   std::vector<int8_t> level(n);
   std::vector<int32_t> order(n);
   std::vector<int32_t> cf;
+  std::vector<int32_t> cf_slot, cf_target;
+  // the one-launch RK3 step needs mutual neighbour tables: every sub-grid whose
+  // halo reads s is read by s (a stage-3 output overwrites what stage-1 halos
+  // read, and a sub-grid waits only for those it reads)
+  {
+    auto reads = [&](int s, int x) {
+      for (int f = 0; f < 6; ++f) {
+        const int rel = d->neighbor_rel[s * 6 + f];
+        for (int q = 0; q < (rel == 1 ? 4 : 1); ++q)
+          if (d->neighbor[((size_t)s * 6 + f) * 4 + q] == x) return true;
+      }
+      return false;
+    };
+    bool mutual = true;
+    for (int s = 0; s < n && mutual; ++s)
+      for (int f = 0; f < 6 && mutual; ++f) {
+        const int rel = d->neighbor_rel[s * 6 + f];
+        for (int q = 0; q < (rel == 1 ? 4 : 1); ++q) {
+          const int x = d->neighbor[((size_t)s * 6 + f) * 4 + q];
+          if (x >= 0 && x != s && !reads(x, s)) mutual = false;
+        }
+      }
+    h->fused_ok = mutual ? 1 : 0;
+  }
   {
     // level ranks from the cell widths (0 = finest) and the queue of every
     // sub-grid in level order, for the in-stage coarse-fine correction
@@ -413,7 +463,30 @@ int hydro_create(const hydro_grid_desc* d, hydro_handle** out) {
             cf.push_back(d->neighbor_rel[s * 6 + f] == 1 ? d->neighbor[(s * 6 + f) * 4 + q] : -1);
       }
       h->n_cf_list = (int)(cf.size() / CF_ENTRY);
+      // the one-launch step's arrival targets: the coarse sub-grid itself and
+      // every finer sub-grid that names it as the neighbour of a coarser face
+      cf_slot.assign(n, -1);
+      cf_target.assign(h->n_cf_list, 1);
+      for (int r = 0; r < h->n_cf_list; ++r) cf_slot[cf[(size_t)r * CF_ENTRY]] = r;
+      for (int s = 0; s < n; ++s)
+        for (int f = 0; f < 6; ++f)
+          if (d->neighbor_rel[s * 6 + f] == -1) {
+            const int r = cf_slot[d->neighbor[((size_t)s * 6 + f) * 4]];
+            if (r < 0)
+              h->fused_ok = 0;  // a coarser neighbour without finer ones: not a mutual table
+            else
+              ++cf_target[r];
+          }
+      for (int r = 0; r < h->n_cf_list; ++r) {
+        int fine = 0;
+        for (int e = 1; e < CF_ENTRY; ++e) fine += cf[(size_t)r * CF_ENTRY + e] >= 0 ? 1 : 0;
+        if (cf_target[r] != 1 + fine) h->fused_ok = 0;
+      }
       ok = ok && cudaMalloc(&h->d_cf, sizeof(int32_t) * cf.size()) == cudaSuccess;
+      ok = ok && cudaMalloc(&h->d_cf_slot, sizeof(int32_t) * n) == cudaSuccess;
+      ok = ok && cudaMalloc(&h->d_cf_target, sizeof(int32_t) * h->n_cf_list) == cudaSuccess;
+      ok = ok && cudaMalloc(&h->d_arrive, sizeof(int32_t) * h->n_cf_list) == cudaSuccess;
+      ok = ok && cudaMalloc(&h->d_order_all, sizeof(int32_t) * n) == cudaSuccess;
       ok = ok && cudaMalloc(&h->d_fb, sizeof(float) * (size_t)n * 6 * NF * NPEN) == cudaSuccess;
       ok = ok && cudaMalloc(&h->d_fb_stamp, sizeof(int32_t) * n) == cudaSuccess;
     } else if (h->n_cf > 0) {
@@ -424,9 +497,10 @@ int hydro_create(const hydro_grid_desc* d, hydro_handle** out) {
       ok = ok && cudaMalloc(&h->d_member, sizeof(int32_t) * n) == cudaSuccess;
       ok = ok && cudaMalloc(&h->d_fb, tsize * (size_t)n * 6 * NF * NPEN) == cudaSuccess;
       ok = ok && cudaMalloc(&h->d_cf_flag, sizeof(int32_t) * n) == cudaSuccess;
-      ok = ok && cudaMalloc(&h->d_abort, sizeof(int)) == cudaSuccess;
     }
   }
+  ok = ok && cudaMalloc(&h->d_abort, sizeof(int)) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->d_done, sizeof(int32_t) * n) == cudaSuccess;
   if (d->precision == HYDRO_MIXED)
     for (int b = 0; b < 3; ++b)
       ok = ok && cudaMalloc(&h->d_shadow[b], sizeof(float) * (size_t)n * NF * SHADOW_FIELD) == cudaSuccess;
@@ -448,16 +522,21 @@ int hydro_create(const hydro_grid_desc* d, hydro_handle** out) {
   ok = ok && cudaMemset(h->d_err, 0, sizeof(int)) == cudaSuccess;
   if (h->n_cf > 0 && d->precision == HYDRO_MIXED) {
     ok = ok && cudaMemcpy(h->d_cf, cf.data(), sizeof(int32_t) * cf.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(h->d_cf_slot, cf_slot.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(h->d_cf_target, cf_target.data(), sizeof(int32_t) * h->n_cf_list,
+                          cudaMemcpyHostToDevice) == cudaSuccess;
     ok = ok && cudaMemset(h->d_fb_stamp, 0, sizeof(int32_t) * n) == cudaSuccess;
+    ok = ok && cudaMemcpy(h->d_order_all, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice) == cudaSuccess;
   } else if (h->n_cf > 0) {
     ok = ok && cudaMemcpy(h->d_level, level.data(), n, cudaMemcpyHostToDevice) == cudaSuccess;
     ok = ok && cudaMemcpy(h->d_order_all, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice) == cudaSuccess;
     ok = ok && cudaMemset(h->d_member, 0, sizeof(int32_t) * n) == cudaSuccess;
     ok = ok && cudaMemset(h->d_cf_flag, 0, sizeof(int32_t) * n) == cudaSuccess;
-    ok = ok && cudaMemset(h->d_abort, 0, sizeof(int)) == cudaSuccess;
   }
+  ok = ok && cudaMemset(h->d_abort, 0, sizeof(int)) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
   h->occupancy = h->precision == HYDRO_MIXED ? stage_blocks_per_sm_mixed() : stage_blocks_per_sm_fp64();
+  h->occupancy_fused = h->precision == HYDRO_MIXED ? rk3_blocks_per_sm_mixed() : rk3_blocks_per_sm_fp64();
   if (!ok) {
     free_all(h);
     delete h;
@@ -613,9 +692,79 @@ int check_rk3(hydro_handle* h, const hydro_batch* batch, double* U, double* scra
 // scratch1 and scratch2 holding the increment pairs, U changed once at the
 // end; shadow buffers A = shadow of U (kept for the whole step), B = stage 1's
 // state, C = stage 2's; with write_next, stage 3 writes the new U's shadow into A.
+// The same step in one persistent launch (rk3_kernel, see FusedArgs): the
+// three stages' arguments as the separate launches take them, one queue, the
+// completion counters zeroed first.
+int enqueue_rk3_fused(hydro_handle* h, const int32_t* ids, int ni, double* U, double* s1, double* s2,
+                      unsigned long long* ms, bool write_next, cudaStream_t cs) {
+  FusedArgs F;
+  std::memset(&F, 0, sizeof(F));
+  const bool mixed = h->precision == HYDRO_MIXED;
+  const bool correct = h->reflux && h->n_cf > 0;
+  const double* dtd = h->d_dt;
+  unsigned long long* mt = h->d_ms_tmp;
+  // each stage's queue lists finer sub-grids first: FP64, the in-stage
+  // correction waits for them; mixed, a coarse sub-grid then completes (its
+  // finer neighbours have arrived) when its own item ends
+  const int32_t* q = correct && h->queue_order == 0 ? h->d_order_all : ids;
+  if (mixed) {
+    float *A = h->d_shadow[0], *B = h->d_shadow[1], *C = h->d_shadow[2];
+    fill_stage(h, F.st[0], q, ni, U, A, nullptr, 1.0, 0.0, dtd, nullptr, B, ms, 0, 1, nullptr, s1, A);
+    fill_stage(h, F.st[1], q, ni, U, B, nullptr, 1.0, 0.0, dtd, nullptr, C, mt, 0, 2, s1, s2, A);
+    fill_stage(h, F.st[2], q, ni, U, C, nullptr, 1.0, 0.0, dtd, U, write_next ? A : nullptr, mt, 0, 3, s2, nullptr, A);
+  } else {
+    fill_stage(h, F.st[0], q, ni, U, nullptr, nullptr, 1.0, 0.0, dtd, s1, nullptr, ms, 0, 0, nullptr, nullptr, nullptr);
+    fill_stage(h, F.st[1], q, ni, s1, nullptr, U, 0.25, 0.0, dtd, s2, nullptr, mt, 0, 0, nullptr, nullptr, nullptr);
+    fill_stage(h, F.st[2], q, ni, s2, nullptr, U, 2.0 / 3.0, 0.0, dtd, U, nullptr, mt, 0, 0, nullptr, nullptr,
+               nullptr);
+  }
+  for (int k = 0; k < 3; ++k) {
+    StageArgs& a = F.st[k];
+    a.abort_word = h->d_abort;
+    a.wait_limit = h->wait_limit;
+    if (!correct) continue;
+    a.fb = h->d_fb;
+    a.call_id = ++h->call_counter;
+    if (mixed) {
+      a.fb_stamp = h->d_fb_stamp;
+      fill_reflux(h, F.rf[k], a);
+    } else {
+      a.cf_flag = h->d_cf_flag;
+      a.member = nullptr;  // every sub-grid
+      a.flag_base = 3 * k;
+    }
+  }
+  F.done = h->d_done;
+  F.arrive = h->d_arrive;
+  F.cf_slot = h->d_cf_slot;
+  F.cf_target = h->d_cf_target;
+  F.n = ni;
+  F.order = h->fused == 2 ? 1 : 0;
+  CUDA_TRY(h, cudaMemsetAsync(ms, 0, 2 * sizeof(unsigned long long), cs));
+  CUDA_TRY(h, cudaMemsetAsync(mt, 0, 2 * sizeof(unsigned long long), cs));
+  CUDA_TRY(h, cudaMemsetAsync(h->d_queue, 0, sizeof(unsigned int), cs));
+  CUDA_TRY(h, cudaMemsetAsync(h->d_done, 0, sizeof(int32_t) * (size_t)h->n, cs));
+  CUDA_TRY(h, cudaMemsetAsync(h->d_abort, 0, sizeof(int), cs));
+  if (correct && mixed) CUDA_TRY(h, cudaMemsetAsync(h->d_arrive, 0, sizeof(int32_t) * (size_t)h->n_cf_list, cs));
+  if (correct && !mixed) CUDA_TRY(h, cudaMemsetAsync(h->d_cf_flag, 0, sizeof(int32_t) * (size_t)h->n, cs));
+  const int per_sm = h->ctas_per_sm > 0 ? std::min(h->ctas_per_sm, h->occupancy_fused) : h->occupancy_fused;
+  int grid = h->grid_cap > 0 ? h->grid_cap : h->sm_count * per_sm;
+  grid = std::max(1, std::min(grid, 3 * ni));
+  cudaError_t e = mixed ? launch_rk3_mixed(F, grid, cs) : launch_rk3_fp64(F, grid, cs);
+  if (e != cudaSuccess) return cuda_fail(h, e, "one-launch RK3 kernel launch");
+  h->launches += 1;
+  return HYDRO_OK;
+}
+
 int enqueue_rk3_stages(hydro_handle* h, const int32_t* ids, int ni, double* U, double* s1, double* s2,
                        unsigned long long* ms, bool write_next, cudaStream_t cs) {
   int rc;
+  if (h->fused && h->fused_ok && ni == h->n) {
+    rc = enqueue_rk3_fused(h, ids, ni, U, s1, s2, ms, write_next, cs);
+    if (!rc && h->tau_resync)
+      rc = enqueue_tau_resync(h, U, h->precision == HYDRO_MIXED && write_next ? h->d_shadow[0] : nullptr, cs);
+    return rc;
+  }
   if (h->precision == HYDRO_MIXED) {
     float *A = h->d_shadow[0], *B = h->d_shadow[1], *C = h->d_shadow[2];
     rc = enqueue_stage(h, ids, ni, U, A, nullptr, 1.0, 0.0, h->d_dt, nullptr, B, ms, 0, cs, 1, nullptr, s1, A, true);
@@ -892,6 +1041,13 @@ int hydro_set_param(hydro_handle* h, int32_t key, int32_t value) {
   if (key == HYDRO_PARAM_REFLUX_SHAPE) {
     if (value < 0 || value >= REFLUX_SHAPES) return fail(h, HYDRO_ERR_INVALID, "correction shape out of range");
     h->reflux_shape = value;
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+    return HYDRO_OK;
+  }
+  if (key == HYDRO_PARAM_FUSED_RK3) {
+    if (value < 0 || value > 2) return fail(h, HYDRO_ERR_INVALID, "one-launch RK3 mode must be 0, 1 or 2");
+    h->fused = value;
     for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
     h->graphs.clear();
     return HYDRO_OK;

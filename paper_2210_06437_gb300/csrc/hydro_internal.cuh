@@ -102,6 +102,7 @@ struct StageArgs {
   int* abort_word;
   long long wait_limit;
   int32_t call_id;
+  int32_t flag_base;     // FP64: cf_flag values are flag_base + d + 1 (stage k of a one-launch RK3 step: 3k)
   int32_t pf_pass;       // the direction pass (0 x, 1 y, 2 z) that prefetches the update's rows into L2
 };
 
@@ -134,6 +135,32 @@ struct RefluxArgs {
 
 // Launch shapes of the correction pass: {threads per CTA, items per thread}.
 constexpr int REFLUX_SHAPES = 4;
+
+// One SSP-RK3 step (three stages over every sub-grid) in one persistent
+// launch.  One work queue of 3 n tickets, stage-major (order 0) or
+// stage-interleaved (order 1, which cannot finish once a CTA holds a later
+// stage of an item whose neighbours' earlier stages are queued behind it: its
+// bounded waits give up, which is what it exists to show).  The stage-k item
+// of sub-grid s starts once s and every face neighbour whose interior its halo
+// gather reads have completed stage k - 1 (done[x] >= k; release / acquire;
+// a wait bounded by st[0].wait_limit cycles that sets ERRBIT_TIMEOUT and
+// *st[0].abort_word when it gives up).  FP64 corrects the coarse-fine fluxes
+// inside the stage (cf_flag, flag_base = 3k; the queue of each stage lists
+// finer sub-grids first).  Mixed precision: the correction of a coarse
+// sub-grid with finer face neighbours (row r of rf[k].cf) runs once its own
+// stage-k item and those of its finer neighbours are done: each of them adds
+// one to arrive[r], and the one that brings it to (k + 1) * cf_target[r]
+// applies the correction and then marks the coarse sub-grid complete.
+struct FusedArgs {
+  StageArgs st[3];
+  RefluxArgs rf[3];          // mixed: the correction of each stage (rf[k].cf: the coarse sub-grids)
+  int32_t* done;             // [n] stages completed in this launch, zero at launch
+  int32_t* arrive;           // [n_cf_list] arrivals, zero at launch
+  const int32_t* cf_slot;    // [n] row of the sub-grid in rf[k].cf, -1 if it has no finer face neighbour
+  const int32_t* cf_target;  // [n_cf_list] 1 + the number of finer face neighbours
+  int32_t n;                 // items per stage (every sub-grid)
+  int32_t order;
+};
 
 // Encode the TMA descriptor of a padded state (n sub-grids) used by
 // StageArgs::tm_in / tm_u0; returns false if cuTensorMapEncodeTiled refuses it.
@@ -168,8 +195,12 @@ cudaError_t launch_pack(const double* U, double* P, int n, cudaStream_t st);
 cudaError_t launch_unpack(const double* P, double* U, int n, cudaStream_t st);
 cudaError_t launch_stage_fp64(const StageArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_stage_mixed(const StageArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_rk3_fp64(const FusedArgs& f, int grid, cudaStream_t st);
+cudaError_t launch_rk3_mixed(const FusedArgs& f, int grid, cudaStream_t st);
 int stage_blocks_per_sm_fp64();
 int stage_blocks_per_sm_mixed();
+int rk3_blocks_per_sm_fp64();
+int rk3_blocks_per_sm_mixed();
 cudaError_t launch_ghost_fill(const GhostArgs& a, int threads, cudaStream_t st);
 // scratch doubles needed by launch_totals for n sub-grids
 size_t totals_scratch_doubles(int n);

@@ -39,6 +39,7 @@
 
 #include "hydro_fp.cuh"
 #include "hydro_internal.cuh"
+#include "hydro_reflux.cuh"
 
 namespace hydro {
 namespace {
@@ -785,6 +786,25 @@ __device__ __forceinline__ void gather(const StageArgs& a, int s, const Nbr& nb,
     gather_halo<D>(a.Uin, s, nb, halo);
 }
 
+// The array a stage's halos and (mixed) interiors are read from.
+template <typename T>
+__device__ __forceinline__ const T* stage_src(const StageArgs& a) {
+  if constexpr (sizeof(T) == 4)
+    return a.Sin;
+  else
+    return a.Uin;
+}
+
+// The source array of the stage of an item fetched ahead (one-launch step:
+// any of the three; read from the parameters with constant offsets).
+template <typename T, bool FUSED>
+__device__ __forceinline__ const T* next_src(const StageArgs* st, int k) {
+  if constexpr (FUSED)
+    return k == 0 ? stage_src<T>(st[0]) : (k == 1 ? stage_src<T>(st[1]) : stage_src<T>(st[2]));
+  else
+    return stage_src<T>(st[0]);
+}
+
 // Mixed path: asynchronous copy of sub-grid s's interior (all fields) from the
 // shadow into the tile; consecutive threads take consecutive cells.
 __device__ __forceinline__ void stage_interior_async(const float* __restrict__ S, int s, float* tile) {
@@ -796,6 +816,18 @@ __device__ __forceinline__ void stage_interior_async(const float* __restrict__ S
     const int t = k * SK + j * SJ + i;
 #pragma unroll
     for (int f = 0; f < NF; ++f) cp_async4(tile + f * ISZ + t, src + f * SHADOW_FIELD + c);
+  }
+}
+
+// Start the copies of the first direction's halo (and, mixed, of the interior)
+// of sub-grid s from src.
+template <typename T>
+__device__ __forceinline__ void start_item(const T* src, int s, const Nbr& nb, T* tile, T* halo) {
+  if constexpr (sizeof(T) == 4) {
+    stage_interior_async(src, s, tile);
+    gather_halo_shadow<0>(src, s, nb, halo);
+  } else {
+    gather_halo<0>(src, s, nb, halo);
   }
 }
 
@@ -832,6 +864,8 @@ struct Meta {
   double lam;    // FP64: dt / dx, the IEEE quotient; mixed: dt * (1/dx)
   double sdx;    // the factor of the speed per cell width: FP64 dx (a quotient), mixed 1/dx (a product)
   float lh, ll;  // lam split into two floats (lh + ll = lam to about 2^-48)
+  int stage;     // one-launch RK3 step: the item's stage (0..2); else 0
+  int ready;     // one-launch RK3 step: its inputs were complete when it was fetched
 };
 
 // The next work item as warp 7 (threads 224..255, one PPM task fewer than
@@ -847,17 +881,52 @@ struct Pf {
   int octv;   // lane 0: octant
   double dx;  // lane 0: dx (FP64) or 1/dx (mixed)
   int fo;     // the item only exports fluxes
+  int stage;  // its stage (one-launch RK3 step)
 };
 
-// (once a bounded wait has given up anywhere, the queue counts as empty)
-__device__ __forceinline__ void pf_ticket(const StageArgs& a, Pf& pf) {
+// The queue: n_total tickets.  A stage launch hands out its batch's items; the
+// one-launch RK3 step (FUSED) hands out 3 n tickets, stage-major (ticket t is
+// item t - k n of stage k = t / n) or, with order 1, stage-interleaved (stage
+// t % 3 of item t / 3).  Once a bounded wait has given up anywhere, the queue
+// counts as empty.
+__device__ __forceinline__ void pf_ticket(const StageArgs& a0, int n_total, Pf& pf) {
   if ((threadIdx.x & 31) == 0)
-    pf.item = (a.abort_word && ld_volatile(a.abort_word)) ? a.n_items : (int)atomicAdd(a.queue, 1u);
+    pf.item = (a0.abort_word && ld_volatile(a0.abort_word)) ? n_total : (int)atomicAdd(a0.queue, 1u);
 }
 
-__device__ __forceinline__ void pf_id(const StageArgs& a, Pf& pf) {
+template <bool FUSED>
+__device__ __forceinline__ void pf_id(const StageArgs* st, const FusedArgs* fx, int n_total, Pf& pf) {
   pf.item = __shfl_sync(0xffffffffu, pf.item, 0);
-  pf.s = pf.item < a.n_items ? a.ids[pf.item] : -1;
+  pf.stage = 0;
+  if (pf.item >= n_total) {
+    pf.s = -1;
+  } else if constexpr (FUSED) {
+    const int n = fx->n;
+    pf.stage = fx->order ? pf.item % 3 : pf.item / n;
+    const int idx = fx->order ? pf.item / 3 : pf.item - pf.stage * n;
+    const int32_t* ids = pf.stage == 0 ? st[0].ids : (pf.stage == 1 ? st[1].ids : st[2].ids);
+    pf.s = ids[idx];
+  } else {
+    pf.s = st[0].ids[pf.item];
+  }
+}
+
+// Whether the stage-k item of sub-grid s may start: s and every face
+// neighbour whose interior its halo gather reads (the neighbour of a same-level
+// or coarser face, the four of a finer one) have completed stage k - 1
+// (done >= k).  One warp: lane l < 24 takes neighbour entry l (id, and the
+// relation of its face), lane 24 takes s; acquire loads, so that the halo
+// copies issued after the CTA barrier that follows see the neighbours' outputs.
+__device__ __forceinline__ bool stage_ready(const int32_t* done, int s, int k, int id, int rel) {
+  const int lane = threadIdx.x & 31;
+  int x = -1;
+  if (lane < 24) {
+    if (((lane & 3) == 0 || rel == 1) && id >= 0) x = id;
+  } else if (lane == 24) {
+    x = s;
+  }
+  const bool ok = x < 0 || ld_acquire(done + x) >= k;
+  return __all_sync(0xffffffffu, ok);
 }
 
 // Check the fetched id and issue the loads of its neighbour table.
@@ -865,11 +934,11 @@ __device__ __forceinline__ void pf_id(const StageArgs& a, Pf& pf) {
 // statement has them; the mixed path multiplies by 1/dx (one FP64 division
 // per sub-grid sits on its critical path, measured 1 % of the step).
 template <bool exact_quotients>
-__device__ __forceinline__ void pf_load(const StageArgs& a, Pf& pf) {
+__device__ __forceinline__ void pf_load(const StageArgs& a, int n_total, Pf& pf) {
   const int lane = threadIdx.x & 31;
   int s = -1;
   pf.fo = 0;
-  if (pf.item < a.n_items) {
+  if (pf.item < n_total) {
     s = pf.s;
     if (s >= 0 && (s & ITEM_FLUX_ONLY)) {
       pf.fo = 1;
@@ -911,17 +980,35 @@ __device__ __forceinline__ void pf_store(double dt, const Pf& pf, Meta& m) {
     m.item = pf.item;
     m.s = pf.s;
     m.flux_only = pf.fo;
+    m.stage = pf.stage;
+  }
+}
+
+// One-launch RK3 step: whether the fetched item's inputs are complete (stage 0
+// items always are); warp-uniform, every lane of the warp calls it.
+template <bool FUSED>
+__device__ __forceinline__ void pf_ready(const FusedArgs* fx, const Pf& pf, Meta& m) {
+  if constexpr (FUSED) {
+    const int lane = threadIdx.x & 31;
+    const int rel = __shfl_sync(0xffffffffu, pf.relv, (lane >> 2) & 7);
+    bool r = true;
+    if (pf.s >= 0 && pf.stage > 0) r = stage_ready(fx->done, pf.s, pf.stage, lane < 24 ? pf.nbv : -1, rel);
+    if (lane == 0) m.ready = r;
+  } else {
+    if ((threadIdx.x & 31) == 0) m.ready = 1;
   }
 }
 
 // All three steps at once (loop prologue and after a bad id).
-template <bool exact_quotients>
-__device__ __forceinline__ void prefetch_meta(const StageArgs& a, double dt, Meta& m) {
+template <bool exact_quotients, bool FUSED>
+__device__ __forceinline__ void prefetch_meta(const StageArgs* st, const FusedArgs* fx, int n_total, double dt,
+                                              Meta& m) {
   Pf pf;
-  pf_ticket(a, pf);
-  pf_id(a, pf);
-  pf_load<exact_quotients>(a, pf);
+  pf_ticket(st[0], n_total, pf);
+  pf_id<FUSED>(st, fx, n_total, pf);
+  pf_load<exact_quotients>(st[0], n_total, pf);
   pf_store<exact_quotients>(dt, pf, m);
+  pf_ready<FUSED>(fx, pf, m);
 }
 
 // Coarse side of the in-stage flux correction.  Thread 0 waits until every
@@ -937,7 +1024,7 @@ __device__ bool wait_fine(const StageArgs& a, const Nbr& nb, unsigned corr) {
     for (int q = 0; q < 4; ++q) {
       const int fs = nb.id[2 * D + side][q];
       if (a.member && a.member[fs] != a.call_id) continue;  // not advanced by this call
-      while (ld_acquire(a.cf_flag + fs) < D + 1) {
+      while (ld_acquire(a.cf_flag + fs) < a.flag_base + D + 1) {
         if (ld_volatile(a.abort_word)) return false;
         if (clock64() - t0 > a.wait_limit) {
           atomicOr(a.err, ERRBIT_TIMEOUT);
@@ -982,13 +1069,13 @@ __device__ __forceinline__ void correct_faces(const Shared<T>& sh, const StageAr
 // and the export of the faces onto a coarser neighbour.  Warp 7 also fetches
 // the next work item, one step per pass.  Returns whether fluxes were exported
 // (for x and y the export flag is raised here; z's after the update).
-template <typename T, int D>
-__device__ __forceinline__ bool direction_pass(const Shared<T>& sh, const StageArgs& a, const Meta& cur,
-                                               Meta& nxt, Pf& pf, double dt, Acc<T> (&acc)[NF], T& amax, T gamma,
-                                               T eta) {
+template <typename T, int D, bool FUSED>
+__device__ __forceinline__ bool direction_pass(const Shared<T>& sh, const StageArgs* st, const FusedArgs* fx,
+                                               int n_total, const StageArgs& a, const Meta& cur, Meta& nxt, Pf& pf,
+                                               double dt, Acc<T> (&acc)[NF], T& amax, T gamma, T eta) {
   const int tid = threadIdx.x;
   if (D == a.pf_pass) prefetch_update_rows(a, cur.s);  // the prefetch distance: a tuning parameter
-  if (D == 2 && (tid >> 5) == THREADS / 32 - 1) pf_load<sizeof(T) == 8>(a, pf);
+  if (D == 2 && (tid >> 5) == THREADS / 32 - 1) pf_load<sizeof(T) == 8>(st[0], n_total, pf);
   // A: PPM, one (field, pencil) task per iteration
 #pragma unroll 1
   for (int task = tid; task < NF * NPEN; task += THREADS) {
@@ -1017,18 +1104,22 @@ __device__ __forceinline__ bool direction_pass(const Shared<T>& sh, const StageA
     }
   }
   if ((tid >> 5) == THREADS / 32 - 1) {
-    if (D == 0) pf_ticket(a, pf);
-    if (D == 1) pf_id(a, pf);
-    if (D == 2) pf_store<sizeof(T) == 8>(dt, pf, nxt);
+    if (D == 0) pf_ticket(st[0], n_total, pf);
+    if (D == 1) pf_id<FUSED>(st, fx, n_total, pf);
+    if (D == 2) {
+      pf_store<sizeof(T) == 8>(dt, pf, nxt);
+      pf_ready<FUSED>(fx, pf, nxt);
+    }
   }
   __syncthreads();
   // the halo buffer is free: start gathering the next slabs; after z the tile
-  // is free too, and the mixed path starts copying the next interior
+  // is free too, and the mixed path starts copying the next interior (an item
+  // of the one-launch RK3 step whose inputs are not complete yet is gathered
+  // at the loop head instead, after its wait)
   if (D < 2) {
     gather<T, (D < 2 ? D + 1 : 2)>(a, cur.s, cur.nb, sh.halo);
-  } else if (nxt.s >= 0) {
-    if constexpr (sizeof(T) == 4) stage_interior_async(a.Sin, nxt.s, sh.tile);
-    gather<T, 0>(a, nxt.s, nxt.nb, sh.halo);
+  } else if (nxt.s >= 0 && nxt.ready) {
+    start_item<T>(next_src<T, FUSED>(st, nxt.stage), nxt.s, nxt.nb, sh.tile, sh.halo);
   }
   // B: one face per iteration
 #pragma unroll 1
@@ -1101,7 +1192,7 @@ __device__ __forceinline__ bool direction_pass(const Shared<T>& sh, const StageA
     __syncthreads();
     if (sizeof(T) == 8 && exported && tid == 0) {
       __threadfence();
-      st_release(a.cf_flag + cur.s, D + 1);
+      st_release(a.cf_flag + cur.s, a.flag_base + D + 1);
     }
   }
   return exported;
@@ -1305,79 +1396,159 @@ __device__ __forceinline__ unsigned update_cells(const StageArgs& a, int s, cons
   return bad | (nf >> 31);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(const __grid_constant__ StageArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Shared<T> sh;
-  sh.tile = reinterpret_cast<T*>(smem_raw);
-  sh.halo = reinterpret_cast<T*>(smem_raw + StageSmem<T>::interior);
-  sh.fsl = reinterpret_cast<T*>(smem_raw + StageSmem<T>::interior + StageSmem<T>::halo);
-  sh.fsr = sh.fsl + NF * FACES_DIR;
-  __shared__ Meta s_meta[2];
-  __shared__ unsigned long long s_red[THREADS / 32];
+// ---------------------------------------------------------------------------
+// The work loop.  A stage launch (FUSED false) processes its batch with st[0].
+// The one-launch RK3 step (FUSED true) processes 3 n items with st[k] for the
+// stage-k ones.  An item of that step whose inputs were not complete when it
+// was fetched (its halo was not gathered ahead) waits at the loop head, after
+// the CTA's previous item has finished, so that a CTA never waits while it
+// holds an unfinished item; every item waits only for items of lower tickets
+// (the previous stage; FP64: finer sub-grids of the same stage), which running
+// CTAs hold or have finished.  A finished item marks its sub-grid complete
+// (done[s] = k + 1, release), except, in mixed precision, a coarse sub-grid
+// with finer face neighbours: that one is marked by the CTA that brings its
+// arrival count to the stage's target, which first applies the coarse-fine
+// correction.
+// ---------------------------------------------------------------------------
 
-  const int tid = threadIdx.x;
-  const T gamma = T(a.gamma), eta = T(a.eta);
-  const double dt = a.dt_dev ? *a.dt_dev : a.dt;
-  const bool blend = a.beta != 1.0;
-  const bool shadow_out = sizeof(T) == 4 && a.Sout != nullptr;
-  unsigned bad = 0;
-
-  // prologue: the first work item, its neighbour table and x halo
-  if ((tid >> 5) == THREADS / 32 - 1) prefetch_meta<sizeof(T) == 8>(a, dt, s_meta[0]);
-  __syncthreads();
-  if (s_meta[0].s >= 0) {
-    if constexpr (sizeof(T) == 4) stage_interior_async(a.Sin, s_meta[0].s, sh.tile);
-    gather<T, 0>(a, s_meta[0].s, s_meta[0].nb, sh.halo);
+// One-launch step, warp 7: wait (bounded) until the stage-k item of s may
+// start; false if the wait gave up (ERRBIT_TIMEOUT, abort raised) or found the
+// launch aborted.
+__device__ __forceinline__ bool wait_ready(const FusedArgs* fx, const StageArgs& a0, int s, int k, const Nbr& nb) {
+  const int lane = threadIdx.x & 31;
+  const int id = lane < 24 ? nb.id[lane >> 2][lane & 3] : -1;
+  const int rel = lane < 24 ? nb.rel[lane >> 2] : 0;
+  const long long t0 = clock64();
+  while (!stage_ready(fx->done, s, k, id, rel)) {
+    int stop = 0;
+    if (lane == 0) {
+      if (ld_volatile(a0.abort_word)) {
+        stop = 1;
+      } else if (clock64() - t0 > a0.wait_limit) {
+        atomicOr(a0.err, ERRBIT_TIMEOUT);
+        atomicExch(a0.abort_word, 1);
+        stop = 1;
+      }
+    }
+    if (__shfl_sync(0xffffffffu, stop, 0)) return false;
+    __nanosleep(200);
   }
-  int par = 0;
-  for (;;) {
-    const Meta& cur = s_meta[par];
-    Meta& nxt = s_meta[par ^ 1];
-    const int item = cur.item;
-    if (item >= a.n_items) break;
-    const int s = cur.s;
-    if (s < 0) {  // bad id: skip it
-      __syncthreads();
-      if ((tid >> 5) == THREADS / 32 - 1) prefetch_meta<sizeof(T) == 8>(a, dt, nxt);
-      __syncthreads();
-      if (nxt.s >= 0) {
-        if constexpr (sizeof(T) == 4) stage_interior_async(a.Sin, nxt.s, sh.tile);
-        gather<T, 0>(a, nxt.s, nxt.nb, sh.halo);
-      }
-      par ^= 1;
-      continue;
-    }
-    if constexpr (sizeof(T) == 8) {
-      // FP64 path: interior of all fields, loaded synchronously
-      const double* Us = a.Uin + field_offset(s, 0);
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        const int c = tid + r * THREADS;
-        const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
-        const int g = (k + NG) * NP2 + (j + NG) * NP + (i + NG);
-        const int t = k * SK + j * SJ + i;
-#pragma unroll
-        for (int f = 0; f < NF; ++f) sh.tile[f * ISZ + t] = Us[(size_t)f * NP3 + g];
-      }
-    }
-    cp_async_wait_all();
-    __syncthreads();  // interior tile and x halo in place
-    const bool flux_only = cur.flux_only != 0;
-    if (sizeof(T) == 4 && a.fb_stamp && tid == 0) a.fb_stamp[s] = flux_only ? -a.call_id : a.call_id;
+  return true;
+}
 
-    Acc<T> acc[NF];
-    Pf pf;
-    T amax = T(0);
-    direction_pass<T, 0>(sh, a, cur, nxt, pf, dt, acc, amax, gamma, eta);
-    direction_pass<T, 1>(sh, a, cur, nxt, pf, dt, acc, amax, gamma, eta);
-    const bool exported_z = direction_pass<T, 2>(sh, a, cur, nxt, pf, dt, acc, amax, gamma, eta);
+// One-launch step, thread 0, after the stage-k item of s (the CTA's writes
+// ordered before it by a barrier): mark the item complete, or, for a coarse
+// sub-grid with finer neighbours (mixed, correcting), count its arrival; count
+// its arrival at each coarser neighbour.  Returns the number of corrections
+// this item completes, their rows in corr[].
+__device__ __forceinline__ int complete_item(const FusedArgs* fx, bool correct, int s, int k, const Nbr& nb,
+                                             int* corr) {
+  __threadfence();
+  const int own = correct ? fx->cf_slot[s] : -1;
+  if (own < 0) st_release(fx->done + s, k + 1);
+  int nc = 0;
+  if (correct) {
+    for (int face = 0; face < 6; ++face) {
+      if (nb.rel[face] != -1) continue;
+      const int slot = fx->cf_slot[nb.id[face][0]];
+      if (slot >= 0 && atomicAdd(fx->arrive + slot, 1) + 1 == (k + 1) * fx->cf_target[slot] && nc < 8)
+        corr[nc++] = slot;
+    }
+    if (own >= 0 && atomicAdd(fx->arrive + own, 1) + 1 == (k + 1) * fx->cf_target[own] && nc < 8) corr[nc++] = own;
+    if (nc) __threadfence();
+  }
+  return nc;
+}
 
-    // update of the owned cells (and, mixed, the output's shadow); an item
-    // that only exports its fluxes writes no state and posts no speed
-    if (flux_only) {
-      amax = T(0);
-    } else if (sizeof(T) == 4 && a.mode != 0) {
+// One-launch step (mixed), every thread of the CTA: apply the nc corrections
+// in corr[] (arguments r of the stage) and mark those sub-grids complete.  Out
+// of line, and called only when there is one: its registers would crowd the
+// stage's.
+#ifndef HYDRO_FUSED_CORR_IPT
+#define HYDRO_FUSED_CORR_IPT 1
+#endif
+__device__ __noinline__ void run_corrections(const RefluxArgs r, int k, int nc, const int* corr, int32_t* done) {
+  __shared__ reflux::CorrSmem s_cs;
+  for (int q = 0; q < nc; ++q) {
+    const int row = corr[q];
+    reflux::correct_coarse<float, THREADS, HYDRO_FUSED_CORR_IPT, true>(r, row, s_cs);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      st_release(done + __ldg(r.cf + (size_t)row * CF_ENTRY), k + 1);
+    }
+  }
+}
+
+// One item (cur) of stage K (FUSED; else st[0]'s stage).  Returns false when
+// the launch must stop (a wait gave up).
+template <typename T, bool FUSED, int K>
+__device__ __forceinline__ bool process_item(const Shared<T>& sh, const StageArgs* st, const FusedArgs* fx,
+                                             int n_total, const Meta& cur, Meta& nxt, double dt, T gamma, T eta,
+                                             unsigned& bad, unsigned long long* s_red) {
+  const int tid = threadIdx.x;
+  const StageArgs& a = st[K];
+  const int s = cur.s;
+  if constexpr (FUSED) {
+    if (!cur.ready) {
+      // wait (bounded) until the item's inputs are complete, then gather
+      __shared__ int s_go;
+      if ((tid >> 5) == THREADS / 32 - 1) {
+        const bool go = wait_ready(fx, st[0], s, K, cur.nb);
+        if ((tid & 31) == 0) s_go = go;
+      }
+      __syncthreads();
+      if (!s_go) return false;
+      start_item<T>(stage_src<T>(a), s, cur.nb, sh.tile, sh.halo);
+    }
+  }
+  if constexpr (sizeof(T) == 8) {
+    // FP64 path: interior of all fields, loaded synchronously
+    const double* Us = a.Uin + field_offset(s, 0);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int c = tid + r * THREADS;
+      const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
+      const int g = (k + NG) * NP2 + (j + NG) * NP + (i + NG);
+      const int t = k * SK + j * SJ + i;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) sh.tile[f * ISZ + t] = Us[(size_t)f * NP3 + g];
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();  // interior tile and x halo in place
+  const bool flux_only = cur.flux_only != 0;
+  if (sizeof(T) == 4 && a.fb_stamp && tid == 0) a.fb_stamp[s] = flux_only ? -a.call_id : a.call_id;
+
+  Acc<T> acc[NF];
+  Pf pf;
+  T amax = T(0);
+  direction_pass<T, 0, FUSED>(sh, st, fx, n_total, a, cur, nxt, pf, dt, acc, amax, gamma, eta);
+  direction_pass<T, 1, FUSED>(sh, st, fx, n_total, a, cur, nxt, pf, dt, acc, amax, gamma, eta);
+  const bool exported_z = direction_pass<T, 2, FUSED>(sh, st, fx, n_total, a, cur, nxt, pf, dt, acc, amax, gamma, eta);
+
+  // update of the owned cells (and, mixed, the output's shadow); an item
+  // that only exports its fluxes writes no state and posts no speed.  The
+  // one-launch step's stages are fixed: mixed stage K runs mode K + 1, FP64
+  // stage K blends for K > 0 and writes no shadow.
+  if (flux_only) {
+    amax = T(0);
+  } else if constexpr (FUSED && sizeof(T) == 4) {
+    const float lh = cur.lh, ll = cur.ll;
+    if constexpr (K == 0)
+      bad |= update_inc<1, true>(a, s, acc, lh, ll);
+    else if constexpr (K == 1)
+      bad |= update_inc<2, true>(a, s, acc, lh, ll);
+    else if (a.Sout != nullptr)
+      bad |= update_inc<3, true>(a, s, acc, lh, ll);
+    else
+      bad |= update_inc<3, false>(a, s, acc, lh, ll);
+  } else if constexpr (FUSED) {
+    bad |= update_cells<T, (K > 0), false>(a, s, acc, cur.lam);
+  } else {
+    const bool blend = a.beta != 1.0;
+    const bool shadow_out = sizeof(T) == 4 && a.Sout != nullptr;
+    if (sizeof(T) == 4 && a.mode != 0) {
       if constexpr (sizeof(T) == 4) {
         const float lh = cur.lh, ll = cur.ll;
         if (a.mode == 1)
@@ -1400,50 +1571,124 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(
       else
         bad |= update_cells<T, false, false>(a, s, acc, cur.lam);
     }
+  }
 
-    // largest face speed of this sub-grid (non-negative values order as their bits)
-    unsigned long long bits;
+  // largest face speed of this sub-grid (non-negative values order as their bits)
+  unsigned long long bits;
+  if constexpr (sizeof(T) == 4) {
+    unsigned b = __float_as_uint((float)amax) & 0x7fffffffu;
+    b = __reduce_max_sync(0xffffffffu, b);
+    bits = b;
+  } else {
+    bits = (unsigned long long)__double_as_longlong((double)amax) & 0x7fffffffffffffffull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long w = __shfl_xor_sync(0xffffffffu, bits, o);
+      bits = w > bits ? w : bits;
+    }
+  }
+  if ((tid & 31) == 0) s_red[tid >> 5] = bits;
+  __syncthreads();
+  if (sizeof(T) == 8 && exported_z && tid == 0) {
+    __threadfence();
+    st_release(a.cf_flag + s, a.flag_base + 3);
+  }
+  if (tid == 0) {
+    unsigned long long m = 0;
+#pragma unroll
+    for (int w = 0; w < THREADS / 32; ++w) m = s_red[w] > m ? s_red[w] : m;
+    double v;
+    if constexpr (sizeof(T) == 4)
+      v = (double)__uint_as_float((unsigned)m);
+    else
+      v = __longlong_as_double((long long)m);
+    const unsigned long long mask = 0x7fffffffffffffffull;
+    atomicMax(&a.max_speed[0], (unsigned long long)__double_as_longlong(v) & mask);
+    const double vdx = sizeof(T) == 8 ? __ddiv_rn(v, cur.sdx) : v * cur.sdx;
+    atomicMax(&a.max_speed[1], (unsigned long long)__double_as_longlong(vdx) & mask);
+  }
+  if constexpr (FUSED) {
+    __shared__ int s_corr[8];
+    __shared__ int s_ncorr;
+    if (tid == 0) s_ncorr = complete_item(fx, sizeof(T) == 4 && a.fb, s, K, cur.nb, s_corr);
     if constexpr (sizeof(T) == 4) {
-      unsigned b = __float_as_uint((float)amax) & 0x7fffffffu;
-      b = __reduce_max_sync(0xffffffffu, b);
-      bits = b;
-    } else {
-      bits = (unsigned long long)__double_as_longlong((double)amax) & 0x7fffffffffffffffull;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long w = __shfl_xor_sync(0xffffffffu, bits, o);
-        bits = w > bits ? w : bits;
-      }
+      __syncthreads();
+      const int nc = s_ncorr;
+      if (nc) run_corrections(fx->rf[K], K, nc, s_corr, fx->done);
     }
-    if ((tid & 31) == 0) s_red[tid >> 5] = bits;
-    __syncthreads();
-    if (sizeof(T) == 8 && exported_z && tid == 0) {
-      __threadfence();
-      st_release(a.cf_flag + s, 3);
+  }
+  return true;
+}
+
+template <typename T, bool FUSED>
+__device__ __forceinline__ void stage_body(const StageArgs* __restrict__ st, const FusedArgs* __restrict__ fx) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Shared<T> sh;
+  sh.tile = reinterpret_cast<T*>(smem_raw);
+  sh.halo = reinterpret_cast<T*>(smem_raw + StageSmem<T>::interior);
+  sh.fsl = reinterpret_cast<T*>(smem_raw + StageSmem<T>::interior + StageSmem<T>::halo);
+  sh.fsr = sh.fsl + NF * FACES_DIR;
+  __shared__ Meta s_meta[2];
+  __shared__ unsigned long long s_red[THREADS / 32];
+
+  const StageArgs& a0 = st[0];
+  const int tid = threadIdx.x;
+  const bool warp7 = (tid >> 5) == THREADS / 32 - 1;
+  const T gamma = T(a0.gamma), eta = T(a0.eta);
+  const double dt = a0.dt_dev ? *a0.dt_dev : a0.dt;
+  const int n_total = FUSED ? 3 * fx->n : a0.n_items;
+  unsigned bad = 0;
+
+  // prologue: the first work item, its neighbour table and x halo
+  if (warp7) prefetch_meta<sizeof(T) == 8, FUSED>(st, fx, n_total, dt, s_meta[0]);
+  __syncthreads();
+  if (s_meta[0].s >= 0 && s_meta[0].ready)
+    start_item<T>(next_src<T, FUSED>(st, s_meta[0].stage), s_meta[0].s, s_meta[0].nb, sh.tile, sh.halo);
+  int par = 0;
+  for (;;) {
+    const Meta& cur = s_meta[par];
+    Meta& nxt = s_meta[par ^ 1];
+    if (cur.item >= n_total) break;
+    if (cur.s < 0) {  // bad id: skip it
+      __syncthreads();
+      if (warp7) prefetch_meta<sizeof(T) == 8, FUSED>(st, fx, n_total, dt, nxt);
+      __syncthreads();
+      if (nxt.s >= 0 && nxt.ready) start_item<T>(next_src<T, FUSED>(st, nxt.stage), nxt.s, nxt.nb, sh.tile, sh.halo);
+      par ^= 1;
+      continue;
     }
-    if (tid == 0) {
-      unsigned long long m = 0;
-#pragma unroll
-      for (int w = 0; w < THREADS / 32; ++w) m = s_red[w] > m ? s_red[w] : m;
-      double v;
-      if constexpr (sizeof(T) == 4)
-        v = (double)__uint_as_float((unsigned)m);
+    bool go;
+    if constexpr (FUSED) {
+      const int k = cur.stage;
+      if (k == 0)
+        go = process_item<T, true, 0>(sh, st, fx, n_total, cur, nxt, dt, gamma, eta, bad, s_red);
+      else if (k == 1)
+        go = process_item<T, true, 1>(sh, st, fx, n_total, cur, nxt, dt, gamma, eta, bad, s_red);
       else
-        v = __longlong_as_double((long long)m);
-      const unsigned long long mask = 0x7fffffffffffffffull;
-      atomicMax(&a.max_speed[0], (unsigned long long)__double_as_longlong(v) & mask);
-      const double vdx = sizeof(T) == 8 ? __ddiv_rn(v, cur.sdx) : v * cur.sdx;
-      atomicMax(&a.max_speed[1], (unsigned long long)__double_as_longlong(vdx) & mask);
+        go = process_item<T, true, 2>(sh, st, fx, n_total, cur, nxt, dt, gamma, eta, bad, s_red);
+    } else {
+      go = process_item<T, false, 0>(sh, st, fx, n_total, cur, nxt, dt, gamma, eta, bad, s_red);
     }
+    if (!go) break;
     par ^= 1;
   }
   cp_async_wait_all();
-  if (bad) atomicOr(a.err, ERRBIT_NONFINITE);
+  if (bad) atomicOr(a0.err, ERRBIT_NONFINITE);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(const __grid_constant__ StageArgs a) {
+  stage_body<T, false>(&a, nullptr);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) rk3_kernel(const __grid_constant__ FusedArgs F) {
+  stage_body<T, true>(F.st, &F);
 }
 
 // The kernel's shared-memory limit is an attribute of the function on each
 // device: set it once per device (under a lock, for callers on several threads).
-template <typename T>
+template <typename T, bool FUSED>
 cudaError_t configure_smem() {
   constexpr int kMaxDevices = 64;
   static std::mutex mu;
@@ -1454,7 +1699,10 @@ cudaError_t configure_smem() {
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(mu);
   if (!done[dev]) {
-    e = cudaFuncSetAttribute(stage_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)StageSmem<T>::total);
+    if constexpr (FUSED)
+      e = cudaFuncSetAttribute(rk3_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)StageSmem<T>::total);
+    else
+      e = cudaFuncSetAttribute(stage_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)StageSmem<T>::total);
     if (e != cudaSuccess) return e;
     done[dev] = true;
   }
@@ -1463,19 +1711,30 @@ cudaError_t configure_smem() {
 
 template <typename T>
 cudaError_t launch(const StageArgs& a, int grid, cudaStream_t st) {
-  cudaError_t e = configure_smem<T>();
+  cudaError_t e = configure_smem<T, false>();
   if (e != cudaSuccess) return e;
   stage_kernel<T><<<grid, THREADS, StageSmem<T>::total, st>>>(a);
   return cudaGetLastError();
 }
 
 template <typename T>
+cudaError_t launch_fused(const FusedArgs& f, int grid, cudaStream_t st) {
+  cudaError_t e = configure_smem<T, true>();
+  if (e != cudaSuccess) return e;
+  rk3_kernel<T><<<grid, THREADS, StageSmem<T>::total, st>>>(f);
+  return cudaGetLastError();
+}
+
+template <typename T, bool FUSED>
 int blocks_per_sm() {
   int n = 0;
-  if (configure_smem<T>() != cudaSuccess) return 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<T>, THREADS, StageSmem<T>::total) !=
-      cudaSuccess)
-    return 1;
+  if (configure_smem<T, FUSED>() != cudaSuccess) return 1;
+  cudaError_t e;
+  if constexpr (FUSED)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rk3_kernel<T>, THREADS, StageSmem<T>::total);
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<T>, THREADS, StageSmem<T>::total);
+  if (e != cudaSuccess) return 1;
   return n > 0 ? n : 1;
 }
 
@@ -1515,7 +1774,11 @@ bool encode_state_map(CUtensorMap* tm, const double* U, int n) {
 
 cudaError_t launch_stage_fp64(const StageArgs& a, int grid, cudaStream_t st) { return launch<double>(a, grid, st); }
 cudaError_t launch_stage_mixed(const StageArgs& a, int grid, cudaStream_t st) { return launch<float>(a, grid, st); }
-int stage_blocks_per_sm_fp64() { return blocks_per_sm<double>(); }
-int stage_blocks_per_sm_mixed() { return blocks_per_sm<float>(); }
+cudaError_t launch_rk3_fp64(const FusedArgs& f, int grid, cudaStream_t st) { return launch_fused<double>(f, grid, st); }
+cudaError_t launch_rk3_mixed(const FusedArgs& f, int grid, cudaStream_t st) { return launch_fused<float>(f, grid, st); }
+int stage_blocks_per_sm_fp64() { return blocks_per_sm<double, false>(); }
+int stage_blocks_per_sm_mixed() { return blocks_per_sm<float, false>(); }
+int rk3_blocks_per_sm_fp64() { return blocks_per_sm<double, true>(); }
+int rk3_blocks_per_sm_mixed() { return blocks_per_sm<float, true>(); }
 
 }  // namespace hydro

@@ -9,7 +9,9 @@ launching stream after a warm-up replay.  The space:
   prefetch_pass      the direction pass (0 x, 1 y, 2 z) in which a stage pulls
                      the rows its update reads into L2 (the prefetch distance);
   reflux_shape       threads per CTA and items per thread of the mixed
-                     correction pass (mixed handles only).
+                     correction pass (mixed handles only);
+  fused_rk3          the step as three stage launches (0) or one persistent
+                     launch with per-sub-grid completion counters (1).
 Results do not depend on any of them (the kernels' arithmetic and order are
 fixed; only the launch shape changes), which a GPU test checks point by point.
 The best point is cached in a JSON file (``$HYDRO_TUNE_CACHE``, else
@@ -31,16 +33,19 @@ PARAMS = {
     "stage_ctas_per_sm": HY.PARAM_STAGE_CTAS_PER_SM,
     "prefetch_pass": HY.PARAM_PREFETCH_PASS,
     "reflux_shape": HY.PARAM_REFLUX_SHAPE,
+    "fused_rk3": HY.PARAM_FUSED_RK3,
 }
 
 SPACE_FP64 = {
     "stage_ctas_per_sm": (1,),      # the FP64 stage fits one CTA per SM
     "prefetch_pass": (0, 1, 2),
+    "fused_rk3": (0, 1),
 }
 SPACE_MIXED = {
     "stage_ctas_per_sm": (1, 2),
     "prefetch_pass": (0, 1, 2),
     "reflux_shape": (0, 1, 2, 3),
+    "fused_rk3": (0, 1),
 }
 
 
