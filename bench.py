@@ -56,7 +56,7 @@ FP64_PEAK_INST = 152 * 2 * 2.070e9
 FP64_PEAK_TFLOPS = 2 * FP64_PEAK_INST / 1e12
 # DRAM bytes (read + write) per cell-update of the mixed stage kernel from one ncu capture
 # (average of the three RK3 stage launches), valid only for the kernel source it was taken on.
-STAGE_TRAFFIC = {"sha256_prefix": "026d5c1d4fcba5cf", "bytes_per_cell": 303.5,
+STAGE_TRAFFIC = {"sha256_prefix": "7deb70a7dc1e0df2", "bytes_per_cell": 303.5,
                  "source": "ncu capture of the three RK3 stage launches on the 4097-leaf reduced binary octree "
                            "(average), scaled by cells"}
 
@@ -83,6 +83,10 @@ def parse():
     p.add_argument("--skip-e2e", action="store_true")
     p.add_argument("--skip-fp64", action="store_true")
     p.add_argument("--skip-cpu", action="store_true")
+    p.add_argument("--stage-only", choices=["mixed", "fp64"], default=None,
+                   help="profiling case: one RK3 step (mixed: the three stage launches of the increment form with "
+                        "their correction passes) or one FP64 stage (beta = 1) on --config with default launch "
+                        "parameters, then exit; prints no benchmark line")
     p.add_argument("--sweep", action="store_true",
                    help="per-configuration table (one JSON line per configuration and precision, errors against "
                         "the oracle, oracle timings); not the benchmark line")
@@ -329,6 +333,30 @@ def run_sweep(args):
     return 0
 
 
+def run_stage_only(args):
+    """A small, fixed launch sequence for ncu (no tuner, no timing)."""
+    import torch
+    from paper_2210_06437_gb300 import build, hydro as HY
+    from paper_2210_06437_gb300 import workloads as W
+    build.build()
+    w = W.config(args.config)
+    U = torch.from_numpy(w.state()).cuda()
+    ids = torch.as_tensor(w.batches.ids, device="cuda")
+    g = HY.HydroGrid(w.grid, precision=args.stage_only)
+    ms = torch.zeros(2, dtype=torch.float64, device="cuda")
+    s1 = torch.empty_like(U)
+    g.step(U, 0.0, U_out=s1, ids=ids, batch_offsets=w.batches.offsets, max_speed=ms)
+    dt = 0.4 / float(ms[1])
+    if args.stage_only == "mixed":
+        g.rk3_step(U, dt, s1, torch.empty_like(U), ids=ids, batch_offsets=w.batches.offsets)
+    else:
+        g.step(U, dt, U_out=s1, ids=ids, batch_offsets=w.batches.offsets)
+    g.sync()
+    g.close()
+    print("stage-only %s config %d: %d sub-grids" % (args.stage_only, args.config, w.grid.n))
+    return 0
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -339,6 +367,8 @@ def main():
         return run_reference(args)
     if args.sweep:
         return run_sweep(args)
+    if args.stage_only:
+        return run_stage_only(args)
     import torch
     rank, world, local = dist_info()
     pg = None
@@ -557,9 +587,12 @@ def main():
     traffic = stage_traffic_bytes(cells)
     roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": traffic,
             "traffic_source": STAGE_TRAFFIC["source"] if traffic else "kernel changed since the last capture",
-            "kernel": "stage_kernel<float>, the 3 stage launches of the mixed SSP-RK3 graph (increment form), "
-                      "average; each launch's time includes the coarse-fine flux-correction pass that follows it "
-                      "(reflux_kernel, about 4 % of it)", "peak_source": hbm_src,
+            "kernel": ("rk3_kernel<float>, the one launch of each mixed SSP-RK3 step (three stages and their "
+                       "coarse-fine corrections), a third of its time per stage"
+                       if r["tuned"].get("fused_rk3") else
+                       "stage_kernel<float>, the 3 stage launches of the mixed SSP-RK3 graph (increment form), "
+                       "average; each launch's time includes the coarse-fine flux-correction pass that follows it "
+                       "(reflux_kernel, about 4 % of it)"), "peak_source": hbm_src,
             "bytes_per_cell_update": BYTES_PER_CELL_RK3_STAGE, "launch_ms": t_st * 1e3}
     kernels = {
         "stage_mixed_ms": t_st * 1e3, "stage_mixed_single_beta1_ms": r["t_single"] * 1e3,
@@ -596,7 +629,9 @@ def main():
                                                "= %.1f instructions, %.1f flops)" % (FP64_INST_PER_CELL_STAGE,
                                                                                      FLOPS_PER_CELL_STAGE),
                                      "peak_source": "unit count: 152 SMs x 2 FP64 instructions/clk x 2.07 GHz",
-                                     "kernel": "stage_kernel<double>", "launch_ms": f["t_stage"] * 1e3,
+                                     "kernel": "rk3_kernel<double> (a third of each step's launch)"
+                                               if f["tuned"].get("fused_rk3") else "stage_kernel<double>",
+                                     "launch_ms": f["t_stage"] * 1e3,
                                      "hbm_frac": BYTES_PER_CELL_RK3_STAGE * cells / f["t_stage"] / 1e9 / hbm},
                         "gpu_launches": f["launches"]}
         line["mixed_speedup_vs_fp64"] = f["t_step"] / r["t_step"]
