@@ -41,7 +41,11 @@ def build(force: bool = False) -> str:
 class _Grid(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("gamma", ctypes.c_double), ("de_switch", ctypes.c_double),
                 ("flux_form", ctypes.c_int32), ("dx", ctypes.c_void_p), ("neighbor", ctypes.c_void_p),
-                ("neighbor_rel", ctypes.c_void_p), ("octant", ctypes.c_void_p), ("reflux", ctypes.c_int32)]
+                ("neighbor_rel", ctypes.c_void_p), ("octant", ctypes.c_void_p), ("reflux", ctypes.c_int32),
+                ("cw84", ctypes.c_int32)]
+
+# CW84 PPM extensions (Oracle(cw84=...)): shock flattening, contact steepening of the density
+CW84_FLATTEN, CW84_STEEPEN = 1, 2
 
 
 _lib = None
@@ -68,6 +72,8 @@ def lib():
         L.oracle_margin_cells.argtypes = [ctypes.POINTER(_Grid), ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                           ctypes.c_double, ctypes.c_void_p]
         L.oracle_margin_cells.restype = ctypes.c_long
+        L.oracle_ghost_cell.argtypes = [ctypes.POINTER(_Grid), ctypes.c_void_p] + [ctypes.c_int] * 6
+        L.oracle_ghost_cell.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -104,7 +110,7 @@ class Oracle:
     """Oracle bound to one grid descriptor (see ``paper_2210_06437_gb300.workloads.Grid``)."""
 
     def __init__(self, grid, flux_form: int = 0, gamma: Optional[float] = None, de_switch: Optional[float] = None,
-                 reflux: bool = True):
+                 reflux: bool = True, cw84: int = 0):
         self.grid = grid
         self._dx = np.ascontiguousarray(grid.dx, np.float64)
         self._nb = np.ascontiguousarray(grid.neighbor, np.int32)
@@ -113,7 +119,7 @@ class Oracle:
         self._g = _Grid(grid.n, grid.gamma if gamma is None else gamma,
                         grid.de_switch if de_switch is None else de_switch, flux_form,
                         self._dx.ctypes.data, self._nb.ctypes.data, self._rel.ctypes.data, self._oct.ctypes.data,
-                        1 if reflux else 0)
+                        1 if reflux else 0, int(cw84))
 
     def _check(self, U):
         assert U.dtype == np.float64 and U.flags.c_contiguous and U.shape == (self.grid.n, NF, NP, NP, NP)
@@ -184,6 +190,13 @@ class Oracle:
         k = lib().oracle_margin_cells(ctypes.byref(self._g), None if ids is None else ids.ctypes.data,
                                       0 if ids is None else len(ids), U.ctypes.data, 64.0 * eps, m.ctypes.data)
         return m, int(k)
+
+    def ghost_cell(self, U: np.ndarray, s: int, face: int, ga: int, c1: int, c2: int, f: int) -> float:
+        """The ghost value of field f of sub-grid s across face at interior
+        coordinate ga along its axis (any depth) by the ghost-fill rules."""
+        self._check(U)
+        return float(lib().oracle_ghost_cell(ctypes.byref(self._g), U.ctypes.data, int(s), int(face), int(ga),
+                                             int(c1), int(c2), int(f)))
 
     def totals(self, U: np.ndarray) -> np.ndarray:
         self._check(U)

@@ -65,6 +65,26 @@ static double limited_slope(double qm, double q0, double qp) {
   return delta > 0.0 ? m : -m;
 }
 
+/* CW84 eq. 1.10: flatten at a local extremum, else pull the far face in so
+ * that the parabola has no interior extremum. */
+static void parabola_limit(double a, double *lp, double *rp) {
+  double l = *lp, r = *rp;
+  if ((r - a) * (a - l) <= 0.0) {
+    l = a;
+    r = a;
+  } else {
+    double da = r - l;
+    double lhs = da * (a - 0.5 * (l + r));
+    double rhs = da * da / 6.0;
+    if (lhs > rhs)
+      l = 3.0 * a - 2.0 * r;
+    else if (-rhs > lhs)
+      r = 3.0 * a - 2.0 * l;
+  }
+  *lp = l;
+  *rp = r;
+}
+
 void oracle_ppm_pencil(const double *q, double *aL, double *aR) {
   double dm[NP];
   double face[NP]; /* face[m] is the interpolant at face m + 1/2 */
@@ -72,25 +92,110 @@ void oracle_ppm_pencil(const double *q, double *aL, double *aR) {
   /* CW84 eq. 1.6 with limited slopes: a_{m+1/2} = (q_m + q_{m+1})/2 - (dm_{m+1} - dm_m)/6 */
   for (int m = 1; m <= 11; ++m) face[m] = 0.5 * (q[m] + q[m + 1]) - (dm[m + 1] - dm[m]) / 6.0;
   for (int m = 2; m <= 11; ++m) {
-    double a = q[m];
     double l = face[m - 1];
     double r = face[m];
-    /* CW84 eq. 1.10: flatten at a local extremum, else pull the far face in so
-     * that the parabola has no interior extremum. */
-    if ((r - a) * (a - l) <= 0.0) {
-      l = a;
-      r = a;
-    } else {
-      double da = r - l;
-      double lhs = da * (a - 0.5 * (l + r));
-      double rhs = da * da / 6.0;
-      if (lhs > rhs)
-        l = 3.0 * a - 2.0 * r;
-      else if (-rhs > lhs)
-        r = 3.0 * a - 2.0 * l;
-    }
+    parabola_limit(q[m], &l, &r);
     aL[m] = l;
     aR[m] = r;
+  }
+}
+
+/* ------------------------------------------------------------------------- */
+/* CW84 shock flattening and contact steepening                               */
+/* ------------------------------------------------------------------------- */
+
+/* Flattening coefficients f[m] of cells m = 2..11 of a pencil (CW84 Section 4,
+ * eqs. 4.1-4.5, constants epsilon = 0.33, omega1 = 0.75, omega2 = 10): with
+ * P[m + 1] = p_m for m = -1..14 (the pressure of cell m; m = -1 and 14 are the
+ * fourth ghost layer) and u[m] the velocity along the pencil (m = 0..13),
+ *   ft_m = max(0, min(1, omega2 ((p_{m+1} - p_{m-1}) / (p_{m+2} - p_{m-2}) - omega1)))
+ * where cell m sees a shock, |p_{m+1} - p_{m-1}| > epsilon min(p_{m+1}, p_{m-1})
+ * and u_{m-1} - u_{m+1} > 0, else ft_m = 0 (m = 1..12); then
+ *   f_m = max(ft_m, ft_{m - sigma_m}),  sigma_m = sgn(p_{m+1} - p_{m-1}),
+ * the larger of the cell's own and its upstream neighbour's. */
+static void flattening(const double *P, const double *u, double *f) {
+  double ft[NP];
+  for (int m = 1; m <= 12; ++m) {
+    const double pm1 = P[m], pp1 = P[m + 2], pm2 = P[m - 1], pp2 = P[m + 3];
+    const double dp = pp1 - pm1;
+    const double pmin = pp1 < pm1 ? pp1 : pm1;
+    ft[m] = 0.0;
+    if (fabs(dp) > 0.33 * pmin && u[m - 1] - u[m + 1] > 0.0) {
+      const double t = 10.0 * (dp / (pp2 - pm2) - 0.75);
+      double v = t > 1.0 ? 1.0 : t;
+      ft[m] = v > 0.0 ? v : 0.0;
+    }
+  }
+  for (int m = 2; m <= 11; ++m) {
+    const double dp = P[m + 2] - P[m];
+    const int up = dp > 0.0 ? m - 1 : (dp < 0.0 ? m + 1 : m);
+    f[m] = ft[up] > ft[m] ? ft[up] : ft[m];
+  }
+}
+
+/* Contact steepening coefficient eta of cell m from the density r (CW84 eqs.
+ * 1.14-1.17 on a uniform pencil, constants eta1 = 20, eta2 = 0.05,
+ * epsilon = 0.01, K0 = 0.1): with d2_k = (r_{k+1} + r_{k-1}) - 2 r_k,
+ *   etat = -(d2_{m+1} - d2_{m-1}) / (6 (r_{m+1} - r_{m-1}))
+ * where d2_{m+1} d2_{m-1} < 0, |r_{m+1} - r_{m-1}| - epsilon min(|r_{m+1}|, |r_{m-1}|) > 0
+ * and the jump is a contact, gamma K0 |r_{m+1} - r_{m-1}| / min(r_{m+1}, r_{m-1}) >=
+ * |p_{m+1} - p_{m-1}| / min(p_{m+1}, p_{m-1}); else etat = 0;
+ *   eta = max(0, min(eta1 (etat - eta2), 1)). */
+static double steepening(const double *r, const double *P, double gamma, int m) {
+  const double d2p = (r[m + 2] + r[m]) - 2.0 * r[m + 1];
+  const double d2m = (r[m] + r[m - 2]) - 2.0 * r[m - 1];
+  const double dr = r[m + 1] - r[m - 1];
+  const double a1 = fabs(r[m + 1]), a0 = fabs(r[m - 1]);
+  const double amin = a1 < a0 ? a1 : a0;
+  double etat = 0.0;
+  if (d2p * d2m < 0.0 && fabs(dr) - 0.01 * amin > 0.0) {
+    const double rmin = r[m + 1] < r[m - 1] ? r[m + 1] : r[m - 1];
+    const double pp1 = P[m + 2], pm1 = P[m];
+    const double pmin = pp1 < pm1 ? pp1 : pm1;
+    if (gamma * 0.1 * fabs(dr) / rmin >= fabs(pp1 - pm1) / pmin) etat = -(d2p - d2m) / (6.0 * dr);
+  }
+  const double t = 20.0 * (etat - 0.05);
+  const double e = t > 1.0 ? 1.0 : t;
+  return e > 0.0 ? e : 0.0;
+}
+
+/* PPM of the NF fields of one pencil with the CW84 extensions of `flags`
+ * (bit 0 flattening, bit 1 contact steepening), in CW84's order: interpolant
+ * (eq. 1.6), steepening, flattening, parabola limiter (eq. 1.10).  P and u as
+ * for flattening().  Both coefficients are properties of the cell, applied to
+ * every conserved field: the flattening one from the pressure and velocity,
+ * the steepening one detected on the density; with conserved variables this
+ * keeps a contact (velocity and pressure uniform, every field affine in the
+ * density) consistent, where steepening the density alone would not.  The
+ * steepened faces are l -> l (1 - eta) + (q_{m-1} + dm_{m-1}/2) eta and
+ * r -> r (1 - eta) + (q_{m+1} - dm_{m+1}/2) eta, dm the limited slopes of eq.
+ * 1.8; the flattened ones l -> f q_m + (1 - f) l, r -> f q_m + (1 - f) r. */
+static void ppm_pencil_cw84(double q[NF][NP], const double *P, const double *u, double gamma, int flags,
+                            double aL[NF][NP], double aR[NF][NP]) {
+  double fl[NP], st[NP];
+  for (int m = 0; m < NP; ++m) fl[m] = st[m] = 0.0;
+  if (flags & 1) flattening(P, u, fl);
+  if (flags & 2)
+    for (int m = 2; m <= 11; ++m) st[m] = steepening(q[F_RHO], P, gamma, m);
+  for (int f = 0; f < NF; ++f) {
+    double dm[NP], face[NP];
+    for (int m = 1; m <= 12; ++m) dm[m] = limited_slope(q[f][m - 1], q[f][m], q[f][m + 1]);
+    for (int m = 1; m <= 11; ++m) face[m] = 0.5 * (q[f][m] + q[f][m + 1]) - (dm[m + 1] - dm[m]) / 6.0;
+    for (int m = 2; m <= 11; ++m) {
+      const double a = q[f][m];
+      double l = face[m - 1], r = face[m];
+      if (st[m] > 0.0) {
+        l = l * (1.0 - st[m]) + (q[f][m - 1] + 0.5 * dm[m - 1]) * st[m];
+        r = r * (1.0 - st[m]) + (q[f][m + 1] - 0.5 * dm[m + 1]) * st[m];
+      }
+      if (fl[m] > 0.0) {
+        l = fl[m] * a + (1.0 - fl[m]) * l;
+        r = fl[m] * a + (1.0 - fl[m]) * r;
+      }
+      parabola_limit(a, &l, &r);
+      aL[f][m] = l;
+      aR[f][m] = r;
+    }
   }
 }
 
@@ -161,6 +266,9 @@ typedef struct {
 
 /* Face fluxes of every pencil of sub-grid s into w->flux; returns the largest
  * face speed. */
+static double ghost_value(const oracle_grid *g, const double *U, int s, int a, int side, int ga, int c1, int c2,
+                          int f);
+
 static double flux_subgrid(const oracle_grid *g, int s, const double *Uin, work_t *w) {
   double q[NF][NP], aL[NF][NP], aR[NF][NP];
   double UL[NF], UR[NF], F[NF];
@@ -168,9 +276,28 @@ static double flux_subgrid(const oracle_grid *g, int s, const double *Uin, work_
   for (int d = 0; d < 3; ++d) {
     for (int t2 = NG; t2 < NG + NX; ++t2) {
       for (int t1 = NG; t1 < NG + NX; ++t1) {
-        for (int f = 0; f < NF; ++f) {
+        for (int f = 0; f < NF; ++f)
           for (int m = 0; m < NP; ++m) q[f][m] = Uin[pencil_at(s, f, d, t1, t2, m)];
-          oracle_ppm_pencil(q[f], aL[f], aR[f]);
+        if (g->cw84) {
+          /* cell pressures along the pencil, m = -1..14 (the fourth ghost
+           * layer from the neighbours' interiors by the ghost-fill rules), and
+           * the velocities along it, m = 0..13 */
+          double P[NP + 2], u[NP], cell[NF], c;
+          for (int m = -1; m <= NP; ++m) {
+            if (m < 0 || m == NP) {
+              const int side = m < 0 ? 0 : 1;
+              for (int f = 0; f < NF; ++f)
+                cell[f] = ghost_value(g, Uin, s, d, side, side ? NX + NG : -1 - NG, t1 - NG, t2 - NG, f);
+            } else {
+              for (int f = 0; f < NF; ++f) cell[f] = q[f][m];
+            }
+            double um;
+            oracle_face_eos(cell, d, g->gamma, g->de_switch, &um, &P[m + 1], &c);
+            if (m >= 0 && m < NP) u[m] = um;
+          }
+          ppm_pencil_cw84(q, P, u, g->gamma, g->cw84, aL, aR);
+        } else {
+          for (int f = 0; f < NF; ++f) oracle_ppm_pencil(q[f], aL[f], aR[f]);
         }
         for (int m = 2; m <= 10; ++m) {
           for (int f = 0; f < NF; ++f) {
@@ -423,69 +550,84 @@ static const int T2[3] = {2, 2, 1}; /* second transverse axis */
 
 static int floor_half(int v) { return v >= 0 ? v / 2 : -((-v + 1) / 2); }
 
+/* The value of field f of the ghost cell of sub-grid s across the face of
+ * axis a on `side`, at interior coordinate ga along a (-1, -2, ... on the low
+ * side; 8, 9, ... on the high side) and interior coordinates (c1, c2) along the
+ * face's transverse axes, from the current interiors. */
+static double ghost_value(const oracle_grid *g, const double *U, int s, int a, int side, int ga, int c1, int c2,
+                          int f) {
+  const int face = 2 * a + side;
+  const int b1 = T1[a], b2 = T2[a];
+  const int rel = g->neighbor_rel[s * 6 + face];
+  const int32_t *nb = g->neighbor + ((size_t)s * 6 + face) * 4;
+  int dst[3];
+  dst[a] = ga + NG;
+  dst[b1] = c1 + NG;
+  dst[b2] = c2 + NG;
+  if (nb[0] < 0) { /* outflow: nearest interior cell */
+    int src[3] = {dst[0], dst[1], dst[2]};
+    src[a] = side ? NG + NX - 1 : NG;
+    return U[at3(s, f, src)];
+  }
+  if (rel == 0) { /* same level: the neighbour's interior cell */
+    int src[3] = {dst[0], dst[1], dst[2]};
+    src[a] = (side ? ga - NX : ga + NX) + NG;
+    return U[at3(nb[0], f, src)];
+  }
+  if (rel < 0) {
+    /* coarser neighbour: value of the coarse cell that contains the centre of
+     * the fine ghost cell.  In coarse-cell units relative to the neighbour's
+     * interior origin, this sub-grid's origin is at 8 (neighbour on the low
+     * side) or -4 (high side) along a, and at 4*octant bit along each
+     * transverse axis. */
+    int oct = g->octant[s];
+    int src[3];
+    src[a] = (side ? -4 : 8) + floor_half(ga) + NG;
+    src[b1] = 4 * ((oct >> b1) & 1) + floor_half(c1) + NG;
+    src[b2] = 4 * ((oct >> b2) & 1) + floor_half(c2) + NG;
+    return U[at3(nb[0], f, src)];
+  }
+  /* finer neighbours: mean of the 2x2x2 fine cells covering the coarse ghost
+   * cell, summed in (k, j, i) order */
+  int q1 = c1 >> 2, q2 = c2 >> 2;
+  int fs = nb[q1 + 2 * q2];
+  int base[3];
+  base[a] = 2 * (side ? ga - NX : ga + 4);
+  base[b1] = 2 * (c1 - 4 * q1);
+  base[b2] = 2 * (c2 - 4 * q2);
+  double sum = 0.0;
+  for (int dk = 0; dk < 2; ++dk)
+    for (int dj = 0; dj < 2; ++dj)
+      for (int di = 0; di < 2; ++di) {
+        int src[3] = {base[0] + di + NG, base[1] + dj + NG, base[2] + dk + NG};
+        sum += U[at3(fs, f, src)];
+      }
+  return sum * 0.125;
+}
+
+double oracle_ghost_cell(const oracle_grid *g, const double *U, int s, int face, int ga, int c1, int c2, int f) {
+  return ghost_value(g, U, s, face / 2, face % 2, ga, c1, c2, f);
+}
+
 int oracle_fill_ghosts(const oracle_grid *g, double *U) {
-  for (int s = 0; s < g->n; ++s) {
+  for (int s = 0; s < g->n; ++s)
     for (int face = 0; face < 6; ++face) {
-      int a = face / 2, side = face % 2;
-      int b1 = T1[a], b2 = T2[a];
-      int rel = g->neighbor_rel[s * 6 + face];
-      const int32_t *nb = g->neighbor + ((size_t)s * 6 + face) * 4;
-      for (int f = 0; f < NF; ++f) {
+      const int a = face / 2, side = face % 2;
+      const int b1 = T1[a], b2 = T2[a];
+      for (int f = 0; f < NF; ++f)
         for (int layer = 0; layer < NG; ++layer) {
           /* interior coordinate of the ghost cell along a: -1,-2,-3 or 8,9,10 */
-          int ga = side ? NX + layer : -1 - layer;
-          for (int c2 = 0; c2 < NX; ++c2) {
+          const int ga = side ? NX + layer : -1 - layer;
+          for (int c2 = 0; c2 < NX; ++c2)
             for (int c1 = 0; c1 < NX; ++c1) {
               int dst[3];
               dst[a] = ga + NG;
               dst[b1] = c1 + NG;
               dst[b2] = c2 + NG;
-              double v;
-              if (nb[0] < 0) { /* outflow: nearest interior cell */
-                int src[3] = {dst[0], dst[1], dst[2]};
-                src[a] = side ? NG + NX - 1 : NG;
-                v = U[at3(s, f, src)];
-              } else if (rel == 0) { /* same level: the neighbour's interior cell */
-                int src[3] = {dst[0], dst[1], dst[2]};
-                src[a] = (side ? ga - NX : ga + NX) + NG;
-                v = U[at3(nb[0], f, src)];
-              } else if (rel < 0) {
-                /* coarser neighbour: value of the coarse cell that contains the
-                 * centre of the fine ghost cell.  In coarse-cell units relative
-                 * to the neighbour's interior origin, this sub-grid's origin is
-                 * at 8 (neighbour on the low side) or -4 (high side) along a,
-                 * and at 4*octant bit along each transverse axis. */
-                int oct = g->octant[s];
-                int src[3];
-                src[a] = (side ? -4 : 8) + floor_half(ga) + NG;
-                src[b1] = 4 * ((oct >> b1) & 1) + floor_half(c1) + NG;
-                src[b2] = 4 * ((oct >> b2) & 1) + floor_half(c2) + NG;
-                v = U[at3(nb[0], f, src)];
-              } else {
-                /* finer neighbours: mean of the 2x2x2 fine cells covering the
-                 * coarse ghost cell, summed in (k, j, i) order */
-                int q1 = c1 >> 2, q2 = c2 >> 2;
-                int fs = nb[q1 + 2 * q2];
-                int base[3];
-                base[a] = 2 * (side ? ga - NX : ga + 4);
-                base[b1] = 2 * (c1 - 4 * q1);
-                base[b2] = 2 * (c2 - 4 * q2);
-                double sum = 0.0;
-                for (int dk = 0; dk < 2; ++dk)
-                  for (int dj = 0; dj < 2; ++dj)
-                    for (int di = 0; di < 2; ++di) {
-                      int src[3] = {base[0] + di + NG, base[1] + dj + NG, base[2] + dk + NG};
-                      sum += U[at3(fs, f, src)];
-                    }
-                v = sum * 0.125;
-              }
-              U[at3(s, f, dst)] = v;
+              U[at3(s, f, dst)] = ghost_value(g, U, s, a, side, ga, c1, c2, f);
             }
-          }
         }
-      }
     }
-  }
   return ORACLE_OK;
 }
 

@@ -44,6 +44,9 @@ typedef struct {
   const int8_t *neighbor_rel;  /* [n][6] level(neighbour) - level(self) */
   const int8_t *octant;        /* [n] position in the parent: bit0 x, bit1 y, bit2 z */
   int32_t reflux;              /* 1: coarse-fine flux correction (the default), 0: none */
+  int32_t cw84;                /* PPM extensions of Colella & Woodward (1984): bit 0 shock flattening
+                                  (Section 4), bit 1 contact steepening of the density (eqs. 1.14-1.17);
+                                  0 (the default): neither */
 } oracle_grid;
 
 /* status codes */
@@ -93,6 +96,13 @@ long oracle_margin_cells(const oracle_grid *g, const int32_t *ids, int32_t n_ids
 
 /* Fill the six face ghost slabs of every sub-grid from the interiors. */
 int oracle_fill_ghosts(const oracle_grid *g, double *U);
+
+/* The ghost value of field f of sub-grid s across `face` (0..5 = -x,+x,-y,+y,
+ * -z,+z) at interior coordinate ga along the face's axis (-1, -2, ... low side;
+ * 8, 9, ... high side) and interior transverse coordinates (c1, c2), by the
+ * ghost-fill rules, from the interiors of U; any depth (the CW84 flattening
+ * reads the fourth layer). */
+double oracle_ghost_cell(const oracle_grid *g, const double *U, int s, int face, int ga, int c1, int c2, int f);
 
 /* Grid totals T_f = sum_s dx_s^3 sum_cells U_f, Neumaier-compensated, fixed order. */
 void oracle_totals(const oracle_grid *g, const double *U, double *totals);
