@@ -376,11 +376,17 @@ typedef enum {
                                         its update reads into L2: the prefetch distance */
   HYDRO_PARAM_REFLUX_SHAPE = 8,      /* launch shape of the mixed correction pass: 0 (default) 256 threads x 3
                                         items, 1: 128 x 3, 2: 256 x 2, 3: 512 x 3 */
-  HYDRO_PARAM_FUSED_RK3 = 9          /* RK3 steps: 0 (default) three stage launches (and, mixed, three
+  HYDRO_PARAM_FUSED_RK3 = 9,         /* RK3 steps: 0 (default) three stage launches (and, mixed, three
                                         correction passes); 1 one persistent launch per step; 2 one launch whose queue
                                         interleaves the stages of each sub-grid, which cannot complete while a
                                         CTA holds a later stage whose inputs are queued behind it: its bounded
                                         waits give up (HYDRO_ERR_TIMEOUT), which is all it is for */
+  HYDRO_PARAM_CW84 = 10              /* PPM extensions of Colella & Woodward (1984), both 0 by default: bit 0
+                                        shock flattening (their Section 4; reads the pressure one cell beyond
+                                        the three ghost layers, from the neighbours' interiors), bit 1 contact
+                                        steepening (their eqs. 1.14-1.17, detected on the density); both
+                                        coefficients apply to every conserved field.  Stages and RK3 steps
+                                        then use a stage kernel built with them (RK3 steps in three launches) */
 } hydro_param;
 
 /* Release the handle and its device scratch (waits for its work first). */

@@ -113,8 +113,8 @@ void oracle_ppm_pencil(const double *q, double *aL, double *aR) {
  * and u_{m-1} - u_{m+1} > 0, else ft_m = 0 (m = 1..12); then
  *   f_m = max(ft_m, ft_{m - sigma_m}),  sigma_m = sgn(p_{m+1} - p_{m-1}),
  * the larger of the cell's own and its upstream neighbour's. */
-static void flattening(const double *P, const double *u, double *f) {
-  double ft[NP];
+static void flattening_candidates(const double *P, const double *u, double *ft) {
+  for (int m = 0; m < NP; ++m) ft[m] = 0.0;
   for (int m = 1; m <= 12; ++m) {
     const double pm1 = P[m], pp1 = P[m + 2], pm2 = P[m - 1], pp2 = P[m + 3];
     const double dp = pp1 - pm1;
@@ -126,6 +126,11 @@ static void flattening(const double *P, const double *u, double *f) {
       ft[m] = v > 0.0 ? v : 0.0;
     }
   }
+}
+
+static void flattening(const double *P, const double *u, double *f) {
+  double ft[NP];
+  flattening_candidates(P, u, ft);
   for (int m = 2; m <= 11; ++m) {
     const double dp = P[m + 2] - P[m];
     const int up = dp > 0.0 ? m - 1 : (dp < 0.0 ? m + 1 : m);
@@ -475,6 +480,105 @@ static int dual_energy_near(const double *U, double eta, double tol) {
   return eta > 0.0 && fabs(ei - eta * E) <= tol * (fabs(E) + fabs(ek));
 }
 
+/* The CW84 tests of one pencil near their thresholds, counted only where
+ * taking the test the other way would change the coefficient: each detector
+ * fires when all of its tests pass, so a test near its threshold matters only
+ * where the detector's other tests pass and its value would be positive
+ * (flattening: shock and compression tests, candidate clamp(omega2 (ratio -
+ * omega1)) > 0, and the sign of its denominator p_{m+2} - p_{m-2}, across
+ * which the candidate jumps between 0 and 1; the sign of dp that picks the
+ * upstream neighbour, where the two
+ * neighbours' candidates differ; steepening: curvature, jump and contact
+ * tests, clamp(eta1 (etat - eta2)) > 0 for the unconditioned etat).  Each of
+ * these switches between outcomes that do not meet at the threshold.  A
+ * pressure enters with the relative uncertainty of its own evaluation: tol
+ * times (|E| + e_k) / |e_i| (the cancellation in e_i = E - e_k), 16 tol on the
+ * tau^gamma branch, and 1 where the dual-energy test itself is near its
+ * threshold (either branch may be taken). */
+static long cw84_margins(const oracle_grid *g, const double *U, int s, int d, int t1, int t2, double tol,
+                         unsigned char *ms) {
+  double P[NP + 2], K[NP + 2], u[NP], r[NP], cell[NF], c, ft[NP];
+  long found = 0;
+  for (int m = -1; m <= NP; ++m) {
+    if (m < 0 || m == NP) {
+      const int side = m < 0 ? 0 : 1;
+      for (int f = 0; f < NF; ++f)
+        cell[f] = ghost_value(g, U, s, d, side, side ? NX + NG : -1 - NG, t1 - NG, t2 - NG, f);
+    } else {
+      for (int f = 0; f < NF; ++f) cell[f] = U[pencil_at(s, f, d, t1, t2, m)];
+      r[m] = cell[F_RHO];
+    }
+    double um;
+    oracle_face_eos(cell, d, g->gamma, g->de_switch, &um, &P[m + 1], &c);
+    if (m >= 0 && m < NP) u[m] = um;
+    /* relative uncertainty of the pressure (K[m + 1] * |p|) */
+    const double E = cell[F_EGAS];
+    const double ek = 0.5 * (cell[F_SX] * cell[F_SX] + cell[F_SX + 1] * cell[F_SX + 1] +
+                             cell[F_SX + 2] * cell[F_SX + 2]) / cell[F_RHO];
+    const double ei = E - ek;
+    if (dual_energy_near(cell, g->de_switch, tol))
+      K[m + 1] = 1.0;
+    else if (g->de_switch > 0.0 && ei < g->de_switch * E)
+      K[m + 1] = 16.0 * tol;
+    else
+      K[m + 1] = ei != 0.0 ? tol * (fabs(E) + fabs(ek)) / fabs(ei) : 1.0;
+    if (K[m + 1] > 1.0) K[m + 1] = 1.0;
+  }
+  if (g->cw84 & 1) flattening_candidates(P, u, ft);
+  for (int m = 1; m <= 12; ++m) {
+    const double pm1 = P[m], pp1 = P[m + 2], pm2 = P[m - 1], pp2 = P[m + 3];
+    const double S = fabs(pp1) > fabs(pm1) ? fabs(pp1) : fabs(pm1);
+    const double pmin = pp1 < pm1 ? pp1 : pm1;
+    const double dp = pp1 - pm1;
+    const double up = K[m] * fabs(pm1) + K[m + 2] * fabs(pp1); /* uncertainty of dp */
+    int near = 0;
+    if (g->cw84 & 1) {
+      const double t = 10.0 * (dp / (pp2 - pm2) - 0.75);
+      {
+        const int shock = fabs(dp) > 0.33 * pmin, comp = u[m - 1] - u[m + 1] > 0.0;
+        const double S2 = fabs(pp2) > fabs(pm2) ? fabs(pp2) : fabs(pm2);
+        const double up2 = K[m - 1] * fabs(pm2) + K[m + 3] * fabs(pp2);
+        near = shock && comp && near_zero(pp2 - pm2, tol * S2 + up2);
+      }
+      if (t > 0.0) {
+        const double us = fabs(u[m - 1]) > fabs(u[m + 1]) ? fabs(u[m - 1]) : fabs(u[m + 1]);
+        const int shock = fabs(dp) > 0.33 * pmin, comp = u[m - 1] - u[m + 1] > 0.0;
+        const int near_shock = fabs(fabs(dp) - 0.33 * pmin) <= tol * S + up;
+        const int near_comp = near_zero(u[m - 1] - u[m + 1], tol * us);
+        near = near || (near_shock && comp) || (near_comp && shock);
+      }
+      if (m >= 2 && m <= 11 && ft[m - 1] != ft[m + 1]) near = near || near_zero(dp, tol * S + up);
+    }
+    if ((g->cw84 & 2) && m >= 2 && m <= 11) {
+      const double d2p = (r[m + 2] + r[m]) - 2.0 * r[m + 1];
+      const double d2m = (r[m] + r[m - 2]) - 2.0 * r[m - 1];
+      const double dr = r[m + 1] - r[m - 1];
+      if (dr != 0.0 && 20.0 * (-(d2p - d2m) / (6.0 * dr) - 0.05) > 0.0) {
+        const double R = max3(r[m - 1], r[m], r[m + 1]);
+        const double a1 = fabs(r[m + 1]), a0 = fabs(r[m - 1]);
+        const double amin = a1 < a0 ? a1 : a0;
+        const double rmin = r[m + 1] < r[m - 1] ? r[m + 1] : r[m - 1];
+        const int curv = d2p * d2m < 0.0, jump = fabs(dr) - 0.01 * amin > 0.0;
+        int contact = 0, near_contact = 0;
+        if (rmin > 0.0 && pmin > 0.0) {
+          const double lhs = g->gamma * 0.1 * fabs(dr) / rmin, rhs = fabs(dp) / pmin;
+          contact = lhs >= rhs;
+          near_contact = fabs(lhs - rhs) <= tol * (fabs(lhs) + fabs(rhs)) + (up / fabs(dp != 0.0 ? dp : 1.0) + K[m] + K[m + 2]) * rhs;
+        }
+        const int near_curv = near_zero(d2p, tol * R) || near_zero(d2m, tol * R);
+        const int near_jump = fabs(fabs(dr) - 0.01 * amin) <= tol * R;
+        near = near || (near_curv && jump && contact) || (near_jump && curv && contact) ||
+               (near_contact && curv && jump);
+      }
+    }
+    if (near) {
+      mark_pencil(ms, d, t1, t2, m, MARGIN_CW84);
+      ++found;
+    }
+  }
+  return found;
+}
+
 long oracle_margin_cells(const oracle_grid *g, const int32_t *ids, int32_t n_ids, const double *U, double tol,
                          unsigned char *mask) {
   int n = ids ? n_ids : g->n;
@@ -533,6 +637,7 @@ long oracle_margin_cells(const oracle_grid *g, const int32_t *ids, int32_t n_ids
               ++found;
             }
           }
+          if (g->cw84) found += cw84_margins(g, U, s, d, t1, t2, tol, ms);
         }
   }
   return found;

@@ -91,6 +91,7 @@ int oracle_stage(const oracle_grid *g, const int32_t *ids, int32_t n_ids, const 
 #define MARGIN_EXTREMUM 2    /* the parabola's extremum test */
 #define MARGIN_OVERSHOOT 4   /* the parabola's two overshoot tests */
 #define MARGIN_DUAL_ENERGY 8 /* the dual-energy test at a face side */
+#define MARGIN_CW84 16       /* a test of the CW84 flattening or steepening (when enabled) */
 long oracle_margin_cells(const oracle_grid *g, const int32_t *ids, int32_t n_ids, const double *U, double tol,
                          unsigned char *mask);
 

@@ -101,6 +101,8 @@ struct hydro_handle {
                                        // stage-interleaved queue (its waits give up: for tests of the bound)
   int fused_ok = 0;                    // the neighbour tables are mutual (the one-launch step relies on it)
   int occupancy_fused = 1;             // resident CTAs per SM of the one-launch kernel
+  int occupancy_cw = 1;                // resident CTAs per SM of the stage kernel with the CW84 extensions
+  int cw84 = 0;                        // CW84 PPM extensions: bit 0 flattening, bit 1 contact steepening
   int32_t* d_done = nullptr;           // [n] stages completed in the current launch
   int32_t* d_arrive = nullptr;         // mixed: [n_cf_list] arrivals at each coarse sub-grid
   int32_t* d_cf_slot = nullptr;        // mixed: [n] row in d_cf, -1 if none
@@ -197,7 +199,8 @@ int check_batch(hydro_handle* h, const hydro_batch* b) {
 }
 
 int stage_grid(hydro_handle* h, int n_items) {
-  int per_sm = h->ctas_per_sm > 0 ? h->ctas_per_sm : h->occupancy;
+  const int occ = h->cw84 ? h->occupancy_cw : h->occupancy;
+  int per_sm = h->ctas_per_sm > 0 ? std::min(h->ctas_per_sm, occ) : occ;
   int grid = h->grid_cap > 0 ? h->grid_cap : h->sm_count * per_sm;
   return n_items < grid ? (n_items > 0 ? n_items : 1) : grid;
 }
@@ -245,6 +248,7 @@ void fill_stage(hydro_handle* h, StageArgs& a, const int32_t* ids, int n_items, 
   a.err = h->d_err;
   a.max_speed = ms;
   a.pf_pass = h->pf_pass;
+  a.cw84 = h->cw84;
   a.ids = ids;
 }
 
@@ -537,6 +541,7 @@ int hydro_create(const hydro_grid_desc* d, hydro_handle** out) {
   ok = ok && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
   h->occupancy = h->precision == HYDRO_MIXED ? stage_blocks_per_sm_mixed() : stage_blocks_per_sm_fp64();
   h->occupancy_fused = h->precision == HYDRO_MIXED ? rk3_blocks_per_sm_mixed() : rk3_blocks_per_sm_fp64();
+  h->occupancy_cw = h->precision == HYDRO_MIXED ? cw_blocks_per_sm_mixed() : cw_blocks_per_sm_fp64();
   if (!ok) {
     free_all(h);
     delete h;
@@ -759,7 +764,7 @@ int enqueue_rk3_fused(hydro_handle* h, const int32_t* ids, int ni, double* U, do
 int enqueue_rk3_stages(hydro_handle* h, const int32_t* ids, int ni, double* U, double* s1, double* s2,
                        unsigned long long* ms, bool write_next, cudaStream_t cs) {
   int rc;
-  if (h->fused && h->fused_ok && ni == h->n) {
+  if (h->fused && h->fused_ok && !h->cw84 && ni == h->n) {
     rc = enqueue_rk3_fused(h, ids, ni, U, s1, s2, ms, write_next, cs);
     if (!rc && h->tau_resync)
       rc = enqueue_tau_resync(h, U, h->precision == HYDRO_MIXED && write_next ? h->d_shadow[0] : nullptr, cs);
@@ -1048,6 +1053,13 @@ int hydro_set_param(hydro_handle* h, int32_t key, int32_t value) {
   if (key == HYDRO_PARAM_FUSED_RK3) {
     if (value < 0 || value > 2) return fail(h, HYDRO_ERR_INVALID, "one-launch RK3 mode must be 0, 1 or 2");
     h->fused = value;
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+    return HYDRO_OK;
+  }
+  if (key == HYDRO_PARAM_CW84) {
+    if (value < 0 || value > 3) return fail(h, HYDRO_ERR_INVALID, "CW84 flags must be in 0..3");
+    h->cw84 = value;
     for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
     h->graphs.clear();
     return HYDRO_OK;

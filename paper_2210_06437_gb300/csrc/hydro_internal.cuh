@@ -103,6 +103,7 @@ struct StageArgs {
   long long wait_limit;
   int32_t call_id;
   int32_t flag_base;     // FP64: cf_flag values are flag_base + d + 1 (stage k of a one-launch RK3 step: 3k)
+  int32_t cw84;          // CW84 PPM extensions: bit 0 shock flattening, bit 1 contact steepening (0: neither)
   int32_t pf_pass;       // the direction pass (0 x, 1 y, 2 z) that prefetches the update's rows into L2
 };
 
@@ -201,6 +202,8 @@ int stage_blocks_per_sm_fp64();
 int stage_blocks_per_sm_mixed();
 int rk3_blocks_per_sm_fp64();
 int rk3_blocks_per_sm_mixed();
+int cw_blocks_per_sm_fp64();
+int cw_blocks_per_sm_mixed();
 cudaError_t launch_ghost_fill(const GhostArgs& a, int threads, cudaStream_t st);
 // scratch doubles needed by launch_totals for n sub-grids
 size_t totals_scratch_doubles(int n);

@@ -15,16 +15,18 @@ pencil).  Two kinds are told apart:
     outcomes that meet at the threshold, so taking them the other way moves a
     face value by about the rounding that put the test near its threshold; those
     cells stay in the gate and are only counted;
-  * the dual-energy test switches between two pressures that need not agree;
-    those cells (and their stencil) are left out of the gate, counted, and their
-    error is reported separately.
+  * the dual-energy test switches between two pressures that need not agree,
+    and the CW84 flattening and steepening tests (when enabled) switch a
+    coefficient on or off; those cells (and their stencil) are left out of the
+    gate, counted, and their error is reported separately.
 No solver arithmetic lives here.
 """
 import numpy as np
 
 FLOOR = 1e-8
 EPS = {"fp64": 2.0 ** -53, "mixed": 2.0 ** -24}
-M_SLOPE, M_EXTREMUM, M_OVERSHOOT, M_DUAL = 1, 2, 4, 8
+M_SLOPE, M_EXTREMUM, M_OVERSHOOT, M_DUAL, M_CW84 = 1, 2, 4, 8, 16
+M_SWITCH = M_DUAL | M_CW84   # tests whose two outcomes need not meet at the threshold
 SL = (slice(None), slice(None), slice(3, 11), slice(3, 11), slice(3, 11))
 
 
@@ -61,7 +63,7 @@ def r12(x, r, margin=None):
     m = e.shape[0]
     if margin is None:
         margin = np.zeros((m, 8, 8, 8), np.uint8)
-    dual = (margin & M_DUAL) != 0
+    dual = (margin & M_SWITCH) != 0
     ppm = ((margin & (M_SLOPE | M_EXTREMUM | M_OVERSHOOT)) != 0) & ~dual
     gated = np.where(dual[:, None], 0.0, e)
     out = {
