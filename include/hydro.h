@@ -134,9 +134,11 @@ int hydro_create(const hydro_grid_desc *desc, hydro_handle **out);
  *          listed sub-grids and their faces of max(a+, -a-) (the CFL signal
  *          speed of the INPUT state) and of that speed divided by dx_s;
  *   stream cudaStream_t (NULL = legacy default stream).
- * A mixed-precision handle first writes the FP32 shadow of U_in (hydro_shadow,
- * all sub-grids, into the handle's own buffer); hydro_step_shadowed skips that
- * pass when the caller already holds the shadow.
+ * A mixed-precision handle first writes the FP32 shadow of U_in into its own
+ * buffer: of the listed sub-grids and the face neighbours their halos read
+ * when the batch lists fewer than an eighth of the sub-grids, else of all of
+ * them (hydro_shadow); hydro_step_shadowed skips that pass when the caller
+ * already holds the shadow.
  * Coarse-fine flux correction (Section V-B.1: compute_fluxes corrects the
  * fluxes on coarse-fine boundaries; HYDRO_PARAM_REFLUX, on by default): where
  * a listed sub-grid meets four finer neighbours, each coarse boundary face

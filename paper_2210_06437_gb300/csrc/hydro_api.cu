@@ -582,8 +582,17 @@ int hydro_step(hydro_handle* h, const hydro_batch* batch, const double* U_in, co
   h->last_stream = st;
   const float* S = nullptr;
   if (h->precision == HYDRO_MIXED && batch->n_items > 0) {
-    rc = enqueue_shadow(h, U_in, h->d_shadow[0], st);
-    if (rc) return rc;
+    // the shadows the stage reads: of the batch and its face neighbours when
+    // the batch is small against the grid, else of the whole grid in one pass
+    if ((int64_t)batch->n_items * 8 < (int64_t)h->n) {
+      cudaError_t e = launch_shadow_ids(U_in, h->d_shadow[0], batch->subgrid_ids, batch->n_items, h->n, h->d_nb,
+                                        h->d_rel, st);
+      if (e != cudaSuccess) return cuda_fail(h, e, "shadow kernel launch");
+      h->launches += 1;
+    } else {
+      rc = enqueue_shadow(h, U_in, h->d_shadow[0], st);
+      if (rc) return rc;
+    }
     S = h->d_shadow[0];
   }
   return enqueue_stage(h, batch->subgrid_ids, batch->n_items, U_in, S, beta == 1.0 ? nullptr : U0, beta, dt,

@@ -148,6 +148,61 @@ __global__ void __launch_bounds__(256) shadow_kernel(const double* __restrict__ 
   }
 }
 
+// The shadows a stage over a batch reads: one CTA per batch item writes the
+// shadow of the item's sub-grid and of every face neighbour its halo gather
+// reads (the neighbour of a same-level or coarser face, the four of a finer
+// one), each value as shadow_kernel writes it; a sub-grid named by several
+// items is written several times with the same values.  Ids outside [0, n)
+// are skipped (the stage reports them); a flux-only flag is ignored.
+__global__ void __launch_bounds__(256) shadow_ids_kernel(const double* __restrict__ U, float* __restrict__ S,
+                                                         const int32_t* __restrict__ ids, int n,
+                                                         const int32_t* __restrict__ nb,
+                                                         const int8_t* __restrict__ rel) {
+  __shared__ int list[25];
+  __shared__ int count;
+  int s = ids[blockIdx.x];
+  if (s >= 0) s &= ~ITEM_FLUX_ONLY;
+  if (s < 0 || s >= n) return;  // uniform over the block
+  if (threadIdx.x == 0) {
+    int c = 0;
+    list[c++] = s;
+    for (int face = 0; face < 6; ++face) {
+      const int r = rel[s * 6 + face];
+      for (int q = 0; q < (r == 1 ? 4 : 1); ++q) {
+        const int x = nb[((size_t)s * 6 + face) * 4 + q];
+        if (x >= 0 && x < n) list[c++] = x;
+      }
+    }
+    count = c;
+  }
+  __syncthreads();
+  for (int e = 0; e < count; ++e) {
+    const int x = list[e];
+    for (int t = threadIdx.x; t < NF * SHADOW_FIELD; t += blockDim.x) {
+      const size_t g = (size_t)x * NF * SHADOW_FIELD + t;
+      const size_t sf = g / SHADOW_FIELD;
+      const int c = t % SHADOW_FIELD;
+      const double* u = U + sf * NP3;
+      if (c < SHADOW_COARSE) {
+        const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
+        S[g] = shadow_round(u[(size_t)(k + NG) * NP2 + (j + NG) * NP + (i + NG)]);
+      } else {
+        const int cc = c - SHADOW_COARSE;
+        const int I = cc & 3, J = (cc >> 2) & 3, K = cc >> 4;
+        const double* b = u + (size_t)(2 * K + NG) * NP2 + (2 * J + NG) * NP + (2 * I + NG);
+        float h[2];
+#pragma unroll
+        for (int dk = 0; dk < 2; ++dk) {
+          const double* bk = b + dk * NP2;
+          h[dk] = __fadd_rn(__fadd_rn(shadow_round(bk[0]), shadow_round(bk[1])),
+                            __fadd_rn(shadow_round(bk[NP]), shadow_round(bk[NP + 1])));
+        }
+        S[g] = __fmul_rn(__fadd_rn(h[0], h[1]), 0.125f);
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Dual-energy reset of the entropy tracer (the paper is silent on the EOS;
 // this completes the dual-energy switch of the face EOS): in every interior cell where
@@ -214,6 +269,13 @@ cudaError_t launch_tau_resync(double* U, float* S, int n, double gamma, double e
     tau_resync_kernel<true><<<n, 256, 0, st>>>(U, S, 1.0 / gamma, eta);
   else
     tau_resync_kernel<false><<<n, 256, 0, st>>>(U, nullptr, 1.0 / gamma, eta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shadow_ids(const double* U, float* S, const int32_t* ids, int n_items, int n, const int32_t* nb,
+                              const int8_t* rel, cudaStream_t st) {
+  if (n_items < 1) return cudaSuccess;
+  shadow_ids_kernel<<<n_items, 256, 0, st>>>(U, S, ids, n, nb, rel);
   return cudaGetLastError();
 }
 

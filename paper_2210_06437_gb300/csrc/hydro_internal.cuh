@@ -183,6 +183,10 @@ constexpr int SHADOW_FIELD = CELLS + CELLS / 8;  // 576 floats per field
 
 // launchers (defined in the .cu files)
 cudaError_t launch_shadow(const double* U, float* S, int n, cudaStream_t st);
+// The shadows of the batch's sub-grids and of the face neighbours their halos
+// read (one CTA per item; for batches small against the grid).
+cudaError_t launch_shadow_ids(const double* U, float* S, const int32_t* ids, int n_items, int n, const int32_t* nb,
+                              const int8_t* rel, cudaStream_t st);
 // Dual-energy tracer reset of every sub-grid of U (and the tau field of its
 // shadow S when mixed and S is not null); nothing when eta <= 0.
 cudaError_t launch_tau_resync(double* U, float* S, int n, double gamma, double eta, bool mixed, cudaStream_t st);

@@ -681,14 +681,15 @@ def test_amr_step_conserves_and_matches_oracle(hydro, oracle_mod, prec):
         g.close()
 
 
+@pytest.mark.parametrize("cfg", [4, 5])
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
-def test_full_size_rk3_in_bench_launch(hydro, oracle_mod, prec):
-    """The benchmark's path on its full workload: one hydro_rk3_run_cfl step
+def test_full_size_rk3_in_bench_launch(hydro, oracle_mod, prec, cfg):
+    """The benchmark's path on the full workloads (configs 4 and 5): one hydro_rk3_run_cfl step
     (graph of the three stage launches with their flux corrections, increment
-    form in mixed precision) on all 65536 sub-grids, against the oracle's
+    form in mixed precision) on all sub-grids (32768 or 65536), against the oracle's
     SSP-RK3 step on the cone of 48 sampled sub-grids and the three rings of
     face neighbours that the three stages read."""
-    w = W.config(5)
+    w = W.config(cfg)
     U = _filled(oracle_mod, w)
     rng = np.random.default_rng(55)
     sample = np.sort(rng.choice(w.grid.n, 48, replace=False))
@@ -710,7 +711,7 @@ def test_full_size_rk3_in_bench_launch(hydro, oracle_mod, prec):
     g.sync()
     assert abs(dts.item() - dt) <= 1e-15 * dt
     got = Ud.index_select(0, torch.as_tensor(sample, device="cuda", dtype=torch.long)).cpu().numpy()
-    check(got, ref, prec, "rk3", 5)
+    check(got, ref, prec, "rk3", cfg)
 
 
 # ---------------------------------------------------------------------------
@@ -898,3 +899,29 @@ def test_flux_correction_wait_timeout_is_reported(hydro, oracle_mod):
     g.sync()
     ref, _, st = oracle_mod.Oracle(w.grid).stage(U, dt)
     assert np.array_equal(_host(out)[IN], ref[IN])
+
+
+def test_mixed_step_on_a_small_batch_shadows_only_what_it_reads(hydro, oracle_mod):
+    """A mixed hydro_step over a batch of fewer than an eighth of the sub-grids
+    writes the shadows of the batch and its face neighbours only (one CTA per
+    item); its results equal those of hydro_step_shadowed from the full shadow
+    bit for bit, on a subset that crosses coarse-fine faces."""
+    w = W.config(3)
+    U = _filled(oracle_mod, w)
+    Ud = _dev(U)
+    rng = np.random.default_rng(12)
+    coarse = np.flatnonzero((w.grid.neighbor_rel == 1).any(axis=1))[:20]
+    sub = np.unique(np.concatenate([coarse, rng.choice(w.grid.n, 200, replace=False)])).astype(np.int32)
+    assert len(sub) * 8 < w.grid.n
+    g = hydro.HydroGrid(w.grid, precision="mixed")
+    ids = torch.as_tensor(sub, device="cuda")
+    ms_a = torch.zeros(2, dtype=torch.float64, device="cuda")
+    a, _ = g.step(Ud, 1e-3, U_out=torch.full_like(Ud, 7.0), ids=ids, max_speed=ms_a)
+    S = g.shadow(Ud)
+    ms_b = torch.zeros(2, dtype=torch.float64, device="cuda")
+    b, _ = g.step_shadowed(Ud, S, 1e-3, U_out=torch.full_like(Ud, 7.0), ids=ids, max_speed=ms_b)
+    g.sync()
+    assert np.array_equal(_host(a)[sub][IN], _host(b)[sub][IN])
+    assert np.array_equal(ms_a.cpu().numpy(), ms_b.cpu().numpy())
+    ref, _, _ = oracle_mod.Oracle(w.grid).stage(U, 1e-3, ids=sub)
+    check(_host(a)[sub], ref[sub], "mixed")
