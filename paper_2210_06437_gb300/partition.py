@@ -159,13 +159,14 @@ def exchange(p: Partition, U_local, dist) -> None:
 # ---------------------------------------------------------------------------
 
 SLAB = 3          # layers of a proxy that a same-level or finer owned neighbour reads across a face
+SLAB_CW84 = 4     # with the CW84 flattening, whose pressures reach one layer further
 WHOLE = -1        # a finer proxy: the whole interior (the coarse owner reads six fine layers for its
                   # 2x2x2 halo means, and the proxy's boundary flux is recomputed from it)
 
 
 def slab_entries(grid: Grid, gids: np.ndarray, owner: np.ndarray, reader: int) -> list:
     """(gid, face) pieces of the proxies gids that rank `reader` reads: face
-    slabs of SLAB layers where a reader's sub-grid is a same-level or finer
+    slabs (of `depth` layers, see _region) where a reader's sub-grid is a same-level or finer
     neighbour across that face, the whole interior (face WHOLE) where a
     reader's sub-grid is coarser.  Both sides of an exchange derive the same
     list from the global grid."""
@@ -185,77 +186,81 @@ def slab_entries(grid: Grid, gids: np.ndarray, owner: np.ndarray, reader: int) -
     return out
 
 
-def _region(face: int):
-    """Index of the padded interior cells of a piece (face slab or WHOLE) within [f, k, j, i]."""
+def _region(face: int, depth: int = SLAB):
+    """Index of the padded interior cells of a piece (a face slab of `depth`
+    layers, or WHOLE) within [f, k, j, i].  A same-level reader's halo reads
+    three layers (four with the CW84 flattening); a finer reader's, by
+    injection, at most two coarse layers."""
     I = slice(NG, NG + NX)
     if face == WHOLE:
         return (slice(None), I, I, I)
     a, side = face // 2, face % 2
-    cut = slice(NG, NG + SLAB) if side == 0 else slice(NG + NX - SLAB, NG + NX)
+    cut = slice(NG, NG + depth) if side == 0 else slice(NG + NX - depth, NG + NX)
     sl = [slice(None), I, I, I]
     sl[3 - a] = cut
     return tuple(sl)
 
 
-def pack_pieces(U, entries, local_index) -> "object":
+def pack_pieces(U, entries, local_index, depth: int = SLAB) -> "object":
     """The cells of `entries` from the local state U (torch, [m,11,14,14,14]) as one flat tensor."""
     import torch
     if not entries:
         return torch.empty(0, dtype=U.dtype, device=U.device)
     li = local_index(np.array([g for g, _ in entries]))
-    return torch.cat([U[int(l)][_region(f)].reshape(-1) for l, (_, f) in zip(li, entries)])
+    return torch.cat([U[int(l)][_region(f, depth)].reshape(-1) for l, (_, f) in zip(li, entries)])
 
 
-def unpack_pieces(U, entries, local_index, buf) -> None:
+def unpack_pieces(U, entries, local_index, buf, depth: int = SLAB) -> None:
     """Write the flat buffer of pack_pieces into the proxy slots of U."""
     if not entries:
         return
     li = local_index(np.array([g for g, _ in entries]))
     o = 0
     for l, (_, f) in zip(li, entries):
-        view = U[int(l)][_region(f)]
+        view = U[int(l)][_region(f, depth)]
         n = view.numel()
         view.copy_(buf[o:o + n].view(view.shape))
         o += n
 
 
-def exchange_slabs(p: Partition, U_local, dist) -> int:
-    """exchange() with only the cells each receiver reads (face slabs, whole
-    interiors of finer proxies); returns the bytes this rank sent."""
+def exchange_slabs(p: Partition, U_local, dist, depth: int = SLAB) -> int:
+    """exchange() with only the cells each receiver reads (face slabs of
+    `depth` layers, whole interiors of finer proxies); returns the bytes this
+    rank sent."""
     import torch
     is_np = isinstance(U_local, np.ndarray)
     T = torch.from_numpy(U_local) if is_np else U_local
     reqs, keep, sent = [], [], 0
     for q, gids in sorted(p.send.items()):
-        buf = pack_pieces(T, slab_entries(p.glob, gids, p.owner, q), p.local_index)
+        buf = pack_pieces(T, slab_entries(p.glob, gids, p.owner, q), p.local_index, depth)
         keep.append(buf)
         sent += buf.numel() * buf.element_size()
         reqs.append(dist.isend(buf, dst=q))
     recvs = []
     for q, gids in sorted(p.recv.items()):
         entries = slab_entries(p.glob, gids, p.owner, p.rank)
-        n = sum(T[0][_region(f)].numel() for _, f in entries)
+        n = sum(T[0][_region(f, depth)].numel() for _, f in entries)
         buf = torch.empty(n, dtype=T.dtype, device=T.device)
         recvs.append((entries, buf))
         reqs.append(dist.irecv(buf, src=q))
     for r in reqs:
         r.wait()
     for entries, buf in recvs:
-        unpack_pieces(T, entries, p.local_index, buf)
+        unpack_pieces(T, entries, p.local_index, buf, depth)
     return sent
 
 
-def exchange_direct(parts: List[Partition], states: list) -> int:
+def exchange_direct(parts: List[Partition], states: list, depth: int = SLAB) -> int:
     """The slab exchange between partitions held in one process (device
     copies): every rank's proxies receive, from their owners' local states,
-    the cells it reads.  Returns the bytes moved."""
+    the cells it reads (face slabs of `depth` layers).  Returns the bytes moved."""
     moved = 0
     for r, p in enumerate(parts):
         for q, gids in sorted(p.recv.items()):
             entries = slab_entries(p.glob, gids, p.owner, r)
-            buf = pack_pieces(states[q], entries, parts[q].local_index)
+            buf = pack_pieces(states[q], entries, parts[q].local_index, depth)
             moved += buf.numel() * buf.element_size()
-            unpack_pieces(states[r], entries, p.local_index, buf)
+            unpack_pieces(states[r], entries, p.local_index, buf, depth)
     return moved
 
 

@@ -13,6 +13,7 @@ import pytest
 
 from paper_2210_06437_gb300 import partition as P
 from paper_2210_06437_gb300 import workloads as W
+from tests import helpers as H
 
 torch = pytest.importorskip("torch")
 import torch.distributed as dist  # noqa: E402
@@ -52,29 +53,39 @@ def _free_port():
     return port
 
 
-def _worker(rank, world, port, cfg, steps, out, slabs=False):
-    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), OMP_NUM_THREADS="2")
+def _workload(cfg):
+    """(grid, initial padded state) of a configuration, or of the small AMR blob."""
+    if cfg == "blob":
+        return H.amr_blob_state()
+    w = W.config(cfg)
+    return w.grid, w.state()
+
+
+def _worker(rank, world, port, cfg, steps, out, slabs=False, cw84=0):
+    nth = max(1, (os.cpu_count() or 2) // world)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), OMP_NUM_THREADS=str(nth))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         import oracle
-        w = W.config(cfg)
-        p = P.build(w.grid, rank, world)
-        o = oracle.Oracle(p.local)
+        grid, U0 = _workload(cfg)
+        p = P.build(grid, rank, world)
+        o = oracle.Oracle(p.local, cw84=cw84)
+        depth = P.SLAB_CW84 if cw84 & 1 else P.SLAB
         own = np.arange(p.n_owned, dtype=np.int32)
-        UL = P.scatter_global(p, w.state())
+        UL = P.scatter_global(p, U0.copy())
         if slabs:   # proxies start stale: only the exchanged cells may be read
             UL[p.n_owned:][INTERIOR] = np.nan
 
         def stage(Uin, dt, U0=None, beta=1.0):
             if slabs:
-                P.exchange_slabs(p, Uin, dist)
+                P.exchange_slabs(p, Uin, dist, depth)
             else:
                 P.exchange(p, Uin, dist)
             o.fill_ghosts(Uin)
             Uout = Uin.copy()
             # every sub-grid of the global grid is advanced by this stage (the
             # proxies by their owners), which the flux correction needs to know
-            _, ms, st = o.stage(Uin, dt, U0=U0, beta=beta, Uout=Uout, ids=own, nthreads=2, batch_all=True)
+            _, ms, st = o.stage(Uin, dt, U0=U0, beta=beta, Uout=Uout, ids=own, nthreads=nth, batch_all=True)
             assert st == 0
             return Uout, P.allreduce_max(ms, dist)
 
@@ -88,13 +99,12 @@ def _worker(rank, world, port, cfg, steps, out, slabs=False):
             UL, _ = stage(U2, dt, U0=UL, beta=2.0 / 3.0)
         got = P.gather_owned(p, UL, dist)
         if rank == 0:
-            g = w.grid
-            og = oracle.Oracle(g)
-            U = og.fill_ghosts(w.state())
-            _, ms, _ = og.stage(U, 0.0, nthreads=2)
+            og = oracle.Oracle(grid, cw84=cw84)
+            U = og.fill_ghosts(U0.copy())
+            _, ms, _ = og.stage(U, 0.0, nthreads=nth)
             for dt in dts:
                 assert dt == 0.4 / ms[1]
-                U, ms, st = og.rk3_step(U, dt, nthreads=2)
+                U, ms, st = og.rk3_step(U, dt, nthreads=nth)
             out.put(("ok", bool(np.array_equal(got, U[INTERIOR])), float(np.abs(got - U[INTERIOR]).max())))
         dist.barrier()
     except Exception as e:  # report to the parent instead of hanging it
@@ -104,16 +114,20 @@ def _worker(rank, world, port, cfg, steps, out, slabs=False):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("cfg,world,steps,slabs", [(3, 2, 2, False), (1, 2, 3, False), (3, 2, 2, True),
-                                                    (3, 3, 1, True)])
-def test_sharded_step_matches_single_domain(oracle_mod, cfg, world, steps, slabs):
+# the small AMR blob (71 sub-grids, coarse-fine faces between ranks) keeps the
+# CPU suite short; the 4096-leaf octree is sharded on the GPU (test_sharded_gpu)
+@pytest.mark.parametrize("cfg,world,steps,slabs,cw84", [("blob", 2, 2, False, 0), (1, 2, 3, False, 0),
+                                                         ("blob", 2, 2, True, 0), ("blob", 3, 2, True, 0),
+                                                         ("blob", 2, 2, True, 3)])
+def test_sharded_step_matches_single_domain(oracle_mod, cfg, world, steps, slabs, cw84):
     """slabs: the exchange moves only the cells each receiver reads (face
     slabs; whole interiors of finer proxies); the proxies' other cells then
-    hold stale values that no owned sub-grid may read."""
+    hold stale values that no owned sub-grid may read.  cw84: the CW84
+    extensions, whose flattening reads four layers (4-layer slabs)."""
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, world, port, cfg, steps, q, slabs)) for r in range(world)]
+    procs = [ctx.Process(target=_worker, args=(r, world, port, cfg, steps, q, slabs, cw84)) for r in range(world)]
     for pr in procs:
         pr.start()
     msg = q.get(timeout=600)

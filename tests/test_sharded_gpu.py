@@ -8,7 +8,8 @@ listed as flux-only items, so the coarse-fine correction sees the fluxes of
 remote fine neighbours; the maximum signal speed is the maximum over the two.
 The gathered owned interiors after two RK3 steps equal the single-domain run
 with the same library bit for bit, in both precisions (and the FP64 one is the
-oracle's to 1e-12 per cell)."""
+oracle's to 1e-12 per cell), also with the CW84 extensions, whose flattening
+reads a fourth layer (4-layer slabs)."""
 import numpy as np
 import pytest
 
@@ -45,12 +46,15 @@ def _rk3(stage, U, ms_first):
     return U, dts
 
 
+@pytest.mark.parametrize("cw84", [0, 3])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_sharded_step_on_one_gpu(hydro, oracle_mod, prec):
+def test_sharded_step_on_one_gpu(hydro, oracle_mod, prec, cw84):
     w = W.config(3)
     grid = w.grid
     # single domain
     g = hydro.HydroGrid(grid, precision=prec)
+    g.set_param(hydro.PARAM_CW84, cw84)
+    depth = P.SLAB_CW84 if cw84 & 1 else P.SLAB   # flattening reads one layer further
     ids_all = torch.as_tensor(w.batches.ids, device="cuda")
 
     def stage1(Uin, dt, U0, beta):
@@ -67,6 +71,8 @@ def test_sharded_step_on_one_gpu(hydro, oracle_mod, prec):
     # two partitions
     parts = [P.build(grid, r, 2) for r in range(2)]
     handles = [hydro.HydroGrid(p.local, precision=prec) for p in parts]
+    for h in handles:
+        h.set_param(hydro.PARAM_CW84, cw84)
     G0 = w.state()
     states = []
     for p in parts:
@@ -80,7 +86,7 @@ def test_sharded_step_on_one_gpu(hydro, oracle_mod, prec):
     moved = []
 
     def stage2(Uins, dt, U0s, beta):
-        moved.append(P.exchange_direct(parts, Uins))
+        moved.append(P.exchange_direct(parts, Uins, depth))
         outs, mss = [], []
         for r, p in enumerate(parts):
             out = torch.full_like(Uins[r], float("nan"))
@@ -100,9 +106,9 @@ def test_sharded_step_on_one_gpu(hydro, oracle_mod, prec):
     assert np.array_equal(got[IN], ref[IN])
     # the slabs moved fewer bytes than whole interiors would
     whole = sum(len(p.proxies) for p in parts) * 11 * 512 * 8
-    assert max(moved) < 0.7 * whole
+    assert max(moved) < (0.7 if depth == P.SLAB else 0.8) * whole
     if prec == "fp64":   # and the FP64 run is the oracle's, to the pow of the dual-energy switch
-        o = oracle_mod.Oracle(grid)
+        o = oracle_mod.Oracle(grid, cw84=cw84)
         Uo = w.state()
         o.fill_ghosts(Uo)
         for dt in dts_ref:
