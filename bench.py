@@ -414,6 +414,13 @@ def main():
         U.copy_(torch.from_numpy(U_host))
         g.fill_ghosts(U)
         tuned = TU.tune(g, U, s1, s2, ids=ids, batch_offsets=offs)   # launch shapes, outside the timed region
+        # the tuner's best RK3 step time of each form (three launches, one launch), from its table
+        forms = {}
+        entry = TU.load_cache().get(TU.cache_key(torch.cuda.get_device_name(), prec, w.grid.n), {})
+        for c, t in entry.get("table", []):
+            if t is not None and "fused_rk3" in c:
+                k = "one_launch_ms" if c["fused_rk3"] else "three_launches_ms"
+                forms[k] = min(forms.get(k, t), t)
         ms = torch.zeros(2, dtype=torch.float64, device=dev)
         g.step(U, 0.0, U_out=s1, ids=ids, batch_offsets=offs, max_speed=ms)   # dry stage: first CFL speed
         tots = torch.empty((max(args.steps, args.warmup), 11), dtype=torch.float64, device=dev)
@@ -477,7 +484,7 @@ def main():
         t_resync = timed(lambda: g.tau_resync(U)) if prec == "mixed" else 0.0
         g.sync()
         g.close()
-        return dict(t_step=t_step, clocks=clocks, launches=launches, t_stage=t_stage, t_single=t_single,
+        return dict(forms=forms, t_step=t_step, clocks=clocks, launches=launches, t_stage=t_stage, t_single=t_single,
                     t_ghost=t_ghost, t_tot=t_tot, t_shadow=t_shadow, t_resync=t_resync, totals=tot.cpu().numpy(),
                     tuned=tuned)
 
@@ -614,7 +621,8 @@ def main():
                                "by each step's last stage)",
                        "l2": "inputs larger than L2 (%.1f GB state)" % (U.numel() * 8 / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "tuned": r["tuned"]},
+                       "tuned": r["tuned"],
+                       "rk3_forms_tuner_ms": r["forms"]},
             "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": r["launches"], "clocks": r["clocks"]}
     if "fp64" in results:
@@ -622,6 +630,7 @@ def main():
         fl = FLOPS_PER_CELL_STAGE * cells / f["t_stage"] / 1e12  # average of the RK3 graph's stage launches
         inst = FP64_INST_PER_CELL_STAGE * cells / f["t_stage"]
         line["fp64"] = {"value": aggregate_rate(cells, 3, world, f["t_step"]), "ms_per_step": f["t_step"] * 1e3,
+                        "rk3_forms_tuner_ms": f["forms"],
                         "roofline": {"bound": "alu", "achieved": fl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                                      "frac": fl / FP64_PEAK_TFLOPS, "traffic": None,
                                      "inst_frac": inst / FP64_PEAK_INST,
