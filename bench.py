@@ -56,7 +56,7 @@ FP64_PEAK_INST = 152 * 2 * 2.070e9
 FP64_PEAK_TFLOPS = 2 * FP64_PEAK_INST / 1e12
 # DRAM bytes (read + write) per cell-update of the mixed stage kernel from one ncu capture
 # (average of the three RK3 stage launches), valid only for the kernel source it was taken on.
-STAGE_TRAFFIC = {"sha256_prefix": "99c6145e37fe0412", "bytes_per_cell": 303.5,
+STAGE_TRAFFIC = {"sha256_prefix": "33a81225b2eb6758", "bytes_per_cell": 303.6,
                  "source": "ncu capture of the three RK3 stage launches on the 4097-leaf reduced binary octree "
                            "(average), scaled by cells"}
 
