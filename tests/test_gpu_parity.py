@@ -336,7 +336,8 @@ def test_host_argument_errors(hydro):
     for key, value in ((hydro.PARAM_TAU_RESYNC, 2), (hydro.PARAM_REFLUX, -1), (hydro.PARAM_STAGE_CTAS_PER_SM, 9),
                        (hydro.PARAM_GHOST_THREADS, 100), (hydro.PARAM_WAIT_LIMIT, 0),
                        (hydro.PARAM_QUEUE_ORDER, 2), (hydro.PARAM_STAGE_GRID, -1), (hydro.PARAM_PREFETCH_PASS, 3),
-                       (hydro.PARAM_REFLUX_SHAPE, 4), (99, 0)):
+                       (hydro.PARAM_REFLUX_SHAPE, 4), (hydro.PARAM_FUSED_RK3, 3), (hydro.PARAM_FUSED_RK3, -1),
+                       (hydro.PARAM_CW84, 4), (hydro.PARAM_CW84, -1), (99, 0)):
         with pytest.raises(hydro.HydroError):
             g.set_param(key, value)
     g.set_param(hydro.PARAM_TAU_RESYNC, 1)
