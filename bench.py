@@ -87,6 +87,8 @@ def parse():
                    help="profiling case: one RK3 step (mixed: the three stage launches of the increment form with "
                         "their correction passes) or one FP64 stage (beta = 1) on --config with default launch "
                         "parameters, then exit; prints no benchmark line")
+    p.add_argument("--cw84", type=int, default=0, help="profiling case: CW84 extensions (HYDRO_PARAM_CW84 bits)")
+    p.add_argument("--fused", type=int, default=0, help="profiling case: the one-launch RK3 step (1)")
     p.add_argument("--sweep", action="store_true",
                    help="per-configuration table (one JSON line per configuration and precision, errors against "
                         "the oracle, oracle timings); not the benchmark line")
@@ -343,17 +345,20 @@ def run_stage_only(args):
     U = torch.from_numpy(w.state()).cuda()
     ids = torch.as_tensor(w.batches.ids, device="cuda")
     g = HY.HydroGrid(w.grid, precision=args.stage_only)
+    g.set_param(HY.PARAM_CW84, args.cw84)
+    g.set_param(HY.PARAM_FUSED_RK3, args.fused)
     ms = torch.zeros(2, dtype=torch.float64, device="cuda")
     s1 = torch.empty_like(U)
     g.step(U, 0.0, U_out=s1, ids=ids, batch_offsets=w.batches.offsets, max_speed=ms)
     dt = 0.4 / float(ms[1])
-    if args.stage_only == "mixed":
+    if args.stage_only == "mixed" or args.fused:
         g.rk3_step(U, dt, s1, torch.empty_like(U), ids=ids, batch_offsets=w.batches.offsets)
     else:
         g.step(U, dt, U_out=s1, ids=ids, batch_offsets=w.batches.offsets)
     g.sync()
     g.close()
-    print("stage-only %s config %d: %d sub-grids" % (args.stage_only, args.config, w.grid.n))
+    print("stage-only %s config %d: %d sub-grids (cw84 %d, one-launch %d)" % (args.stage_only, args.config, w.grid.n,
+                                                                              args.cw84, args.fused))
     return 0
 
 
