@@ -74,6 +74,11 @@ def lib():
         L.oracle_margin_cells.restype = ctypes.c_long
         L.oracle_ghost_cell.argtypes = [ctypes.POINTER(_Grid), ctypes.c_void_p] + [ctypes.c_int] * 6
         L.oracle_ghost_cell.restype = ctypes.c_double
+        L.oracle_fill_ghosts_full.argtypes = [ctypes.POINTER(_Grid), ctypes.c_void_p]
+        L.oracle_simpson_flux.argtypes = [dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, dp]
+        L.oracle_simpson_flux.restype = ctypes.c_double
+        L.oracle_stage3d.argtypes = [ctypes.POINTER(_Grid), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_void_p, dp, ctypes.c_int]
         _lib = L
     return _lib
 
@@ -96,6 +101,17 @@ def face_eos(U, d, gamma=5.0 / 3.0, eta=1e-3):
     u, p, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     lib().oracle_face_eos(_dptr(U), d, gamma, eta, ctypes.byref(u), ctypes.byref(p), ctypes.byref(c))
     return u.value, p.value, c.value
+
+
+def simpson_flux(AL, AR, d, gamma=5.0 / 3.0, eta=1e-3, form=0):
+    """Simpson flux of one face from the face averages [3][3][11] (left, right) of
+    the 3 x 3 faces around it.  Returns (F[11], speed)."""
+    AL = np.ascontiguousarray(AL, np.float64)
+    AR = np.ascontiguousarray(AR, np.float64)
+    assert AL.shape == (3, 3, NF) and AR.shape == (3, 3, NF)
+    F = np.zeros(NF)
+    a = lib().oracle_simpson_flux(_dptr(AL), _dptr(AR), int(d), float(gamma), float(eta), int(form), _dptr(F))
+    return F, a
 
 
 def face_flux(UL, UR, d, gamma=5.0 / 3.0, eta=1e-3, form=0):
@@ -197,6 +213,37 @@ class Oracle:
         self._check(U)
         return float(lib().oracle_ghost_cell(ctypes.byref(self._g), U.ctypes.data, int(s), int(face), int(ga),
                                              int(c1), int(c2), int(f)))
+
+    def fill_ghosts_full(self, U: np.ndarray) -> np.ndarray:
+        """Every ghost cell of the padded cubes (faces, edges, corners) of a grid of one level."""
+        self._check(U)
+        if lib().oracle_fill_ghosts_full(ctypes.byref(self._g), U.ctypes.data) != 0:
+            raise ValueError("the 3D reconstruction needs a grid of one level")
+        return U
+
+    def stage3d(self, Uin: np.ndarray, dt: float, U0: Optional[np.ndarray] = None, beta: float = 1.0,
+                Uout: Optional[np.ndarray] = None, nthreads: int = 0):
+        """One RK stage with the 3D reconstruction and Simpson face quadrature
+        (every sub-grid; ghosts filled by fill_ghosts_full).  Returns (Uout,
+        max_speed[2], status)."""
+        self._check(Uin)
+        if U0 is not None:
+            self._check(U0)
+        Uout = Uin.copy() if Uout is None else Uout
+        ms = np.zeros(2)
+        st = lib().oracle_stage3d(ctypes.byref(self._g), Uin.ctypes.data, None if U0 is None else U0.ctypes.data,
+                                  float(beta), float(dt), Uout.ctypes.data, _dptr(ms), int(nthreads))
+        return Uout, ms, st
+
+    def rk3_step3d(self, U: np.ndarray, dt: float, nthreads: int = 0):
+        """One SSP-RK3 step with stage3d (ghosts refilled before each stage)."""
+        self.fill_ghosts_full(U)
+        U1, ms, st1 = self.stage3d(U, dt, nthreads=nthreads)
+        self.fill_ghosts_full(U1)
+        U2, _, st2 = self.stage3d(U1, dt, U0=U, beta=0.25, nthreads=nthreads)
+        self.fill_ghosts_full(U2)
+        U3, _, st3 = self.stage3d(U2, dt, U0=U, beta=2.0 / 3.0, nthreads=nthreads)
+        return U3, ms, st1 | st2 | st3
 
     def totals(self, U: np.ndarray) -> np.ndarray:
         self._check(U)

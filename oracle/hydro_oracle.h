@@ -105,6 +105,19 @@ int oracle_fill_ghosts(const oracle_grid *g, double *U);
  * reads the fourth layer). */
 double oracle_ghost_cell(const oracle_grid *g, const double *U, int s, int face, int ga, int c1, int c2, int f);
 
+/* Three-dimensional reconstruction with Simpson face quadrature (grids of one
+ * level only; see the definition): fill every ghost cell of the padded cube,
+ * faces, edges and corners (ORACLE_ERR_INVALID on a grid of several levels),
+ * and one RK stage of every sub-grid, as oracle_stage with the face fluxes
+ * of that reconstruction (no coarse-fine faces, no correction). */
+int oracle_fill_ghosts_full(const oracle_grid *g, double *U);
+/* The Simpson flux of one face from the face averages of the 3 x 3 faces
+ * around it (AL, AR: [b2][b1][f], the left and right states); returns the
+ * largest point signal speed. */
+double oracle_simpson_flux(const double *AL, const double *AR, int d, double gamma, double eta, int form, double *F);
+int oracle_stage3d(const oracle_grid *g, const double *Uin, const double *U0, double beta, double dt, double *Uout,
+                   double *max_speed, int nthreads);
+
 /* Grid totals T_f = sum_s dx_s^3 sum_cells U_f, Neumaier-compensated, fixed order. */
 void oracle_totals(const oracle_grid *g, const double *U, double *totals);
 

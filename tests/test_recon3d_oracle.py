@@ -1,0 +1,196 @@
+"""Pins of the oracle's three-dimensional reconstruction with Simpson face
+quadrature (grids of one level; `Oracle.stage3d`, `oracle.simpson_flux`).
+
+What fixes it here: the full ghost fill reproduces the periodic global field in
+every padded cell (faces, edges, corners); the Simpson flux of a face is the
+exact face average of the flux for states quadratic across the face (a shear
+whose momentum flux rho u^2 + p the midpoint rule misses by b^2 h^2 / 12), is
+the point flux for a uniform face, takes a constant transverse profile at a
+local extremum and the monotonized-central line where the parabola would leave
+the neighbours' range; one stage keeps a uniform state bit-exact, conserves on
+a periodic domain, keeps mirror images bit for bit, reduces to the
+dimension-split midpoint scheme when the state varies along one axis only or
+when every flux is linear in the state (uniform velocity and temperature), and
+refuses grids of several levels."""
+import numpy as np
+import pytest
+
+from paper_2210_06437_gb300 import workloads as W
+from tests import helpers as H
+from tests import r12 as R
+
+G53 = 5.0 / 3.0
+IN = (slice(None), slice(None), slice(3, 11), slice(3, 11), slice(3, 11))
+NB = (2, 2, 2)
+
+
+def _grid(nb=NB, periodic=True):
+    return W.uniform_grid(nb, (0.0, 0.0, 0.0), 1.0 / (8 * nb[0]), periodic=(periodic,) * 3)
+
+
+def test_full_ghost_fill_is_the_periodic_field(oracle_mod):
+    G = H.random_smooth_global((16, 16, 16), 3)
+    g = _grid()
+    o = oracle_mod.Oracle(g)
+    U = o.fill_ghosts_full(H.scatter(G, NB))
+    for s in range(g.n):
+        base = np.round(g.origin[s] / g.dx[s]).astype(int) - 3   # global index of padded cell 0 (x, y, z)
+        idx = [(base[a] + np.arange(14)) % 16 for a in range(3)]
+        expect = G[:, idx[2]][:, :, idx[1]][:, :, :, idx[0]]
+        assert np.array_equal(U[s], expect), s
+
+
+def _face_state(rho, u, p):
+    """Conserved state (11) of density rho, x velocity u, pressure p."""
+    X = [0.1, 0.2, 0.3, 0.4, 0.5]
+    E = p / (G53 - 1.0) + 0.5 * rho * u * u
+    tau = (p / (G53 - 1.0)) ** (1.0 / G53)
+    return np.array([rho, rho * u, 0.0, 0.0, E, tau] + [rho * x for x in X])
+
+
+def _averages(rho, u_avg, u2_avg, p):
+    """Face-average state of a face cell with rho, p uniform, mean velocity
+    u_avg and mean u^2 u2_avg (the energy carries the mean kinetic energy)."""
+    A = _face_state(rho, u_avg, p)
+    A[4] = p / (G53 - 1.0) + 0.5 * rho * u2_avg
+    return A
+
+
+def test_simpson_flux_is_exact_for_a_transverse_quadratic(oracle_mod):
+    """u = U0 + b y across the face (first transverse axis, cells of width 1),
+    rho = 1, p = 1, and a first scalar X = X0 + c1 y + c2 y^2 (monotone, with a
+    parabola inside its neighbours' range, so unlimited):
+      * the x-momentum flux averages rho u^2 + p = U0^2 + b^2 / 12 + 1
+        exactly; the point flux of the averaged state misses b^2 / 12;
+      * the scalar's flux X u is cubic in y, which the Simpson rule integrates
+        exactly when the parabola's point values are exact:
+        X0 U0 + (c2 U0 + c1 b) / 12; the midpoint flux misses c1 b / 12."""
+    U0, b, p = 0.7, 0.9, 1.0
+    X0, c1, c2 = 0.3, 0.1, 0.02
+    AL = np.zeros((3, 3, 11))
+    for b2 in range(3):
+        for b1 in range(3):
+            y = float(b1 - 1)
+            AL[b2, b1] = _averages(1.0, U0 + b * y, (U0 + b * y) ** 2 + b * b / 12.0, p)
+            AL[b2, b1, 6] = X0 + c1 * y + c2 * (y * y + 1.0 / 12.0)
+    F, _ = oracle_mod.simpson_flux(AL, AL, 0, eta=0.0)
+    exact = U0 ** 2 + b * b / 12.0 + p
+    assert F[1] == pytest.approx(exact, rel=1e-14)
+    exact_x = X0 * U0 + (c2 * U0 + c1 * b) / 12.0
+    assert F[6] == pytest.approx(exact_x, rel=1e-14)
+    Fmid, _ = oracle_mod.face_flux(AL[1, 1], AL[1, 1], 0, eta=0.0)
+    assert abs(Fmid[1] - exact) > 0.5 * b * b / 12.0
+    assert abs(Fmid[6] - exact_x) > 0.5 * c1 * b / 12.0
+
+
+def test_simpson_flux_of_a_uniform_face_is_the_point_flux(oracle_mod):
+    rng = np.random.default_rng(2)
+    for _ in range(3):
+        A = _face_state(rng.uniform(0.5, 2), rng.uniform(-1, 1), rng.uniform(0.5, 2))
+        AL = np.broadcast_to(A, (3, 3, 11)).copy()
+        B = _face_state(rng.uniform(0.5, 2), rng.uniform(-1, 1), rng.uniform(0.5, 2))
+        AR = np.broadcast_to(B, (3, 3, 11)).copy()
+        F, a = oracle_mod.simpson_flux(AL, AR, 0)
+        Fp, ap = oracle_mod.face_flux(A, B, 0)
+        np.testing.assert_allclose(F, Fp, rtol=4e-16 * 8, atol=1e-300)
+        assert a == ap
+
+
+def test_transverse_limiter(oracle_mod):
+    """At a local extremum of the three averages the profile is constant: with
+    u = 1, 2, 1 across the face (rho = p = 1, so E = 2, 3.5, 2, also an
+    extremum) the momentum flux is that of u = 2, i.e. 4 + 1.  Where the
+    parabola would leave the neighbours' range the line with the
+    monotonized-central slope min(|a+ - a-| / 2, 2|a0 - a-|, 2|a+ - a0|) takes
+    over: u = 0, 0.1, 1 gives the slope 0.2 and points 0, 0.1, 0.2; E = 1.5,
+    1.505, 2 gives the slope 0.01 and points 1.5, 1.505, 1.51; the pressures
+    (2/3)(E - u^2/2) at the points are 1, 1, 0.99333..., and the Simpson mean
+    of u^2 + p is (1 + 4 (0.01 + 1) + (0.04 + 2/3 * 1.49)) / 6."""
+    cases = (((1.0, 2.0, 1.0), 5.0),
+             ((0.0, 0.1, 1.0), (1.0 + 4.0 * 1.01 + (0.04 + 2.0 / 3.0 * 1.49)) / 6.0))
+    for us, expect in cases:
+        AL = np.zeros((3, 3, 11))
+        for b2 in range(3):
+            for b1 in range(3):
+                AL[b2, b1] = _face_state(1.0, us[b1], 1.0)
+        F, _ = oracle_mod.simpson_flux(AL, AL, 0, eta=0.0)
+        assert F[1] == pytest.approx(expect, rel=1e-14), (us, F[1])
+
+
+def _stage(oracle_mod, G, nb=NB, dt=0.004, threed=True):
+    g = _grid(nb)
+    o = oracle_mod.Oracle(g)
+    U = o.fill_ghosts_full(H.scatter(G, nb))
+    if threed:
+        U1, ms, st = o.stage3d(U, dt)
+    else:
+        U1, ms, st = o.stage(U, dt)
+    assert st == 0
+    return U1, U, g
+
+
+def test_uniform_state_and_conservation(oracle_mod):
+    G = H.prim_to_global(*(np.full((16, 16, 16), v) for v in (1.3, 0.2, -0.4, 0.1, 0.8)))
+    U1, U, _ = _stage(oracle_mod, G)
+    assert np.array_equal(U1[IN], U[IN])
+    G = H.random_smooth_global((16, 16, 16), 11)
+    U1, U, g = _stage(oracle_mod, G)
+    for f in range(W.NF):
+        before, absb = H.exact_total(g, U, f)
+        after, _ = H.exact_total(g, U1, f)
+        assert abs(after - before) <= 1e-13 * absb, f
+    assert np.max(np.abs(U1 - U)[IN]) > 1e-3
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_mirror_symmetry(oracle_mod, axis):
+    """The transverse parabolas negate their odd part exactly and the Simpson
+    sums add the two outer points first, so mirror images agree bit for bit."""
+    G = H.random_smooth_global((16, 16, 16), 21 + axis)
+    ax = 3 - axis
+
+    def mirror(X):
+        M = np.flip(X, axis=ax).copy()
+        M[1 + axis] *= -1.0
+        return M
+
+    a, _, _ = _stage(oracle_mod, G)
+    b, _, _ = _stage(oracle_mod, mirror(G))
+    assert np.array_equal(mirror(H.gather(a, NB)), H.gather(b, NB))
+
+
+def test_one_dimensional_data_is_the_midpoint_scheme(oracle_mod):
+    x = (np.arange(16) + 0.5) / 16
+    rho = np.broadcast_to(1.0 + 0.3 * np.sin(2 * np.pi * x), (16, 16, 16))
+    vx = np.broadcast_to(0.4 * np.cos(2 * np.pi * x), (16, 16, 16))
+    p = np.broadcast_to(1.0 + 0.2 * np.sin(4 * np.pi * x), (16, 16, 16))
+    z = np.zeros((16, 16, 16))
+    G = H.prim_to_global(rho, vx, z, z, p)
+    a, _, _ = _stage(oracle_mod, G)
+    b, _, _ = _stage(oracle_mod, G, threed=False)
+    res = R.r12(a, b)
+    assert np.all(res["err"] <= 1e-14), R.summary(res)
+
+
+def test_flux_linear_states_are_the_midpoint_scheme(oracle_mod):
+    """Uniform velocity and an isothermal density wave (p = rho): every
+    conserved field but the entropy tracer is proportional to rho, so the
+    limiters decide alike, the sound speed and with it the KNP speeds are
+    uniform, each flux is linear in the state, and the Simpson rule returns
+    the flux of the face averages."""
+    x = (np.arange(16) + 0.5) / 16
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    rho = np.broadcast_to(1.0 + 0.3 * np.sin(2 * np.pi * (X + Y)), (16, 16, 16))
+    one = np.ones((16, 16, 16))
+    G = H.prim_to_global(rho, 0.5 * one, 0.3 * one, 0.0 * one, rho)
+    a, _, _ = _stage(oracle_mod, G)
+    b, _, _ = _stage(oracle_mod, G, threed=False)
+    res = R.r12(a, b)
+    assert np.all(res["err"] <= 1e-13), R.summary(res)
+
+
+def test_grids_of_several_levels_are_refused(oracle_mod):
+    w = W.config(3)
+    o = oracle_mod.Oracle(w.grid)
+    with pytest.raises(ValueError):
+        o.fill_ghosts_full(w.state())
