@@ -15,7 +15,10 @@
  *     Kurganov-Tadmor (2000) flux as the a+ = -a- special case;
  *   - Shu-Osher SSP-RK3 stage blend U0 + beta (U* - U0), beta supplied by the
  *     caller (alpha = 1 - beta; the form keeps a uniform state exactly);
- *   - Neumaier compensated summation for the totals.
+ *   - Neumaier compensated summation for the totals;
+ *   - the three-dimensional reconstruction with Simpson face quadrature that
+ *     Sections IV-C and V-B.1 name, for grids of one level, in the reading
+ *     stated where it is defined (oracle_stage3d).
  * Readings where the paper is silent are listed with the design notes.
  *
  * Build: -O2 -ffp-contract=off, no -ffast-math, optional -fopenmp.
