@@ -54,21 +54,38 @@ TAU_RESYNC_BYTES_PER_CELL = 56.0  # tracer reset: read rho, s, E, tau (48 B), wr
 # per clock at 100 %); an FMA counts 2 flops
 FP64_PEAK_INST = 152 * 2 * 2.070e9
 FP64_PEAK_TFLOPS = 2 * FP64_PEAK_INST / 1e12
+# FP64 operations per cell-update of one stage of the 3D reconstruction with Simpson face quadrature,
+# the plain evaluation of the reading (every operation as written, branches taken per value): ncu's
+# per-opcode counters on the kernels' plain form (recon3d_faces + recon3d_flux + recon3d_update, one
+# stage on the 64^3 lognormal box, 262,144 cells): DADD 1,542,778,255, DMUL 1,342,567,247, DFMA 760,421,186
+RECON3D_FP64_INST_PER_CELL = (1542778255 + 1342567247 + 760421186) / 262144.0      # 13907.5
+RECON3D_FLOPS_PER_CELL = (1542778255 + 1342567247 + 2 * 760421186) / 262144.0     # 16808.3
 # DRAM bytes (read + write) per cell-update of the mixed stage kernel from one ncu capture
-# (average of the three RK3 stage launches), valid only for the kernel source it was taken on.
-STAGE_TRAFFIC = {"sha256_prefix": "33a81225b2eb6758", "bytes_per_cell": 303.6,
+# (average of the three RK3 stage launches), valid only for the kernel sources it was taken on
+# (STAGE_SOURCES, hashed in that order).
+STAGE_TRAFFIC = {"sha256_prefix": "9e9b4e981b1715ab", "bytes_per_cell": 302.4,
                  "source": "ncu capture of the three RK3 stage launches on the 4097-leaf reduced binary octree "
                            "(average), scaled by cells"}
+
+
+STAGE_SOURCES = ("hydro_stage.cu", "hydro_scheme.cuh", "hydro_cw84.cuh", "hydro_reflux.cuh", "hydro_fp.cuh",
+                 "hydro_internal.cuh")
+
+
+def stage_source_sha():
+    """sha256 of the stage kernel's sources (the .cu file and the headers it includes, in that order)."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in STAGE_SOURCES:
+        with open(os.path.join(ROOT, "paper_2210_06437_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def stage_traffic_bytes(cells):
     """Measured DRAM traffic of one mixed stage launch, or None if the kernel
     source changed since the counters were taken."""
-    import hashlib
-    path = os.path.join(ROOT, "paper_2210_06437_gb300", "csrc", "hydro_stage.cu")
-    with open(path, "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()
-    if not sha.startswith(STAGE_TRAFFIC["sha256_prefix"]):
+    if not stage_source_sha().startswith(STAGE_TRAFFIC["sha256_prefix"]):
         return None
     return STAGE_TRAFFIC["bytes_per_cell"] * cells
 
@@ -89,6 +106,10 @@ def parse():
                         "parameters, then exit; prints no benchmark line")
     p.add_argument("--cw84", type=int, default=0, help="profiling case: CW84 extensions (HYDRO_PARAM_CW84 bits)")
     p.add_argument("--fused", type=int, default=0, help="profiling case: the one-launch RK3 step (1)")
+    p.add_argument("--recon3d", type=int, default=0,
+                   help="profiling case (FP64, a grid of one level): the 3D reconstruction with Simpson face "
+                        "quadrature (1)")
+    p.add_argument("--skip-recon3d", action="store_true")
     p.add_argument("--sweep", action="store_true",
                    help="per-configuration table (one JSON line per configuration and precision, errors against "
                         "the oracle, oracle timings); not the benchmark line")
@@ -347,6 +368,7 @@ def run_stage_only(args):
     g = HY.HydroGrid(w.grid, precision=args.stage_only)
     g.set_param(HY.PARAM_CW84, args.cw84)
     g.set_param(HY.PARAM_FUSED_RK3, args.fused)
+    g.set_param(HY.PARAM_RECON3D, args.recon3d)
     ms = torch.zeros(2, dtype=torch.float64, device="cuda")
     s1 = torch.empty_like(U)
     g.step(U, 0.0, U_out=s1, ids=ids, batch_offsets=w.batches.offsets, max_speed=ms)
@@ -357,9 +379,44 @@ def run_stage_only(args):
         g.step(U, dt, U_out=s1, ids=ids, batch_offsets=w.batches.offsets)
     g.sync()
     g.close()
-    print("stage-only %s config %d: %d sub-grids (cw84 %d, one-launch %d)" % (args.stage_only, args.config, w.grid.n,
-                                                                              args.cw84, args.fused))
+    print("stage-only %s config %d: %d sub-grids (cw84 %d, one-launch %d, recon3d %d)"
+          % (args.stage_only, args.config, w.grid.n, args.cw84, args.fused, args.recon3d))
     return 0
+
+
+def run_recon3d(dev, stream, steps, warmup):
+    """One FP64 Shu-Osher stage with the 3D reconstruction and Simpson face
+    quadrature (three kernels) on the periodic 128^3 box of one level, timed
+    with CUDA events over `steps` stages after `warmup`, beside the face-centre
+    FP64 stage on the same state.  Returns (config name, {form: (s per stage,
+    launches per stage)})."""
+    import torch
+    from paper_2210_06437_gb300 import hydro as HY
+    from paper_2210_06437_gb300 import workloads as W
+    w = W.config(7)
+    U = torch.from_numpy(w.state()).to(dev)
+    out = torch.empty_like(U)
+    ms = torch.zeros(2, dtype=torch.float64, device=dev)
+    res = {}
+    for form in ("simpson", "face_centre"):
+        g = HY.HydroGrid(w.grid, precision="fp64")
+        g.set_param(HY.PARAM_RECON3D, 1 if form == "simpson" else 0)
+        g.step(U, 0.0, U_out=out, max_speed=ms)
+        dt = 0.4 / float(ms[1])
+        for _ in range(warmup):
+            g.step(U, dt, U_out=out, max_speed=ms)
+        torch.cuda.synchronize()
+        l0 = g.launches
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            g.step(U, dt, U_out=out, max_speed=ms)
+        b.record(stream)
+        torch.cuda.synchronize()
+        res[form] = (a.elapsed_time(b) / 1e3 / steps, (g.launches - l0) / steps)
+        g.sync()
+        g.close()
+    return w, res
 
 
 # ---------------------------------------------------------------------------
@@ -498,6 +555,8 @@ def main():
     results["mixed"] = run_precision("mixed", ClockSampler(smi_index) if rank == 0 else None)
     if not args.skip_fp64:
         results["fp64"] = run_precision("fp64", None)
+    if not args.skip_recon3d and world == 1:
+        results["recon3d"] = run_recon3d(dev, stream, args.steps, args.warmup)
 
     # end-to-end through the public API with host buffers (mixed path): the
     # state lives on the host as packed interiors (pinned) and every step
@@ -649,6 +708,27 @@ def main():
                                      "hbm_frac": BYTES_PER_CELL_RK3_STAGE * cells / f["t_stage"] / 1e9 / hbm},
                         "gpu_launches": f["launches"]}
         line["mixed_speedup_vs_fp64"] = f["t_step"] / r["t_step"]
+    if "recon3d" in results:
+        w3, t3 = results["recon3d"]
+        t_s, n_l = t3["simpson"]
+        counted = RECON3D_FP64_INST_PER_CELL is not None
+        inst3 = RECON3D_FP64_INST_PER_CELL * w3.cells / t_s if counted else None
+        fl3 = RECON3D_FLOPS_PER_CELL * w3.cells / t_s / 1e12 if counted else None
+        line["recon3d"] = {
+            "workload": "%s (config %d): %s" % (w3.name, w3.index, w3.description),
+            "value": w3.cells / t_s, "unit": "cell-updates/s", "ms_per_stage": t_s * 1e3,
+            "launches_per_stage": n_l, "face_centre_fp64_stage_ms": t3["face_centre"][0] * 1e3,
+            "cost_vs_face_centre": t_s / t3["face_centre"][0],
+            "l2": "inputs larger than L2 (1.0 GB state, 2.6 GB scratch)",
+            "roofline": {"bound": "alu", "achieved": fl3, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": fl3 / FP64_PEAK_TFLOPS if counted else None, "traffic": None,
+                         "inst_frac": inst3 / FP64_PEAK_INST if counted else None,
+                         "counts": ("FP64 operations per cell-update of the three kernels counted by ncu (DADD + "
+                                    "DMUL + DFMA = %.1f instructions, %.1f flops)" % (RECON3D_FP64_INST_PER_CELL,
+                                                                                    RECON3D_FLOPS_PER_CELL))
+                                   if counted else "not counted for this source",
+                         "peak_source": "unit count: 152 SMs x 2 FP64 instructions/clk x 2.07 GHz",
+                         "kernel": "recon3d_faces + recon3d_flux + recon3d_update (one FP64 stage)"}}
     print(json.dumps(line))
     if pg:
         pg.destroy_process_group()

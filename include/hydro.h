@@ -40,7 +40,7 @@ typedef enum {
   HYDRO_OK = 0,
   HYDRO_ERR_INVALID = -1,   /* bad argument (host) or bad sub-grid id (device) */
   HYDRO_ERR_CUDA = -2,      /* a CUDA runtime call failed; see hydro_last_error */
-  HYDRO_ERR_NOMEM = -3,     /* device or host allocation failed in hydro_create */
+  HYDRO_ERR_NOMEM = -3,     /* device or host allocation failed in hydro_create (or hydro_set_param) */
   HYDRO_ERR_NONFINITE = -4, /* an updated value is not finite, or a density <= 0 */
   HYDRO_ERR_TIMEOUT = -5,   /* a bounded device wait gave up (HYDRO_PARAM_WAIT_LIMIT) */
   HYDRO_ERR_STATE = -6      /* call not valid in the handle's current state */
@@ -383,12 +383,34 @@ typedef enum {
                                         interleaves the stages of each sub-grid, which cannot complete while a
                                         CTA holds a later stage whose inputs are queued behind it: its bounded
                                         waits give up (HYDRO_ERR_TIMEOUT), which is all it is for */
-  HYDRO_PARAM_CW84 = 10              /* PPM extensions of Colella & Woodward (1984), both 0 by default: bit 0
+  HYDRO_PARAM_CW84 = 10,             /* PPM extensions of Colella & Woodward (1984), both 0 by default: bit 0
                                         shock flattening (their Section 4; reads the pressure one cell beyond
                                         the three ghost layers, from the neighbours' interiors), bit 1 contact
                                         steepening (their eqs. 1.14-1.17, detected on the density); both
                                         coefficients apply to every conserved field.  Stages and RK3 steps
                                         then use a stage kernel built with them (RK3 steps in three launches) */
+  HYDRO_PARAM_RECON3D = 11           /* face fluxes: 0 (default) the face-centre flux of the states that PPM
+                                        along the face normal gives; 1 the three-dimensional reconstruction
+                                        with Simpson face quadrature (Section IV-C names a full 3D
+                                        reconstruction, Section V-B.1 a Newton-Cotes rule over each face):
+                                        the left and right face averages of the 3 x 3 faces around a face
+                                        determine, per field, the tensor product of the parabolas with those
+                                        three-cell averages across the face (first along the face's first
+                                        transverse axis, then its second), limited to stay monotone (constant
+                                        at a local extremum of the three averages; the monotonized-central
+                                        line where an edge value leaves the neighbouring averages' range or
+                                        the centre value the edge values' range); its values at the 3 x 3
+                                        Simpson points (offsets -1/2, 0, +1/2 of the face width) give nine
+                                        central-upwind fluxes, combined with the weights (1, 4, 1)/6 along
+                                        each transverse axis (outer points added first).  FP64 handles on
+                                        grids of one level (one cell width, no coarse-fine faces) only,
+                                        without CW84 extensions, else HYDRO_ERR_INVALID; enabling it
+                                        allocates 627 kB of device scratch per sub-grid (HYDRO_ERR_NOMEM
+                                        when that fails).  Stages (at most n_subgrids items) and RK3 steps
+                                        (three launches) then run three kernels per stage: face averages
+                                        (halos read from face, edge and corner neighbours), Simpson fluxes,
+                                        update; results equal a plain FP64 evaluation bit for bit, with the
+                                        same exception as hydro_step (tau^gamma) */
 } hydro_param;
 
 /* Release the handle and its device scratch (waits for its work first). */

@@ -16,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhydro.so")
-SOURCES = ["hydro_stage.cu", "hydro_ghost.cu", "hydro_totals.cu", "hydro_reflux.cu", "hydro_queue.cu", "hydro_api.cu"]
+SOURCES = ["hydro_stage.cu", "hydro_ghost.cu", "hydro_totals.cu", "hydro_reflux.cu", "hydro_queue.cu", "hydro_api.cu",
+           "hydro_recon3d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), "-I", CSRC,
          "--expt-relaxed-constexpr"]

@@ -103,6 +103,10 @@ struct hydro_handle {
   int occupancy_fused = 1;             // resident CTAs per SM of the one-launch kernel
   int occupancy_cw = 1;                // resident CTAs per SM of the stage kernel with the CW84 extensions
   int cw84 = 0;                        // CW84 PPM extensions: bit 0 flattening, bit 1 contact steepening
+  int single_level = 0;                // one cell width and no coarse-fine faces
+  int recon3d = 0;                     // FP64 stages by the 3D reconstruction with Simpson face quadrature
+  double* d_r3_fa = nullptr;           // its scratch: face averages and face fluxes of n items
+  double* d_r3_fl = nullptr;
   int32_t* d_done = nullptr;           // [n] stages completed in the current launch
   int32_t* d_arrive = nullptr;         // mixed: [n_cf_list] arrivals at each coarse sub-grid
   int32_t* d_cf_slot = nullptr;        // mixed: [n] row in d_cf, -1 if none
@@ -167,6 +171,8 @@ void free_all(hydro_handle* h) {
   cudaFree(h->d_arrive);
   cudaFree(h->d_cf_slot);
   cudaFree(h->d_cf_target);
+  cudaFree(h->d_r3_fa);
+  cudaFree(h->d_r3_fl);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
 }
 
@@ -273,12 +279,45 @@ void fill_reflux(hydro_handle* h, RefluxArgs& r, const StageArgs& a) {
   r.shape = h->reflux_shape;
 }
 
+// One FP64 stage by the 3D reconstruction (the handle's parameter checks made
+// it a grid of one level); the batch may list at most n items.
+int enqueue_recon3d(hydro_handle* h, const int32_t* ids, int n_items, const double* Uin, const double* U0,
+                    double beta, double dt, const double* dt_dev, double* Uout, unsigned long long* ms,
+                    cudaStream_t st) {
+  if (n_items > h->n) return fail(h, HYDRO_ERR_INVALID, "the 3D reconstruction takes at most n items per stage");
+  Recon3dArgs r;
+  std::memset(&r, 0, sizeof(r));
+  r.Uin = Uin;
+  r.U0 = U0;
+  r.Uout = Uout;
+  r.ids = ids;
+  r.n_items = n_items;
+  r.n_sub = h->n;
+  r.dx = h->d_dx;
+  r.nb = h->d_nb;
+  r.beta = beta;
+  r.dt = dt;
+  r.dt_dev = dt_dev;
+  r.gamma = h->gamma;
+  r.eta = h->eta;
+  r.form = h->form;
+  r.fa = h->d_r3_fa;
+  r.fl = h->d_r3_fl;
+  r.max_speed = ms;
+  r.err = h->d_err;
+  cudaError_t e = launch_recon3d(r, st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "3D reconstruction kernel launch");
+  h->launches += 3;
+  return HYDRO_OK;
+}
+
 int enqueue_stage(hydro_handle* h, const int32_t* ids, int n_items, const double* Uin, const float* Sin,
                   const double* U0, double beta, double dt, const double* dt_dev, double* Uout, float* Sout,
                   unsigned long long* ms, int queue_slot, cudaStream_t st, int mode = 0, const double* Din = nullptr,
                   double* Dout = nullptr, const float* S0 = nullptr, bool all_items = false) {
   CUDA_TRY(h, cudaMemsetAsync(ms, 0, 2 * sizeof(unsigned long long), st));
   if (n_items == 0) return HYDRO_OK;
+  if (h->recon3d) return enqueue_recon3d(h, ids, n_items, Uin, U0, beta, dt, dt_dev, Uout, ms, st);
   CUDA_TRY(h, cudaMemsetAsync(h->d_queue + queue_slot, 0, sizeof(unsigned int), st));
   StageArgs a;
   fill_stage(h, a, ids, n_items, Uin, Sin, U0, beta, dt, dt_dev, Uout, Sout, ms, queue_slot, mode, Din, Dout, S0);
@@ -450,6 +489,9 @@ int hydro_create(const hydro_grid_desc* d, hydro_handle** out) {
     std::sort(widths.begin(), widths.end());
     widths.erase(std::unique(widths.begin(), widths.end()), widths.end());
     h->n_levels = (int)widths.size();
+    bool same = h->n_levels == 1;
+    for (int s = 0; s < n * 6 && same; ++s) same = d->neighbor_rel[s] == 0;
+    h->single_level = same ? 1 : 0;
     for (int s = 0; s < n; ++s)
       level[s] = (int8_t)(std::lower_bound(widths.begin(), widths.end(), d->dx[s]) - widths.begin());
     // the queue of a whole-grid stage: every sub-grid, finest level first
@@ -773,7 +815,7 @@ int enqueue_rk3_fused(hydro_handle* h, const int32_t* ids, int ni, double* U, do
 int enqueue_rk3_stages(hydro_handle* h, const int32_t* ids, int ni, double* U, double* s1, double* s2,
                        unsigned long long* ms, bool write_next, cudaStream_t cs) {
   int rc;
-  if (h->fused && h->fused_ok && !h->cw84 && ni == h->n) {
+  if (h->fused && h->fused_ok && !h->cw84 && !h->recon3d && ni == h->n) {
     rc = enqueue_rk3_fused(h, ids, ni, U, s1, s2, ms, write_next, cs);
     if (!rc && h->tau_resync)
       rc = enqueue_tau_resync(h, U, h->precision == HYDRO_MIXED && write_next ? h->d_shadow[0] : nullptr, cs);
@@ -1068,7 +1110,32 @@ int hydro_set_param(hydro_handle* h, int32_t key, int32_t value) {
   }
   if (key == HYDRO_PARAM_CW84) {
     if (value < 0 || value > 3) return fail(h, HYDRO_ERR_INVALID, "CW84 flags must be in 0..3");
+    if (value && h->recon3d) return fail(h, HYDRO_ERR_INVALID, "CW84 extensions with the 3D reconstruction");
     h->cw84 = value;
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+    return HYDRO_OK;
+  }
+  if (key == HYDRO_PARAM_RECON3D) {
+    if (value != 0 && value != 1) return fail(h, HYDRO_ERR_INVALID, "3D reconstruction must be 0 or 1");
+    if (value) {
+      if (h->precision != HYDRO_FP64) return fail(h, HYDRO_ERR_INVALID, "the 3D reconstruction is FP64 only");
+      if (!h->single_level) return fail(h, HYDRO_ERR_INVALID, "the 3D reconstruction needs a grid of one level");
+      if (h->cw84) return fail(h, HYDRO_ERR_INVALID, "the 3D reconstruction with CW84 extensions");
+      cudaError_t e = recon3d_prepare();
+      if (e != cudaSuccess) return cuda_fail(h, e, "3D reconstruction kernel attributes");
+      if (!h->d_r3_fa) {
+        if (cudaMalloc(&h->d_r3_fa, recon3d_scratch_doubles(h->n, 0) * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&h->d_r3_fl, recon3d_scratch_doubles(h->n, 1) * sizeof(double)) != cudaSuccess) {
+          cudaGetLastError();
+          cudaFree(h->d_r3_fa);
+          h->d_r3_fa = nullptr;
+          h->d_r3_fl = nullptr;
+          return fail(h, HYDRO_ERR_NOMEM, "3D reconstruction scratch allocation");
+        }
+      }
+    }
+    h->recon3d = value;
     for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
     h->graphs.clear();
     return HYDRO_OK;

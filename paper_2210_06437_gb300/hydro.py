@@ -21,7 +21,7 @@ HYDRO_FP64, HYDRO_MIXED = 0, 1
 HYDRO_FLUX_KNP, HYDRO_FLUX_KT = 0, 1
 PARAM_STAGE_CTAS_PER_SM, PARAM_GHOST_THREADS, PARAM_REFLUX, PARAM_TAU_RESYNC = 0, 1, 2, 3
 PARAM_WAIT_LIMIT, PARAM_QUEUE_ORDER, PARAM_STAGE_GRID = 4, 5, 6
-PARAM_PREFETCH_PASS, PARAM_REFLUX_SHAPE, PARAM_FUSED_RK3, PARAM_CW84 = 7, 8, 9, 10
+PARAM_PREFETCH_PASS, PARAM_REFLUX_SHAPE, PARAM_FUSED_RK3, PARAM_CW84, PARAM_RECON3D = 7, 8, 9, 10, 11
 CW84_FLATTEN, CW84_STEEPEN = 1, 2
 ITEM_FLUX_ONLY = 0x40000000   # batch id flag: export the sub-grid's coarse-fine fluxes, do not advance it
 RK3_BETA = (1.0, 0.25, 2.0 / 3.0)

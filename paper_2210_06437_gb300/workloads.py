@@ -379,7 +379,8 @@ def _smooth_periodic(g: np.ndarray, sigma: float) -> np.ndarray:
 
 def _init_lognormal(w: Workload, out):
     rng = np.random.Generator(np.random.PCG64(SEED_BASE + w.index))
-    m = 64
+    bx = int(round(w.grid.n ** (1.0 / 3.0)))    # sub-grids per edge of the periodic cube
+    m = bx * NX
     g = rng.standard_normal((m, m, m))          # [z][y][x]
     g = _smooth_periodic(g, 2.0)
     g = (g - g.mean()) / g.std()
@@ -387,7 +388,6 @@ def _init_lognormal(w: Workload, out):
     u = rng.uniform(-0.5, 0.5, (3, m, m, m))
     X = rng.uniform(0.0, 1.0, (5, m, m, m))
     U = empty_state(w.grid.n, out)
-    bx = m // NX
     for s in range(w.grid.n):
         i, j, k = s % bx, (s // bx) % bx, s // (bx * bx)
         sl = (slice(k * NX, (k + 1) * NX), slice(j * NX, (j + 1) * NX), slice(i * NX, (i + 1) * NX))
@@ -466,7 +466,8 @@ _CACHE: Dict[int, Workload] = {}
 
 def config(index: int) -> Workload:
     """Configurations 1..5 of the benchmark ladder (grid, batches, recipe); 6 is a
-    reduced copy of 5 for profiling."""
+    reduced copy of 5 for profiling; 7 a periodic box of one level for the
+    three-dimensional reconstruction."""
     if index in _CACHE:
         return _CACHE[index]
     if index == 1:
@@ -504,7 +505,14 @@ def config(index: int) -> Workload:
         b = zipf_batches(g.n, 1.1, 1024, rng)
         w = Workload("binary4k", 6, g, b, steps=5, cfl=0.4, precision="both", init=_init_binary,
                      description="4097-leaf reduced binary octree (levels 0-4) for profiling")
+    elif index == 7:
+        # a periodic box of one level at the size of the profiling octree: the
+        # measurement case of the three-dimensional reconstruction, which takes
+        # grids of one level only
+        g = uniform_grid((16, 16, 16), (0.0, 0.0, 0.0), 1.0 / 128)
+        w = Workload("lognormal128", 7, g, single_batch(g.n), steps=3, cfl=0.4, precision="fp64",
+                     init=_init_lognormal, description="4096 sub-grids, 128^3 periodic, smoothed lognormal density")
     else:
-        raise ValueError("configs are numbered 1..6")
+        raise ValueError("configs are numbered 1..7")
     _CACHE[index] = w
     return w
