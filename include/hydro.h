@@ -402,15 +402,20 @@ typedef enum {
                                         the centre value the edge values' range); its values at the 3 x 3
                                         Simpson points (offsets -1/2, 0, +1/2 of the face width) give nine
                                         central-upwind fluxes, combined with the weights (1, 4, 1)/6 along
-                                        each transverse axis (outer points added first).  FP64 handles on
-                                        grids of one level (one cell width, no coarse-fine faces) only,
-                                        without CW84 extensions, else HYDRO_ERR_INVALID; enabling it
-                                        allocates 627 kB of device scratch per sub-grid (HYDRO_ERR_NOMEM
-                                        when that fails).  Stages (at most n_subgrids items) and RK3 steps
-                                        (three launches) then run three kernels per stage: face averages
-                                        (halos read from face, edge and corner neighbours), Simpson fluxes,
-                                        update; results equal a plain FP64 evaluation bit for bit, with the
-                                        same exception as hydro_step (tau^gamma) */
+                                        each transverse axis (outer points added first).  Grids of one
+                                        level (one cell width, no coarse-fine faces) only, without CW84
+                                        extensions, else HYDRO_ERR_INVALID; enabling it allocates 627 kB of
+                                        device scratch per sub-grid (HYDRO_ERR_NOMEM when that fails).
+                                        Stages (at most n_subgrids items) and RK3 steps (three launches,
+                                        Shu-Osher stages in both precisions, scratch1/scratch2 holding U1
+                                        and U2) then run three kernels per stage: face averages (halos read
+                                        from face, edge and corner neighbours of the FP64 state), Simpson
+                                        fluxes, update.  FP64 handles: results equal a plain FP64
+                                        evaluation bit for bit, with the same exception as hydro_step
+                                        (tau^gamma).  Mixed handles: the state rounded to FP32 as for the
+                                        shadows, reconstruction, transverse parabolas, point fluxes and
+                                        Simpson sums in FP32, flux differences and update in FP64;
+                                        hydro_step_shadowed returns HYDRO_ERR_STATE */
 } hydro_param;
 
 /* Release the handle and its device scratch (waits for its work first). */

@@ -79,6 +79,8 @@ def lib():
         L.oracle_simpson_flux.restype = ctypes.c_double
         L.oracle_stage3d.argtypes = [ctypes.POINTER(_Grid), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_void_p, dp, ctypes.c_int]
+        L.oracle_margin_cells3d.argtypes = [ctypes.POINTER(_Grid), ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]
+        L.oracle_margin_cells3d.restype = ctypes.c_long
         _lib = L
     return _lib
 
@@ -234,6 +236,20 @@ class Oracle:
         st = lib().oracle_stage3d(ctypes.byref(self._g), Uin.ctypes.data, None if U0 is None else U0.ctypes.data,
                                   float(beta), float(dt), Uout.ctypes.data, _dptr(ms), int(nthreads))
         return Uout, ms, st
+
+    def margin_cells3d(self, U: np.ndarray, eps: float, mask: Optional[np.ndarray] = None):
+        """Interior cells beside faces whose 3D-reconstruction point states sit
+        within 64 eps of a transverse test or of the dual-energy test (U: any
+        padded state; its ghosts are filled on a copy).  Returns (mask [n, 8,
+        8, 8] uint8, OR-ed into `mask` when given, number of marked faces)."""
+        self._check(U)
+        Uf = self.fill_ghosts_full(U.copy())
+        m = np.zeros((self.grid.n, 8, 8, 8), np.uint8) if mask is None else mask
+        assert m.dtype == np.uint8 and m.flags.c_contiguous and m.shape == (self.grid.n, 8, 8, 8)
+        k = lib().oracle_margin_cells3d(ctypes.byref(self._g), Uf.ctypes.data, 64.0 * eps, m.ctypes.data)
+        if k < 0:
+            raise ValueError("the 3D reconstruction needs a grid of one level")
+        return m, int(k)
 
     def rk3_step3d(self, U: np.ndarray, dt: float, nthreads: int = 0):
         """One SSP-RK3 step with stage3d (ghosts refilled before each stage)."""

@@ -936,6 +936,48 @@ static void transverse_points(double am, double a0, double ap, double *lo, doubl
   *hi = h;
 }
 
+/* Whether a test of transverse_points(am, a0, ap) sits within t = tol S of its
+ * threshold (S the largest magnitude of the three averages and the parabola's
+ * three values) where taking it the other way would move a point value by
+ * more than t:
+ *   the extremum test, when a0 - am or ap - a0 is non-zero and at most t: the
+ *     other outcome is the parabola (or, if a range test holds, the line,
+ *     whose half-slope is at most that small difference);
+ *   the range tests, once the extremum test passes, when one of lo - am,
+ *     a0 - lo, hi - a0, ap - hi, mid - lo, hi - mid is non-zero and at most t
+ *     while no other range test holds by more than t: the outcomes are the
+ *     parabola and the line a0 -+ sl/2. */
+static int transverse_near(double am, double a0, double ap, double tol) {
+  const double d1 = ap - am;
+  const double d2 = (ap + am) - 2.0 * a0;
+  const double l = (a0 + d2 / 12.0) - d1 / 4.0;
+  const double h = (a0 + d2 / 12.0) + d1 / 4.0;
+  const double c = a0 - d2 / 24.0;
+  double S = max3(am, a0, ap);
+  const double S2 = max3(l, h, c);
+  if (S2 > S) S = S2;
+  const double t = tol * S;
+  /* the line of the limiter as if the extremum test passed */
+  double m = fabs(0.5 * d1);
+  if (2.0 * fabs(a0 - am) < m) m = 2.0 * fabs(a0 - am);
+  if (2.0 * fabs(ap - a0) < m) m = 2.0 * fabs(ap - a0);
+  const double half = 0.5 * (d1 > 0.0 ? m : -m);
+  const double jump_line = fmax(fmax(fabs(l - (a0 - half)), fabs(c - a0)), fabs(h - (a0 + half)));
+  const double a[3] = {l - am, h - a0, c - l}, b[3] = {a0 - l, ap - h, h - c};
+  int near_range = 0, clear_out = 0;
+  for (int k = 0; k < 3; ++k) {
+    const int nk = near_zero(a[k], t) || near_zero(b[k], t);
+    if (nk) near_range = 1;
+    else if (a[k] * b[k] < 0.0) clear_out = 1;
+  }
+  if (near_zero(ap - a0, t) || near_zero(a0 - am, t)) {
+    const double jump = clear_out ? fabs(half) : fmax(fmax(fabs(l - a0), fabs(c - a0)), fabs(h - a0));
+    if (jump > t) return 1;
+  }
+  if ((ap - a0) * (a0 - am) <= 0.0) return 0;
+  return near_range && !clear_out && jump_line > t;
+}
+
 /* The value of field f at padded cell (i, j, k) of sub-grid s, for any cell of
  * the 14^3 padded cube of a grid of one level: each coordinate outside the
  * interior moves to the neighbour across that face (outflow: the nearest
@@ -986,24 +1028,29 @@ typedef struct {
  * right face-average states of the 3 x 3 faces around it (b = 0, 1, 2 for
  * offsets -1, 0, +1 along the face's first and second transverse axes); F[f]
  * the Simpson flux; returns the largest point signal speed. */
+/* Steps 2-3 for one state of one face: A [b2][b1][f] the face averages of
+ * the 3 x 3 faces around it -> P [q2][q1][f] the point states; with near !=
+ * NULL, *near is set when one of the parabolas has a test near its threshold
+ * (transverse_near). */
+static void point_states(const double *A, double (*P)[3][NF], double tol, int *near) {
+  for (int f = 0; f < NF; ++f) {
+    double rows[3][3]; /* [b2][q1] */
+    for (int b2 = 0; b2 < 3; ++b2) {
+      const double am = A[(b2 * 3 + 0) * NF + f], a0 = A[(b2 * 3 + 1) * NF + f], ap = A[(b2 * 3 + 2) * NF + f];
+      transverse_points(am, a0, ap, &rows[b2][0], &rows[b2][1], &rows[b2][2]);
+      if (near && transverse_near(am, a0, ap, tol)) *near = 1;
+    }
+    for (int q1 = 0; q1 < 3; ++q1) {
+      transverse_points(rows[0][q1], rows[1][q1], rows[2][q1], &P[0][q1][f], &P[1][q1][f], &P[2][q1][f]);
+      if (near && transverse_near(rows[0][q1], rows[1][q1], rows[2][q1], tol)) *near = 1;
+    }
+  }
+}
+
 double oracle_simpson_flux(const double *AL, const double *AR, int d, double gamma, double eta, int form, double *F) {
   double PL[3][3][NF], PR[3][3][NF]; /* [q2][q1][f] point states */
-  for (int side = 0; side < 2; ++side)
-    for (int f = 0; f < NF; ++f) {
-      const double *A = side ? AR : AL;
-      double rows[3][3]; /* [b2][q1] */
-      for (int b2 = 0; b2 < 3; ++b2)
-        transverse_points(A[(b2 * 3 + 0) * NF + f], A[(b2 * 3 + 1) * NF + f], A[(b2 * 3 + 2) * NF + f],
-                          &rows[b2][0], &rows[b2][1], &rows[b2][2]);
-      for (int q1 = 0; q1 < 3; ++q1) {
-        double lo, mid, hi;
-        transverse_points(rows[0][q1], rows[1][q1], rows[2][q1], &lo, &mid, &hi);
-        double(*P)[3][NF] = side ? PR : PL;
-        P[0][q1][f] = lo;
-        P[1][q1][f] = mid;
-        P[2][q1][f] = hi;
-      }
-    }
+  point_states(AL, PL, 0.0, NULL);
+  point_states(AR, PR, 0.0, NULL);
   double Fq[3][3][NF];
   double amax = 0.0;
   for (int q2 = 0; q2 < 3; ++q2)
@@ -1052,6 +1099,76 @@ static double flux3d_subgrid(const oracle_grid *g, int s, const double *Uin, wor
         }
   }
   return amax;
+}
+
+/* Margin cells of the 3D reconstruction: per face, a transverse test of its
+ * point states within tol of its threshold (transverse_near) or the
+ * dual-energy test at one of its 18 point states (dual_energy_near) marks
+ * the two cells beside the face (their update is the only one that face's
+ * flux enters).  The transverse tests switch between outcomes that do not
+ * meet at the threshold (a parabola against a constant or a line), as the
+ * dual-energy test does.  U: every ghost cell filled
+ * (oracle_fill_ghosts_full); mask as for oracle_margin_cells, OR-ed with
+ * MARGIN_RECON3D and MARGIN_DUAL_ENERGY; returns the number of marked faces,
+ * or ORACLE_ERR_INVALID on a grid of several levels. */
+static void mark_cell(unsigned char *mask, int d, int t1, int t2, int c, unsigned char bit) {
+  if (c < NG || c >= NG + NX) return;
+  int i, j, k;
+  if (d == 0) { i = c; j = t1; k = t2; }
+  else if (d == 1) { i = t1; j = c; k = t2; }
+  else { i = t1; j = t2; k = c; }
+  mask[((k - NG) * NX + (j - NG)) * NX + (i - NG)] |= bit;
+}
+
+long oracle_margin_cells3d(const oracle_grid *g, const double *U, double tol, unsigned char *mask) {
+  if (!g || !U || !mask || !single_level(g)) return ORACLE_ERR_INVALID;
+  long found = 0;
+#ifdef _OPENMP
+#pragma omp parallel reduction(+ : found)
+#endif
+  {
+    face_avg_t *fa = (face_avg_t *)malloc(sizeof(face_avg_t));
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 4)
+#endif
+    for (int s = 0; s < g->n; ++s) {
+      unsigned char *ms = mask + (size_t)s * NX * NX * NX;
+      for (int d = 0; d < 3; ++d) {
+        for (int t2 = NG - 1; t2 <= NG + NX; ++t2)
+          for (int t1 = NG - 1; t1 <= NG + NX; ++t1)
+            for (int f = 0; f < NF; ++f) {
+              double q[NP];
+              for (int m = 0; m < NP; ++m) q[m] = U[pencil_at(s, f, d, t1, t2, m)];
+              oracle_ppm_pencil(q, fa->aL[t2 - NG + 1][t1 - NG + 1][f], fa->aR[t2 - NG + 1][t1 - NG + 1][f]);
+            }
+        for (int t2 = 0; t2 < NX; ++t2)
+          for (int t1 = 0; t1 < NX; ++t1)
+            for (int m = 2; m <= 10; ++m) {
+              double AL[3][3][NF], AR[3][3][NF], PL[3][3][NF], PR[3][3][NF];
+              for (int b2 = 0; b2 < 3; ++b2)
+                for (int b1 = 0; b1 < 3; ++b1)
+                  for (int f = 0; f < NF; ++f) {
+                    AL[b2][b1][f] = fa->aR[t2 + b2][t1 + b1][f][m];
+                    AR[b2][b1][f] = fa->aL[t2 + b2][t1 + b1][f][m + 1];
+                  }
+              int near = 0, dual = 0;
+              point_states(&AL[0][0][0], PL, tol, &near);
+              point_states(&AR[0][0][0], PR, tol, &near);
+              for (int q2 = 0; q2 < 3; ++q2)
+                for (int q1 = 0; q1 < 3; ++q1)
+                  if (dual_energy_near(PL[q2][q1], g->de_switch, tol) || dual_energy_near(PR[q2][q1], g->de_switch, tol))
+                    dual = 1;
+              if (!near && !dual) continue;
+              const unsigned char bit = (unsigned char)((near ? MARGIN_RECON3D : 0) | (dual ? MARGIN_DUAL_ENERGY : 0));
+              mark_cell(ms, d, t1 + NG, t2 + NG, m, bit);
+              mark_cell(ms, d, t1 + NG, t2 + NG, m + 1, bit);
+              ++found;
+            }
+      }
+    }
+    free(fa);
+  }
+  return found;
 }
 
 int oracle_stage3d(const oracle_grid *g, const double *Uin, const double *U0, double beta, double dt, double *Uout,

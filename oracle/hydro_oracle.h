@@ -92,6 +92,7 @@ int oracle_stage(const oracle_grid *g, const int32_t *ids, int32_t n_ids, const 
 #define MARGIN_OVERSHOOT 4   /* the parabola's two overshoot tests */
 #define MARGIN_DUAL_ENERGY 8 /* the dual-energy test at a face side */
 #define MARGIN_CW84 16       /* a test of the CW84 flattening or steepening (when enabled) */
+#define MARGIN_RECON3D 32    /* a transverse test of the 3D reconstruction (oracle_margin_cells3d) */
 long oracle_margin_cells(const oracle_grid *g, const int32_t *ids, int32_t n_ids, const double *U, double tol,
                          unsigned char *mask);
 
@@ -117,6 +118,11 @@ int oracle_fill_ghosts_full(const oracle_grid *g, double *U);
 double oracle_simpson_flux(const double *AL, const double *AR, int d, double gamma, double eta, int form, double *F);
 int oracle_stage3d(const oracle_grid *g, const double *Uin, const double *U0, double beta, double dt, double *Uout,
                    double *max_speed, int nthreads);
+/* Margin cells of the 3D reconstruction (see the definition): U with every
+ * ghost cell filled; mask [n][512] OR-ed with MARGIN_RECON3D and
+ * MARGIN_DUAL_ENERGY; returns the number of marked faces, ORACLE_ERR_INVALID
+ * on a grid of several levels. */
+long oracle_margin_cells3d(const oracle_grid *g, const double *U, double tol, unsigned char *mask);
 
 /* Grid totals T_f = sum_s dx_s^3 sum_cells U_f, Neumaier-compensated, fixed order. */
 void oracle_totals(const oracle_grid *g, const double *U, double *totals);

@@ -279,8 +279,8 @@ void fill_reflux(hydro_handle* h, RefluxArgs& r, const StageArgs& a) {
   r.shape = h->reflux_shape;
 }
 
-// One FP64 stage by the 3D reconstruction (the handle's parameter checks made
-// it a grid of one level); the batch may list at most n items.
+// One stage by the 3D reconstruction (the handle's parameter checks made it a
+// grid of one level); the batch may list at most n items.
 int enqueue_recon3d(hydro_handle* h, const int32_t* ids, int n_items, const double* Uin, const double* U0,
                     double beta, double dt, const double* dt_dev, double* Uout, unsigned long long* ms,
                     cudaStream_t st) {
@@ -301,6 +301,7 @@ int enqueue_recon3d(hydro_handle* h, const int32_t* ids, int n_items, const doub
   r.gamma = h->gamma;
   r.eta = h->eta;
   r.form = h->form;
+  r.mixed = h->precision == HYDRO_MIXED ? 1 : 0;
   r.fa = h->d_r3_fa;
   r.fl = h->d_r3_fl;
   r.max_speed = ms;
@@ -623,7 +624,7 @@ int hydro_step(hydro_handle* h, const hydro_batch* batch, const double* U_in, co
   cudaStream_t st = (cudaStream_t)stream;
   h->last_stream = st;
   const float* S = nullptr;
-  if (h->precision == HYDRO_MIXED && batch->n_items > 0) {
+  if (h->precision == HYDRO_MIXED && !h->recon3d && batch->n_items > 0) {
     // the shadows the stage reads: of the batch and its face neighbours when
     // the batch is small against the grid, else of the whole grid in one pass
     if ((int64_t)batch->n_items * 8 < (int64_t)h->n) {
@@ -704,6 +705,7 @@ int hydro_step_shadowed(hydro_handle* h, const hydro_batch* batch, const double*
                         void* stream) {
   if (!h) return HYDRO_ERR_INVALID;
   if (h->precision != HYDRO_MIXED) return fail(h, HYDRO_ERR_STATE, "hydro_step_shadowed needs a mixed-precision handle");
+  if (h->recon3d) return fail(h, HYDRO_ERR_STATE, "the 3D reconstruction reads no shadow");
   int rc = check_step(h, batch, U_in, U0, beta, dt, U_out, d_max_speed);
   if (rc) return rc;
   if (!S_in || !aligned(S_in, 16) || (S_out && !aligned(S_out, 16)))
@@ -821,7 +823,7 @@ int enqueue_rk3_stages(hydro_handle* h, const int32_t* ids, int ni, double* U, d
       rc = enqueue_tau_resync(h, U, h->precision == HYDRO_MIXED && write_next ? h->d_shadow[0] : nullptr, cs);
     return rc;
   }
-  if (h->precision == HYDRO_MIXED) {
+  if (h->precision == HYDRO_MIXED && !h->recon3d) {
     float *A = h->d_shadow[0], *B = h->d_shadow[1], *C = h->d_shadow[2];
     rc = enqueue_stage(h, ids, ni, U, A, nullptr, 1.0, 0.0, h->d_dt, nullptr, B, ms, 0, cs, 1, nullptr, s1, A, true);
     if (!rc)
@@ -862,7 +864,8 @@ int get_graph(hydro_handle* h, const GraphKey& k, GraphEntry** out) {
   // the stage kernel gathers halos from the neighbours' interiors itself, so
   // no ghost fill is needed between stages; in mixed precision each stage
   // reads the shadow of its input and writes the shadow of its output
-  const bool mixed = h->precision == HYDRO_MIXED;
+  // (the 3D reconstruction reads the FP64 state in both precisions)
+  const bool mixed = h->precision == HYDRO_MIXED && !h->recon3d;
   int rc = mixed ? enqueue_shadow(h, k.U, h->d_shadow[0], cs) : HYDRO_OK;
   if (k.n_steps == 0) {
     if (!rc) rc = enqueue_rk3_stages(h, k.ids, k.n_items, k.U, k.s1, k.s2, ms, false, cs);
@@ -1119,7 +1122,6 @@ int hydro_set_param(hydro_handle* h, int32_t key, int32_t value) {
   if (key == HYDRO_PARAM_RECON3D) {
     if (value != 0 && value != 1) return fail(h, HYDRO_ERR_INVALID, "3D reconstruction must be 0 or 1");
     if (value) {
-      if (h->precision != HYDRO_FP64) return fail(h, HYDRO_ERR_INVALID, "the 3D reconstruction is FP64 only");
       if (!h->single_level) return fail(h, HYDRO_ERR_INVALID, "the 3D reconstruction needs a grid of one level");
       if (h->cw84) return fail(h, HYDRO_ERR_INVALID, "the 3D reconstruction with CW84 extensions");
       cudaError_t e = recon3d_prepare();

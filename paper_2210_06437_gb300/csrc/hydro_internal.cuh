@@ -184,8 +184,9 @@ struct Recon3dArgs {
   double gamma;
   double eta;
   int32_t form;          // 0 KNP, 1 KT
-  double* fa;            // scratch: face averages, recon3d_scratch_doubles(n_items, 0)
-  double* fl;            // scratch: face fluxes, recon3d_scratch_doubles(n_items, 1)
+  int32_t mixed;         // 0: FP64 throughout; 1: FP32 reconstruction and fluxes, FP64 update
+  double* fa;            // scratch: face averages, recon3d_scratch_doubles(n_items, 0) (FP32 uses half)
+  double* fl;            // scratch: face fluxes, recon3d_scratch_doubles(n_items, 1) (FP32 uses half)
   unsigned long long* max_speed;  // [2] ordered bits of non-negative doubles
   int* err;
 };
@@ -232,7 +233,7 @@ int rk3_blocks_per_sm_mixed();
 int cw_blocks_per_sm_fp64();
 int cw_blocks_per_sm_mixed();
 cudaError_t launch_ghost_fill(const GhostArgs& a, int threads, cudaStream_t st);
-cudaError_t recon3d_prepare();  // kernel attributes, once before the first launch (outside graph capture)
+cudaError_t recon3d_prepare();  // kernel attributes of the current device (once per device; the launch calls it too)
 cudaError_t launch_recon3d(const Recon3dArgs& a, cudaStream_t st);
 // scratch doubles of the 3D stage for n_items items: which 0 face averages, 1 fluxes
 size_t recon3d_scratch_doubles(int n_items, int which);

@@ -31,6 +31,8 @@
 //           plane's largest point speed -> the global maximum;
 //   update  U* = U_in + dt/dx dU, U_out = U0 + beta (U* - U0).
 // Scratch (per item): face averages [3][2][11][9][100], fluxes [3][11][9][64].
+#include <mutex>
+
 #include "hydro_internal.cuh"
 #include "hydro_scheme.cuh"
 
@@ -69,8 +71,9 @@ __device__ __forceinline__ long long full_cell_offset(const int32_t* __restrict_
 // Step 1: face averages of the pencils along d.  fa[item][d][side][f][m][p]:
 // side 0 the right edge of cell m + 2 (the left state of face m + 2 + 1/2),
 // side 1 the left edge of cell m + 3; p = t2 * 10 + t1, t = -1 .. 8 + 1.
+template <typename T>
 __global__ void __launch_bounds__(R3_THREADS) recon3d_faces(Recon3dArgs a) {
-  __shared__ double q[NPEN3 * QS];
+  __shared__ T q[NPEN3 * QS];
   __shared__ long long src[NPEN3 * NP];
   const int t = blockIdx.x, d = blockIdx.y, tid = threadIdx.x;
   const int s = a.ids ? (a.ids[t] & ~ITEM_FLUX_ONLY) : t;
@@ -84,19 +87,19 @@ __global__ void __launch_bounds__(R3_THREADS) recon3d_faces(Recon3dArgs a) {
     const int i = d == 0 ? m : a1, j = d == 1 ? m : (d == 0 ? a1 : a2), k = d == 2 ? m : a2;
     src[e] = full_cell_offset(a.nb, s, i, j, k);
   }
-  double* out = a.fa + (size_t)t * 3 * FA_DIR + d * FA_DIR;
+  T* out = reinterpret_cast<T*>(a.fa) + (size_t)t * 3 * FA_DIR + d * FA_DIR;
   for (int f = 0; f < NF; ++f) {
     __syncthreads();  // src written / the previous field's pencils read
     for (int e = tid; e < NPEN3 * NP; e += R3_THREADS) {
       const int p = e / NP, m = e - p * NP;
-      q[p * QS + m] = __ldg(a.Uin + src[e] + (long long)f * NP3);
+      q[p * QS + m] = Arith<T>::from64(__ldg(a.Uin + src[e] + (long long)f * NP3));
     }
     __syncthreads();
     if (tid < NPEN3) {
-      double v[NP], ul[NFACE], ur[NFACE];
+      T v[NP], ul[NFACE], ur[NFACE];
 #pragma unroll
       for (int m = 0; m < NP; ++m) v[m] = q[tid * QS + m];
-      ppm_pencil<double>(v, ul, ur);
+      ppm_pencil<T>(v, ul, ur);
 #pragma unroll
       for (int m = 0; m < NFACE; ++m) {
         out[((size_t)(0 * NF + f) * NFACE + m) * NPEN3 + tid] = ul[m];
@@ -196,24 +199,59 @@ __device__ __forceinline__ void transverse_points(double am, double a0, double a
   mid = (flat || outside) ? a0 : c;
 }
 
+// FP32 (mixed precision): the same limited parabola, each product and sum
+// rounded separately (no contraction, so mirror images stay exact), d2/12 and
+// d2/24 as products with the rounded reciprocals, the half-slope as
+// min(|d1|/4, |a0 - am|, |ap - a0|) with the sign of a0 - am.
+__device__ __forceinline__ void transverse_points(float am, float a0, float ap, float& lo, float& mid, float& hi) {
+  const float dl = __fsub_rn(a0, am), dr = __fsub_rn(ap, a0);
+  const float d1 = __fsub_rn(ap, am);
+  const float d2 = __fsub_rn(__fadd_rn(ap, am), __fmul_rn(2.0f, a0));
+  const float q12 = __fmul_rn(d2, 1.0f / 12.0f);
+  const float q4 = __fmul_rn(d1, 0.25f);
+  const float base = __fadd_rn(a0, q12);
+  const float l = __fsub_rn(base, q4);
+  const float h = __fadd_rn(base, q4);
+  const float c = __fsub_rn(a0, __fmul_rn(d2, 1.0f / 24.0f));
+  const bool outside = __fmul_rn(__fsub_rn(l, am), __fsub_rn(a0, l)) < 0.0f ||
+                       __fmul_rn(__fsub_rn(h, a0), __fsub_rn(ap, h)) < 0.0f ||
+                       __fmul_rn(__fsub_rn(c, l), __fsub_rn(h, c)) < 0.0f;
+  const float mag = fminf(fabsf(q4), fminf(fabsf(dl), fabsf(dr)));
+  const float half = copysignf(mag, dl);
+  const bool flat = __fmul_rn(dr, dl) <= 0.0f;
+  lo = flat ? a0 : (outside ? __fsub_rn(a0, half) : l);
+  hi = flat ? a0 : (outside ? __fadd_rn(a0, half) : h);
+  mid = (flat || outside) ? a0 : c;
+}
+
+// The Simpson sum ((F0 + F2) + 4 F1) / 6: FP64 with the correctly rounded
+// quotient, FP32 with the product by the rounded reciprocal.
+__device__ __forceinline__ double simpson(double f0, double f1, double f2) {
+  return div_const<6>(__dadd_rn(__dadd_rn(f0, f2), __dmul_rn(4.0, f1)));
+}
+__device__ __forceinline__ float simpson(float f0, float f1, float f2) {
+  return __fmul_rn(__fadd_rn(__fadd_rn(f0, f2), __fmul_rn(4.0f, f1)), 1.0f / 6.0f);
+}
+
+template <typename T>
 struct FluxSmem {
-  double P[2][NPEN][NQ][NF];  // point states [side][face][q2 * 3 + q1][f]; then the point fluxes in P[0]
+  T P[2][NPEN][NQ][NF];  // point states [side][face][q2 * 3 + q1][f]; then the point fluxes in P[0]
   unsigned long long red[R3_THREADS / 32];
 };
 
 // Steps 2-4 for the 64 faces of plane m (faces m + 2 + 1/2 along D) of item t.
-template <int D>
-__device__ __forceinline__ void flux_plane(const Recon3dArgs& a, FluxSmem& sm, int t, int s, int m) {
+template <typename T, int D>
+__device__ __forceinline__ void flux_plane(const Recon3dArgs& a, FluxSmem<T>& sm, int t, int s, int m) {
   constexpr int d = D;
   const int tid = threadIdx.x;
-  const double* fa = a.fa + (size_t)t * 3 * FA_DIR + d * FA_DIR;
+  const T* fa = reinterpret_cast<const T*>(a.fa) + (size_t)t * 3 * FA_DIR + d * FA_DIR;
   // point states: one unit per (side, field, t1, half of the face column):
   // the row parabolas (along t1) of the 6 pencil rows that the 4 faces
   // t2 = 4 half .. 4 half + 3 read, then each face's 3 column parabolas
   for (int e = tid; e < 2 * NF * NX * 2; e += R3_THREADS) {
     const int t1 = e & 7, half = (e >> 3) & 1, sf = e >> 4, f = sf % NF, side = sf / NF;
-    const double* A = fa + ((size_t)(side * NF + f) * NFACE + m) * NPEN3 + 4 * half * TP + t1;
-    double rows[6][3];  // [row - 4 half][q1]
+    const T* A = fa + ((size_t)(side * NF + f) * NFACE + m) * NPEN3 + 4 * half * TP + t1;
+    T rows[6][3];  // [row - 4 half][q1]
 #pragma unroll
     for (int r = 0; r < 6; ++r)
       transverse_points(__ldg(A + r * TP), __ldg(A + r * TP + 1), __ldg(A + r * TP + 2), rows[r][0], rows[r][1],
@@ -223,7 +261,7 @@ __device__ __forceinline__ void flux_plane(const Recon3dArgs& a, FluxSmem& sm, i
       const int p = (4 * half + c) * NX + t1;
 #pragma unroll
       for (int q1 = 0; q1 < 3; ++q1) {
-        double lo, mid, hi;
+        T lo, mid, hi;
         transverse_points(rows[c][q1], rows[c + 1][q1], rows[c + 2][q1], lo, mid, hi);
         sm.P[side][p][0 * 3 + q1][f] = lo;
         sm.P[side][p][1 * 3 + q1][f] = mid;
@@ -233,35 +271,33 @@ __device__ __forceinline__ void flux_plane(const Recon3dArgs& a, FluxSmem& sm, i
   }
   __syncthreads();
   // point fluxes: one unit per (face, point); the flux overwrites the left state
-  double amax = 0.0;
+  T amax = T(0);
   for (int e = tid; e < NPEN * NQ; e += R3_THREADS) {
     const int p = e / NQ, qq = e - p * NQ;
-    double UL[NF], UR[NF], F[NF];
+    T UL[NF], UR[NF], F[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       UL[f] = sm.P[0][p][qq][f];
       UR[f] = sm.P[1][p][qq][f];
     }
-    const double sp = face_flux64(UL, UR, d, a.gamma, a.eta, a.form, F);
+    const T sp = face_flux<T>(UL, UR, d, T(a.gamma), T(a.eta), a.form, F);
     amax = (sp > amax || sp != sp) ? sp : amax;  // a NaN speed sticks
 #pragma unroll
     for (int f = 0; f < NF; ++f) sm.P[0][p][qq][f] = F[f];
   }
   __syncthreads();
   // Simpson sums: one unit per (field, face)
-  double* fl = a.fl + (size_t)t * 3 * FL_DIR + d * FL_DIR;
+  T* fl = reinterpret_cast<T*>(a.fl) + (size_t)t * 3 * FL_DIR + d * FL_DIR;
   for (int e = tid; e < NF * NPEN; e += R3_THREADS) {
     const int p = e & (NPEN - 1), f = e >> 6;
-    double row[3];
+    T row[3];
 #pragma unroll
     for (int q2 = 0; q2 < 3; ++q2)
-      row[q2] = div_const<6>(__dadd_rn(__dadd_rn(sm.P[0][p][q2 * 3 + 0][f], sm.P[0][p][q2 * 3 + 2][f]),
-                                       __dmul_rn(4.0, sm.P[0][p][q2 * 3 + 1][f])));
-    fl[((size_t)f * NFACE + m) * NPEN + p] =
-        div_const<6>(__dadd_rn(__dadd_rn(row[0], row[2]), __dmul_rn(4.0, row[1])));
+      row[q2] = simpson(sm.P[0][p][q2 * 3 + 0][f], sm.P[0][p][q2 * 3 + 1][f], sm.P[0][p][q2 * 3 + 2][f]);
+    fl[((size_t)f * NFACE + m) * NPEN + p] = simpson(row[0], row[1], row[2]);
   }
   // the plane's largest point speed (non-negative values order as their bits)
-  unsigned long long bits = (unsigned long long)__double_as_longlong(amax) & 0x7fffffffffffffffull;
+  unsigned long long bits = (unsigned long long)__double_as_longlong((double)amax) & 0x7fffffffffffffffull;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const unsigned long long w = __shfl_xor_sync(0xffffffffu, bits, o);
@@ -280,23 +316,25 @@ __device__ __forceinline__ void flux_plane(const Recon3dArgs& a, FluxSmem& sm, i
   }
 }
 
+template <typename T>
 __global__ void __launch_bounds__(R3_THREADS) recon3d_flux(Recon3dArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  FluxSmem& sm = *reinterpret_cast<FluxSmem*>(smem_raw);
+  FluxSmem<T>& sm = *reinterpret_cast<FluxSmem<T>*>(smem_raw);
   const int t = blockIdx.x, m = blockIdx.z;
   const int s = a.ids ? (a.ids[t] & ~ITEM_FLUX_ONLY) : t;
   if (s < 0 || s >= a.n_sub) return;  // reported by recon3d_faces
   if (blockIdx.y == 0)
-    flux_plane<0>(a, sm, t, s, m);
+    flux_plane<T, 0>(a, sm, t, s, m);
   else if (blockIdx.y == 1)
-    flux_plane<1>(a, sm, t, s, m);
+    flux_plane<T, 1>(a, sm, t, s, m);
   else
-    flux_plane<2>(a, sm, t, s, m);
+    flux_plane<T, 2>(a, sm, t, s, m);
 }
 
 // The update of one item, one thread per (field, cell) unit:
 //   dU = ((Fx(i-1/2) - Fx(i+1/2)) + (Fy(j-1/2) - Fy(j+1/2))) + (Fz(k-1/2) - Fz(k+1/2)),
 //   U* = U_in + (dt/dx) dU, U_out = U0 + beta (U* - U0) (U* when beta == 1).
+template <typename T>
 __global__ void __launch_bounds__(256) recon3d_update(Recon3dArgs a) {
   const int t = blockIdx.x;
   const int id = a.ids ? a.ids[t] : t;
@@ -304,14 +342,15 @@ __global__ void __launch_bounds__(256) recon3d_update(Recon3dArgs a) {
   if (s < 0 || s >= a.n_sub || (id & ITEM_FLUX_ONLY)) return;
   const double dt = a.dt_dev ? *a.dt_dev : a.dt;
   const double lam = __ddiv_rn(dt, __ldg(a.dx + s));
-  const double* fl = a.fl + (size_t)t * 3 * FL_DIR;
+  const T* fl = reinterpret_cast<const T*>(a.fl) + (size_t)t * 3 * FL_DIR;
   bool bad = false;
   for (int e = threadIdx.x; e < NF * CELLS; e += 256) {
     const int f = e / CELLS, c = e - f * CELLS;
     const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
-    const double* fx = fl + 0 * FL_DIR + (size_t)f * NFACE * NPEN;
-    const double* fy = fl + 1 * FL_DIR + (size_t)f * NFACE * NPEN;
-    const double* fz = fl + 2 * FL_DIR + (size_t)f * NFACE * NPEN;
+    const T* fx = fl + 0 * FL_DIR + (size_t)f * NFACE * NPEN;
+    const T* fy = fl + 1 * FL_DIR + (size_t)f * NFACE * NPEN;
+    const T* fz = fl + 2 * FL_DIR + (size_t)f * NFACE * NPEN;
+    // FP32 fluxes convert to FP64 exactly; the differences and the update are FP64
     const double fxl = fx[i * NPEN + k * 8 + j], fxh = fx[(i + 1) * NPEN + k * 8 + j];
     const double fyl = fy[j * NPEN + k * 8 + i], fyh = fy[(j + 1) * NPEN + k * 8 + i];
     const double fzl = fz[k * NPEN + j * 8 + i], fzh = fz[(k + 1) * NPEN + j * 8 + i];
@@ -335,15 +374,42 @@ size_t recon3d_scratch_doubles(int n_items, int which) {
   return (size_t)n_items * 3 * (which == 0 ? FA_DIR : FL_DIR);
 }
 
+// The flux kernel's shared-memory limit is an attribute of the function on
+// each device: set once per device, under a lock.
 cudaError_t recon3d_prepare() {
-  return cudaFuncSetAttribute(recon3d_flux, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FluxSmem));
+  constexpr int kMaxDevices = 64;
+  static std::mutex mu;
+  static bool done[kMaxDevices] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!done[dev]) {
+    e = cudaFuncSetAttribute(recon3d_flux<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(FluxSmem<double>));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(recon3d_flux<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(FluxSmem<float>));
+    if (e != cudaSuccess) return e;
+    done[dev] = true;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_recon3d(const Recon3dArgs& a, cudaStream_t st) {
   if (a.n_items <= 0) return cudaSuccess;
-  recon3d_faces<<<dim3(a.n_items, 3), R3_THREADS, 0, st>>>(a);
-  recon3d_flux<<<dim3(a.n_items, 3, NFACE), R3_THREADS, sizeof(FluxSmem), st>>>(a);
-  recon3d_update<<<a.n_items, 256, 0, st>>>(a);
+  const cudaError_t e = recon3d_prepare();
+  if (e != cudaSuccess) return e;
+  if (a.mixed) {
+    recon3d_faces<float><<<dim3(a.n_items, 3), R3_THREADS, 0, st>>>(a);
+    recon3d_flux<float><<<dim3(a.n_items, 3, NFACE), R3_THREADS, sizeof(FluxSmem<float>), st>>>(a);
+    recon3d_update<float><<<a.n_items, 256, 0, st>>>(a);
+  } else {
+    recon3d_faces<double><<<dim3(a.n_items, 3), R3_THREADS, 0, st>>>(a);
+    recon3d_flux<double><<<dim3(a.n_items, 3, NFACE), R3_THREADS, sizeof(FluxSmem<double>), st>>>(a);
+    recon3d_update<double><<<a.n_items, 256, 0, st>>>(a);
+  }
   return cudaGetLastError();
 }
 

@@ -25,8 +25,8 @@ import numpy as np
 
 FLOOR = 1e-8
 EPS = {"fp64": 2.0 ** -53, "mixed": 2.0 ** -24}
-M_SLOPE, M_EXTREMUM, M_OVERSHOOT, M_DUAL, M_CW84 = 1, 2, 4, 8, 16
-M_SWITCH = M_DUAL | M_CW84   # tests whose two outcomes need not meet at the threshold
+M_SLOPE, M_EXTREMUM, M_OVERSHOOT, M_DUAL, M_CW84, M_RECON3D = 1, 2, 4, 8, 16, 32
+M_SWITCH = M_DUAL | M_CW84 | M_RECON3D   # tests whose two outcomes need not meet at the threshold
 SL = (slice(None), slice(None), slice(3, 11), slice(3, 11), slice(3, 11))
 
 
@@ -95,7 +95,7 @@ def margin_union(oracle_obj, states, eps, ids=None):
     return mask
 
 
-def momentum_scaled(x, r, gamma=5.0 / 3.0):
+def momentum_scaled(x, r, gamma=5.0 / 3.0, margin=None):
     """Per field of the three momenta, the largest per-cell error measured
     against the cell's own momentum-density scale:
         max_cells |x - r| / max(|r|, rho c, 1e-8 ||r_f||_inf),
@@ -103,7 +103,8 @@ def momentum_scaled(x, r, gamma=5.0 / 3.0):
     (E - |s|^2 / 2 rho), clipped at 0).  It reads like R12 wherever a cell moves
     faster than sound and like an error relative to rho c in near-static cells,
     where the momentum one stage makes is a difference of face pressures far
-    below the pressure itself.  Returns an array of 3."""
+    below the pressure itself.  margin (optional, as for r12): cells with an
+    M_SWITCH bit are left out.  Returns an array of 3."""
     xi, ri = interiors(x), interiors(r)
     rho = ri[:, 0]
     s2 = ri[:, 1] ** 2 + ri[:, 2] ** 2 + ri[:, 3] ** 2
@@ -116,5 +117,7 @@ def momentum_scaled(x, r, gamma=5.0 / 3.0):
         sc = np.maximum(np.maximum(np.abs(ri[:, f]), rc), FLOOR * np.abs(ri[:, f]).max())
         with np.errstate(divide="ignore", invalid="ignore"):
             e = np.where(sc > 0, d / np.where(sc > 0, sc, 1.0), np.where(d == 0, 0.0, np.inf))
+        if margin is not None:
+            e = np.where((margin & M_SWITCH) != 0, 0.0, e)
         out[k] = e.max()
     return out

@@ -11,7 +11,8 @@ the neighbours' range; one stage keeps a uniform state bit-exact, conserves on
 a periodic domain, keeps mirror images bit for bit, reduces to the
 dimension-split midpoint scheme when the state varies along one axis only or
 when every flux is linear in the state (uniform velocity and temperature), and
-refuses grids of several levels."""
+refuses grids of several levels; its margin cells (transverse tests near their
+thresholds) are the faces a planted near-tie reaches and no others."""
 import numpy as np
 import pytest
 
@@ -194,3 +195,54 @@ def test_grids_of_several_levels_are_refused(oracle_mod):
     o = oracle_mod.Oracle(w.grid)
     with pytest.raises(ValueError):
         o.fill_ghosts_full(w.state())
+
+
+def _y_profile_state(ry):
+    rho = np.broadcast_to(ry[None, :, None], (16, 16, 16)).copy()
+    one = np.ones((16, 16, 16))
+    return H.scatter(H.prim_to_global(rho, 0.2 * one, 0.0 * one, 0.0 * one, one), NB)
+
+
+def _flagged_rows(m):
+    rows = set()
+    for s in range(8):
+        j = (s // 2) % 2
+        _, jj, _ = np.nonzero(m[s])
+        rows.update((jj + 8 * j).tolist())
+    return sorted(rows)
+
+
+def test_margin_cells_of_the_transverse_tests(oracle_mod):
+    """Density varying along y only (uniform u, p): the x- and z-faces see the
+    y-profile across them.  A smooth profile puts no transverse test near a
+    threshold where it matters.  Rows 4, 5, 6 set to A, A + D, A + 5 D (1 +
+    1e-9) give the parabola through those averages an edge value within 1e-9
+    D of the row-4 average: a range test within 64 x 2^-24 of its threshold
+    (not within 64 x 2^-53), between the parabola and the limited line, whose
+    edge values differ by D/2: exactly the x- and z-faces of row 5 are marked
+    (16 pencils x 18 face planes x 2 directions = 576) and the cells beside
+    them, all in row 5.  With A + 4.5 D in row 6 nothing is near.  (An
+    extremum test near its threshold alone is not marked: where one side's
+    difference is tiny the parabola leaves the range, and the line's slope is
+    at most that difference.)"""
+    o = oracle_mod.Oracle(_grid())
+    y = np.arange(16)
+    ry = 1.0 + 0.3 * np.sin(2 * np.pi * y / 16 + 0.3)
+    m, k = o.margin_cells3d(_y_profile_state(ry), 2.0 ** -24)
+    assert k == 0 and not m.any()
+    A, D = ry[4], 0.05
+    ry[5], ry[6] = A + D, A + 5.0 * D * (1.0 + 1e-9)
+    m, k = o.margin_cells3d(_y_profile_state(ry), 2.0 ** -24)
+    assert k == 576
+    assert _flagged_rows(m) == [5]
+    assert np.all((m == 0) | (m == R.M_RECON3D))
+    m, k = o.margin_cells3d(_y_profile_state(ry), 2.0 ** -53)
+    assert k == 0
+    ry[6] = A + 4.5 * D
+    m, k = o.margin_cells3d(_y_profile_state(ry), 2.0 ** -24)
+    assert k == 0
+    ry[5], ry[6] = A + 1e-9 * D, A + D      # a near extremum test alone
+    m, k = o.margin_cells3d(_y_profile_state(ry), 2.0 ** -24)
+    assert 5 not in _flagged_rows(m)
+    with pytest.raises(ValueError):
+        oracle_mod.Oracle(W.config(3).grid).margin_cells3d(W.config(3).state(), 2.0 ** -24)
