@@ -257,3 +257,60 @@ def test_mixed_shadowed_step_is_refused(hydro):
     S = g.empty_shadow()
     with pytest.raises(hydro.HydroError):
         g.step_shadowed(Ud, S, 1e-3)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_subset_and_empty_batches(hydro, oracle_mod, prec):
+    """A batch of some sub-grids (ragged, unordered) updates exactly those, as
+    the whole-grid stage does (their halos read the unlisted neighbours'
+    inputs); the others keep the output buffer's contents; an empty batch
+    launches nothing and reports zero speeds."""
+    grid, U = _box()
+    g = _grid3d_prec(hydro, grid, prec)
+    Ud = torch.from_numpy(U).cuda()
+    full, _ = g.step(Ud, 1e-3, U_out=torch.zeros_like(Ud))
+    ids = np.array([7, 2, 11, 0, 5], np.int32)
+    part, _ = g.step(Ud, 1e-3, U_out=torch.zeros_like(Ud), ids=ids)
+    g.sync()
+    full, part = full.cpu().numpy(), part.cpu().numpy()
+    assert np.array_equal(part[ids][IN], full[ids][IN])
+    rest = np.setdiff1d(np.arange(grid.n), ids)
+    assert not part[rest].any()
+    n0 = g.launches
+    out, ms = g.step(Ud, 1e-3, U_out=torch.zeros_like(Ud), ids=np.zeros(0, np.int32))
+    g.sync()
+    assert g.launches == n0 and not out.any().item() and not ms.any().item()
+
+
+def _grid3d_prec(hydro, grid, prec):
+    g = hydro.HydroGrid(grid, precision=prec)
+    g.set_param(hydro.PARAM_RECON3D, 1)
+    return g
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_run_graph_matches_separate_steps(hydro, prec):
+    """hydro_rk3_run_cfl over 3 steps (device CFL dt, totals) is bit-identical
+    to 3 hydro_rk3_step_cfl calls each followed by hydro_totals."""
+    w = W.config(2)
+    U = w.state()
+    g = _grid3d_prec(hydro, w.grid, prec)
+    res = []
+    for mode in ("separate", "run"):
+        Ud = torch.from_numpy(U).cuda()
+        s1, s2 = torch.empty_like(Ud), torch.empty_like(Ud)
+        ms = torch.zeros(2, dtype=torch.float64, device="cuda")
+        g.step(Ud, 0.0, U_out=s1, max_speed=ms)
+        dts = torch.zeros(3, dtype=torch.float64, device="cuda")
+        tots = torch.zeros((3, 11), dtype=torch.float64, device="cuda")
+        if mode == "separate":
+            for k in range(3):
+                g.rk3_step_cfl(Ud, 0.4, s1, s2, ms, dt_out=dts[k:k + 1])
+                g.totals(Ud, out=tots[k])
+        else:
+            g.rk3_run_cfl(Ud, 0.4, s1, s2, ms, 3, dt_out=dts, totals=tots)
+        g.sync()
+        res.append((Ud.cpu().numpy()[IN], dts.cpu().numpy(), tots.cpu().numpy(), ms.cpu().numpy()))
+    for a, b in zip(*res):
+        assert np.array_equal(a, b)
+    assert np.all(res[0][1] > 0)
