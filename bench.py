@@ -730,9 +730,9 @@ def main():
             "roofline": {"bound": "alu", "achieved": fl3, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": fl3 / FP64_PEAK_TFLOPS if counted else None, "traffic": None,
                          "inst_frac": inst3 / FP64_PEAK_INST if counted else None,
-                         "counts": ("FP64 operations per cell-update of the three kernels counted by ncu (DADD + "
-                                    "DMUL + DFMA = %.1f instructions, %.1f flops)" % (RECON3D_FP64_INST_PER_CELL,
-                                                                                    RECON3D_FLOPS_PER_CELL))
+                         "counts": ("FP64 operations per cell-update of the plain evaluation, counted by ncu on "
+                                    "the three kernels' plain form (DADD + DMUL + DFMA = %.1f instructions, %.1f "
+                                    "flops)" % (RECON3D_FP64_INST_PER_CELL, RECON3D_FLOPS_PER_CELL))
                                    if counted else "not counted for this source",
                          "peak_source": "unit count: 152 SMs x 2 FP64 instructions/clk x 2.07 GHz",
                          "kernel": "recon3d_faces + recon3d_flux + recon3d_update (one FP64 stage)"}}
