@@ -71,6 +71,9 @@ __device__ __forceinline__ long long full_cell_offset(const int32_t* __restrict_
 // Step 1: face averages of the pencils along d.  fa[item][d][side][f][m][p]:
 // side 0 the right edge of cell m + 2 (the left state of face m + 2 + 1/2),
 // side 1 the left edge of cell m + 3; p = t2 * 10 + t1, t = -1 .. 8 + 1.
+// (Loading field f + 1 into registers during field f's PPM was measured
+// slower: the registers it takes lower the occupancy more than the overlap
+// gains.)
 template <typename T>
 __global__ void __launch_bounds__(R3_THREADS) recon3d_faces(Recon3dArgs a) {
   __shared__ T q[NPEN3 * QS];
@@ -331,6 +334,28 @@ __global__ void __launch_bounds__(R3_THREADS) recon3d_flux(Recon3dArgs a) {
     flux_plane<T, 2>(a, sm, t, s, m);
 }
 
+// dU = ((fxl - fxh) + (fyl - fyh)) + (fzl - fzh) of one cell and field.
+// FP64: as written.  FP32 fluxes (mixed): each difference exactly as a float
+// pair (TwoSum), the three pairs summed by a TwoSum cascade (about 48 bits),
+// then widened, so that the scarce FP64 pipe sees one addition instead of the
+// six conversions and five operations of the FP64 form.
+__device__ __forceinline__ double divergence(double fxl, double fxh, double fyl, double fyh, double fzl, double fzh) {
+  return __dadd_rn(__dadd_rn(__dsub_rn(fxl, fxh), __dsub_rn(fyl, fyh)), __dsub_rn(fzl, fzh));
+}
+__device__ __forceinline__ double divergence(float fxl, float fxh, float fyl, float fyh, float fzl, float fzh) {
+  float sx, ex, sy, ey, sz, ez;
+  two_sum1(fxl, -fxh, sx, ex);
+  two_sum1(fyl, -fyh, sy, ey);
+  two_sum1(fzl, -fzh, sz, ez);
+  float h, l;
+  two_sum1(sx, sy, h, l);
+  l = __fadd_rn(l, __fadd_rn(ex, ey));
+  float h2, l2;
+  two_sum1(h, sz, h2, l2);
+  l2 = __fadd_rn(l2, __fadd_rn(l, ez));
+  return __dadd_rn(f32_to_f64(h2), f32_to_f64(l2));
+}
+
 // The update of one item, one thread per (field, cell) unit:
 //   dU = ((Fx(i-1/2) - Fx(i+1/2)) + (Fy(j-1/2) - Fy(j+1/2))) + (Fz(k-1/2) - Fz(k+1/2)),
 //   U* = U_in + (dt/dx) dU, U_out = U0 + beta (U* - U0) (U* when beta == 1).
@@ -350,11 +375,10 @@ __global__ void __launch_bounds__(256) recon3d_update(Recon3dArgs a) {
     const T* fx = fl + 0 * FL_DIR + (size_t)f * NFACE * NPEN;
     const T* fy = fl + 1 * FL_DIR + (size_t)f * NFACE * NPEN;
     const T* fz = fl + 2 * FL_DIR + (size_t)f * NFACE * NPEN;
-    // FP32 fluxes convert to FP64 exactly; the differences and the update are FP64
-    const double fxl = fx[i * NPEN + k * 8 + j], fxh = fx[(i + 1) * NPEN + k * 8 + j];
-    const double fyl = fy[j * NPEN + k * 8 + i], fyh = fy[(j + 1) * NPEN + k * 8 + i];
-    const double fzl = fz[k * NPEN + j * 8 + i], fzh = fz[(k + 1) * NPEN + j * 8 + i];
-    const double dU = __dadd_rn(__dadd_rn(__dsub_rn(fxl, fxh), __dsub_rn(fyl, fyh)), __dsub_rn(fzl, fzh));
+    const T fxl = fx[i * NPEN + k * 8 + j], fxh = fx[(i + 1) * NPEN + k * 8 + j];
+    const T fyl = fy[j * NPEN + k * 8 + i], fyh = fy[(j + 1) * NPEN + k * 8 + i];
+    const T fzl = fz[k * NPEN + j * 8 + i], fzh = fz[(k + 1) * NPEN + j * 8 + i];
+    const double dU = divergence(fxl, fxh, fyl, fyh, fzl, fzh);
     const size_t o = field_offset(s, f) + ((k + NG) * NP + (j + NG)) * NP + (i + NG);
     const double us = __dadd_rn(__ldg(a.Uin + o), __dmul_rn(lam, dU));
     double v = us;
