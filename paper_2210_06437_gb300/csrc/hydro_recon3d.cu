@@ -1,5 +1,6 @@
 // hydro_recon3d.cu -- one Runge-Kutta stage with the three-dimensional
-// reconstruction and Simpson face quadrature (FP64, grids of one level).
+// reconstruction and Simpson face quadrature (grids of one level; FP64, and
+// mixed precision).
 //
 // The paper names a full three-dimensional reconstruction (Section IV-C) and a
 // flux kernel that integrates over each face with a Newton-Cotes rule
@@ -17,9 +18,12 @@
 //      the range of the edge values;
 //   4. the central-upwind flux at each point, combined with the Simpson
 //      weights (1, 4, 1)/6 along each transverse axis, outer points first.
-// Every operation is rounded as the plain FP64 statement rounds it (no
-// contraction, correctly rounded quotients), so the stage equals a plain
-// evaluation of that reading bit for bit.
+// T = double: every operation is rounded as the plain FP64 statement rounds it
+// (no contraction, correctly rounded quotients), so the stage equals a plain
+// evaluation of that reading bit for bit.  T = float (mixed precision): the
+// FP64 state rounded to FP32 as for the shadows, the reconstruction, the
+// transverse parabolas, the point fluxes and the Simpson sums in FP32, the
+// flux differences as exact FP32 pairs and the update in FP64.
 //
 // Three launches per stage, each with one CTA per (item, direction[, plane]):
 //   faces   PPM of the 10 x 10 pencils along d around the sub-grid (their
@@ -70,7 +74,8 @@ __device__ __forceinline__ long long full_cell_offset(const int32_t* __restrict_
 
 // Step 1: face averages of the pencils along d.  fa[item][d][side][f][m][p]:
 // side 0 the right edge of cell m + 2 (the left state of face m + 2 + 1/2),
-// side 1 the left edge of cell m + 3; p = t2 * 10 + t1, t = -1 .. 8 + 1.
+// side 1 the left edge of cell m + 3; p = (t2 + 1) * 10 + (t1 + 1) for the
+// pencils at interior transverse coordinates t1, t2 = -1 .. 8.
 // (Loading field f + 1 into registers during field f's PPM was measured
 // slower: the registers it takes lower the occupancy more than the overlap
 // gains.)
