@@ -76,9 +76,10 @@ __device__ __forceinline__ long long full_cell_offset(const int32_t* __restrict_
 // side 0 the right edge of cell m + 2 (the left state of face m + 2 + 1/2),
 // side 1 the left edge of cell m + 3; p = (t2 + 1) * 10 + (t1 + 1) for the
 // pencils at interior transverse coordinates t1, t2 = -1 .. 8.
-// (Loading field f + 1 into registers during field f's PPM was measured
-// slower: the registers it takes lower the occupancy more than the overlap
-// gains.)
+// (Loading field f + 1 into registers during field f's PPM was measured: on
+// the L2-resident 64^3 box it was slower, 129 against 118 us, its registers
+// lowering the occupancy; on the 128^3 box the mixed stage took 3.11 against
+// 3.19 ms, within the run-to-run spread.  The simpler form stays.)
 template <typename T>
 __global__ void __launch_bounds__(R3_THREADS) recon3d_faces(Recon3dArgs a) {
   __shared__ T q[NPEN3 * QS];
