@@ -246,3 +246,26 @@ def test_margin_cells_of_the_transverse_tests(oracle_mod):
     assert 5 not in _flagged_rows(m)
     with pytest.raises(ValueError):
         oracle_mod.Oracle(W.config(3).grid).margin_cells3d(W.config(3).state(), 2.0 ** -24)
+
+
+@pytest.mark.parametrize("nb,seed", [((1, 1, 1), 3), ((2, 2, 2), 4), ((3, 2, 1), 5)])
+def test_numpy_restatement_on_the_global_array(oracle_mod, nb, seed):
+    """tests/numpy_stage3d.py states the same stage on the global array of a
+    periodic box (neighbours by np.roll: no sub-grids, ghost fill or
+    neighbour tables); one blended stage agrees with the oracle bit for bit,
+    maximum speed included, on one sub-grid, on 2 x 2 x 2 and on a box with
+    unequal sub-grid counts per axis."""
+    from tests import numpy_stage3d as N3
+    G = H.random_smooth_global((8 * nb[2], 8 * nb[1], 8 * nb[0]), seed)
+    g = W.uniform_grid(nb, (0.0, 0.0, 0.0), 1.0 / (8 * max(nb)))
+    o = oracle_mod.Oracle(g)
+    U = o.fill_ghosts_full(H.scatter(G, nb))
+    _, ms0, _ = o.stage3d(U, 0.0)
+    dt = 0.4 / ms0[1]
+    G0 = G * (1.0 + 1e-3 * np.sin(np.arange(G.size).reshape(G.shape)))
+    U0 = o.fill_ghosts_full(H.scatter(G0, nb))
+    ref, ms, st = o.stage3d(U, dt, U0=U0, beta=0.25)
+    assert st == 0
+    got, amax = N3.stage(G, g.dx[0], dt, G0=G0, beta=0.25)
+    assert np.array_equal(H.gather(ref, nb), got)
+    assert amax == ms[0]
