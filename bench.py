@@ -63,7 +63,7 @@ RECON3D_FLOPS_PER_CELL = (1542778255 + 1342567247 + 2 * 760421186) / 262144.0   
 # DRAM bytes (read + write) per cell-update of the mixed stage kernel from one ncu capture
 # (average of the three RK3 stage launches), valid only for the kernel sources it was taken on
 # (STAGE_SOURCES, hashed in that order).
-STAGE_TRAFFIC = {"sha256_prefix": "9e9b4e981b1715ab", "bytes_per_cell": 302.4,
+STAGE_TRAFFIC = {"sha256_prefix": "61593a21ff5defa8", "bytes_per_cell": 302.4,
                  "source": "ncu capture of the three RK3 stage launches on the 4097-leaf reduced binary octree "
                            "(average), scaled by cells"}
 

@@ -19,6 +19,7 @@
 
 #include "hydro.h"
 #include "hydro_internal.cuh"
+#include "hydro_recon3d.cuh"
 
 using namespace hydro;
 

@@ -38,6 +38,7 @@
 #include <mutex>
 
 #include "hydro_internal.cuh"
+#include "hydro_recon3d.cuh"
 #include "hydro_scheme.cuh"
 
 namespace hydro {
