@@ -1,6 +1,6 @@
 """GPU parity of the three-dimensional reconstruction with Simpson face
-quadrature (HYDRO_PARAM_RECON3D, FP64, grids of one level) against the
-oracle's `stage3d` / `rk3_step3d`, through the C ABI.
+quadrature (HYDRO_PARAM_RECON3D, grids of one level, both precisions) against
+the oracle's `stage3d` / `rk3_step3d`, through the C ABI.
 
 Gate: the FP64 gate of the other parity tests (R12 <= 1e-12 per field; the
 kernels round every operation as the oracle does, so the results agree bit for
