@@ -41,6 +41,23 @@ def test_full_ghost_fill_is_the_periodic_field(oracle_mod):
         assert np.array_equal(U[s], expect), s
 
 
+def test_full_ghost_fill_clamps_at_outflow_boundaries(oracle_mod):
+    """On a 3 x 2 x 2 box with outflow boundaries every padded cell (faces,
+    edges, corners) holds the global cell at its index clamped to the box,
+    axis by axis."""
+    nb = (3, 2, 2)
+    G = H.random_smooth_global((16, 16, 24), 9)
+    g = W.uniform_grid(nb, (0.0, 0.0, 0.0), 1.0 / 24, periodic=(False, False, False))
+    o = oracle_mod.Oracle(g)
+    U = o.fill_ghosts_full(H.scatter(G, nb))
+    dims = (24, 16, 16)                                       # x, y, z
+    for s in range(g.n):
+        base = np.round(g.origin[s] / g.dx[s]).astype(int) - 3
+        idx = [np.clip(base[a] + np.arange(14), 0, dims[a] - 1) for a in range(3)]
+        expect = G[:, idx[2]][:, :, idx[1]][:, :, :, idx[0]]
+        assert np.array_equal(U[s], expect), s
+
+
 def _face_state(rho, u, p):
     """Conserved state (11) of density rho, x velocity u, pressure p."""
     X = [0.1, 0.2, 0.3, 0.4, 0.5]
