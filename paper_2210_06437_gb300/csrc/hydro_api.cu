@@ -105,7 +105,7 @@ struct hydro_handle {
   int occupancy_cw = 1;                // resident CTAs per SM of the stage kernel with the CW84 extensions
   int cw84 = 0;                        // CW84 PPM extensions: bit 0 flattening, bit 1 contact steepening
   int single_level = 0;                // one cell width and no coarse-fine faces
-  int recon3d = 0;                     // FP64 stages by the 3D reconstruction with Simpson face quadrature
+  int recon3d = 0;                     // stages by the 3D reconstruction with Simpson face quadrature
   double* d_r3_fa = nullptr;           // its scratch: face averages and face fluxes of n items
   double* d_r3_fl = nullptr;
   int32_t* d_done = nullptr;           // [n] stages completed in the current launch
